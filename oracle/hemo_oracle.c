@@ -1,0 +1,783 @@
+/*
+ * CPU oracle for the coupled lattice-Boltzmann / immersed-boundary time step
+ * of the HemoCell method (Zavodszky et al., "Cellular blood flow modelling
+ * with HemoCell").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline / reference leg load this library; the product
+ * (the CUDA library) never calls it and shares no code with it.
+ *
+ * Plain FP64 loops, two population arrays and pull streaming, in the order
+ * the method states.  Paper passages followed:
+ *   Sec. 2.2  BGK lattice-Boltzmann update (eq. for f_i(x+e_i, t+1)), the
+ *             moments rho = sum_i f_i and u = sum_i f_i e_i / rho, the
+ *             second-order equilibrium w_i rho [1 + 3 e.u + 9/2 (e.u)^2 -
+ *             3/2 u^2], nu = c_s^2 (tau - 1/2), c_s = 1/sqrt(3), D3Q19.
+ *   Sec. 2.3  explicit immersed-boundary coupling through external force
+ *             terms: lattice velocity interpolated to the membrane vertices,
+ *             vertex forces spread back onto the lattice;
+ *             F_total = F_link + F_bend + F_area + F_volume.
+ *   Sec. 2.5  no-slip walls, periodic boundaries, walls moving in opposite
+ *             directions (shear).
+ *   Sec. 2.6  Euler integration of the vertex positions, cell update every
+ *             fluid step.
+ * Readings where the paper is silent (each also applied by the CUDA path,
+ * which implements them independently):
+ *   - forcing: Guo-Zheng-Shi source term with the half-force velocity;
+ *   - walls: halfway bounce-back; moving wall adds -6 w_i rho (e_i . u_w)
+ *     with rho the density of the colliding fluid node; nodes outside a
+ *     non-periodic axis behave as resting walls;
+ *   - coupling kernel: Peskin's 4-point kernel (not the 2-point "linear"
+ *     kernel), interpolating the post-streaming velocity that includes F/2;
+ *     spreading onto wall nodes is discarded; interpolation sees the wall
+ *     velocity at wall nodes;
+ *   - link: strain-stiffening energy K L0 [eps^2/2 - 1/2 ln(1 - eps^2/m^2)],
+ *     K = k_link kBT / p, eps = (L - L0)/L0, m = maximum strain;
+ *   - bending: 1/2 k_bend kBT (theta - theta0)^2 per edge, theta the signed
+ *     angle between the outward normals of the two triangles of the edge;
+ *   - area / volume: per cell, in strain form 1/2 k_area ((A - A0)/A0)^2 and
+ *     1/2 k_volume ((V - V0)/V0)^2 with k in lattice energy units.  (The form
+ *     1/2 k (V - V0)^2 / V0 with k_volume = 20 makes the explicit coupling
+ *     diverge within 20 steps on a single red cell in shear; Sec. 2.3 says
+ *     the free parameters are tuned for numerical stability.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 19
+
+/* ------------------------------------------------------------------------ */
+/* D3Q19 velocity set: every c in {-1,0,1}^3 with |c|^2 <= 2, enumerated with */
+/* cx slowest and cz fastest; weights 1/3 (|c|^2 = 0), 1/18 (1), 1/36 (2).   */
+/* ------------------------------------------------------------------------ */
+static int C[Q][3];
+static double W[Q];
+static int OPP[Q];
+static int tables_ready = 0;
+
+static void build_tables(void) {
+    if (tables_ready) return;
+    int q = 0;
+    for (int cx = -1; cx <= 1; ++cx)
+        for (int cy = -1; cy <= 1; ++cy)
+            for (int cz = -1; cz <= 1; ++cz) {
+                int n2 = cx * cx + cy * cy + cz * cz;
+                if (n2 > 2) continue;
+                C[q][0] = cx; C[q][1] = cy; C[q][2] = cz;
+                W[q] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+                ++q;
+            }
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j)
+            if (C[j][0] == -C[i][0] && C[j][1] == -C[i][1] && C[j][2] == -C[i][2]) OPP[i] = j;
+    tables_ready = 1;
+}
+
+void ora_d3q19(int *c, double *w, int *opp) {
+    build_tables();
+    for (int i = 0; i < Q; ++i) {
+        for (int d = 0; d < 3; ++d) c[3 * i + d] = C[i][d];
+        w[i] = W[i];
+        opp[i] = OPP[i];
+    }
+}
+
+/* Sec. 2.2 equilibrium */
+void ora_equilibrium(double rho, const double *u, double *feq) {
+    build_tables();
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+        double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        feq[i] = W[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+/* Peskin's 4-point kernel (Peskin 2002), piecewise definition */
+double ora_phi(double r) {
+    double a = fabs(r);
+    if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+    if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) / 8.0;
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                      */
+/* ------------------------------------------------------------------------ */
+static void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------------ */
+/* membrane mesh type                                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nv, nt, ne;
+    int *tri;       /* nt*3, outward counter-clockwise */
+    int *edge;      /* ne*4: v0, v1, a, b; triangle (v0,v1,a) and (v1,v0,b) */
+    double *L0;     /* rest length per edge */
+    double *th0;    /* rest dihedral angle per edge */
+    double A0, V0;
+    double k_link, k_bend, k_area, k_volume, kbt, persistence, max_strain;
+} omesh;
+
+/* Edge table: triangles in order, their directed edges (t0,t1), (t1,t2),
+ * (t2,t0); an undirected edge met for the first time gets the next id with
+ * v0, v1 in the direction met and a = the triangle's third vertex; the second
+ * time (necessarily in the reverse direction for an oriented closed mesh) b
+ * = that triangle's third vertex.  Returns the number of edges, or -1 if the
+ * mesh is not a consistently oriented closed 2-manifold. */
+int ora_build_edges(int nv, int nt, const int *tri, int *edge_out /* capacity 3*nt/2*4 */) {
+    int maxe = 3 * nt / 2 + 1;
+    int *head = (int *)malloc(sizeof(int) * nv);
+    int *next = (int *)malloc(sizeof(int) * maxe);
+    int *seen = (int *)malloc(sizeof(int) * maxe); /* times seen */
+    for (int v = 0; v < nv; ++v) head[v] = -1;
+    int ne = 0, bad = 0;
+    for (int t = 0; t < nt && !bad; ++t) {
+        for (int k = 0; k < 3; ++k) {
+            int a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3], o = tri[3 * t + (k + 2) % 3];
+            int lo = a < b ? a : b, hi = a < b ? b : a;
+            int found = -1;
+            for (int e = head[lo]; e >= 0; e = next[e]) {
+                int e0 = edge_out[4 * e], e1 = edge_out[4 * e + 1];
+                int elo = e0 < e1 ? e0 : e1, ehi = e0 < e1 ? e1 : e0;
+                if (elo == lo && ehi == hi) { found = e; break; }
+            }
+            if (found < 0) {
+                if (ne >= maxe) { bad = 1; break; }
+                edge_out[4 * ne + 0] = a;
+                edge_out[4 * ne + 1] = b;
+                edge_out[4 * ne + 2] = o;
+                edge_out[4 * ne + 3] = -1;
+                seen[ne] = 1;
+                next[ne] = head[lo];
+                head[lo] = ne;
+                ++ne;
+            } else {
+                if (seen[found] != 1 || edge_out[4 * found] != b || edge_out[4 * found + 1] != a) { bad = 1; break; }
+                edge_out[4 * found + 3] = o;
+                seen[found] = 2;
+            }
+        }
+    }
+    for (int e = 0; e < ne && !bad; ++e) if (seen[e] != 2) bad = 1;
+    free(head); free(next); free(seen);
+    return bad ? -1 : ne;
+}
+
+/* signed dihedral angle of edge (p0,p1) with wings pa (triangle p0,p1,pa) and
+ * pb (triangle p1,p0,pb): atan2(e^ . (n1 x n2), n1 . n2) */
+static double dihedral(const double *p0, const double *p1, const double *pa, const double *pb) {
+    double e[3], da[3], db[3], n1[3], n2[3], c[3];
+    sub3(p1, p0, e); sub3(pa, p0, da); sub3(pb, p0, db);
+    cross3(e, da, n1);
+    cross3(db, e, n2);
+    cross3(n1, n2, c);
+    double L = sqrt(dot3(e, e));
+    return atan2(dot3(c, e) / L, dot3(n1, n2));
+}
+
+static void cell_area_volume(const omesh *m, const double *X, double *A, double *V) {
+    double ctr[3] = {0, 0, 0};
+    for (int v = 0; v < m->nv; ++v) for (int d = 0; d < 3; ++d) ctr[d] += X[3 * v + d];
+    for (int d = 0; d < 3; ++d) ctr[d] /= m->nv;
+    double a = 0, vol = 0;
+    for (int t = 0; t < m->nt; ++t) {
+        const double *x0 = X + 3 * m->tri[3 * t], *x1 = X + 3 * m->tri[3 * t + 1], *x2 = X + 3 * m->tri[3 * t + 2];
+        double e1[3], e2[3], n[3], r0[3], r1[3], r2[3], rc[3];
+        sub3(x1, x0, e1); sub3(x2, x0, e2); cross3(e1, e2, n);
+        a += 0.5 * sqrt(dot3(n, n));
+        sub3(x0, ctr, r0); sub3(x1, ctr, r1); sub3(x2, ctr, r2);
+        cross3(r1, r2, rc);
+        vol += dot3(r0, rc) / 6.0;
+    }
+    *A = a; *V = vol;
+}
+
+static int mesh_init(omesh *m, int nv, int nt, const int *tri, const double *rest, const double *params) {
+    m->nv = nv; m->nt = nt;
+    m->tri = (int *)malloc(sizeof(int) * 3 * nt);
+    memcpy(m->tri, tri, sizeof(int) * 3 * nt);
+    m->edge = (int *)malloc(sizeof(int) * 4 * (3 * nt / 2 + 1));
+    m->ne = ora_build_edges(nv, nt, tri, m->edge);
+    if (m->ne < 0) return -1;
+    m->L0 = (double *)malloc(sizeof(double) * m->ne);
+    m->th0 = (double *)malloc(sizeof(double) * m->ne);
+    for (int e = 0; e < m->ne; ++e) {
+        const int *E = m->edge + 4 * e;
+        double d[3];
+        sub3(rest + 3 * E[1], rest + 3 * E[0], d);
+        m->L0[e] = sqrt(dot3(d, d));
+        m->th0[e] = dihedral(rest + 3 * E[0], rest + 3 * E[1], rest + 3 * E[2], rest + 3 * E[3]);
+    }
+    cell_area_volume(m, rest, &m->A0, &m->V0);
+    m->k_link = params[0]; m->k_bend = params[1]; m->k_area = params[2]; m->k_volume = params[3];
+    m->kbt = params[4]; m->persistence = params[5]; m->max_strain = params[6];
+    return 0;
+}
+
+static void mesh_free(omesh *m) {
+    free(m->tri); free(m->edge); free(m->L0); free(m->th0);
+}
+
+/* Sec. 2.3: F_v = -dE/dX_v with E = E_link + E_bend + E_area + E_volume.
+ * Adds forces into F (nv*3); returns the four energies in E4 (may be NULL);
+ * writes the cell's area and volume. */
+static void membrane_forces(const omesh *m, const double *X, double *F, double *E4, double *Aout, double *Vout) {
+    double El = 0, Eb = 0, Ea = 0, Ev = 0;
+    /* link: per edge */
+    double K = m->k_link * m->kbt / m->persistence;
+    double mm = m->max_strain * m->max_strain;
+    for (int e = 0; e < m->ne; ++e) {
+        const int *E = m->edge + 4 * e;
+        double d[3];
+        sub3(X + 3 * E[1], X + 3 * E[0], d);
+        double L = sqrt(dot3(d, d));
+        double eps = (L - m->L0[e]) / m->L0[e];
+        El += K * m->L0[e] * (0.5 * eps * eps - 0.5 * log(1.0 - eps * eps / mm));
+        double dEdL = K * (eps + eps / (mm - eps * eps));
+        for (int k = 0; k < 3; ++k) {
+            F[3 * E[0] + k] += dEdL * d[k] / L;
+            F[3 * E[1] + k] -= dEdL * d[k] / L;
+        }
+    }
+    /* bending: per edge, gradient of the dihedral angle */
+    double kb = m->k_bend * m->kbt;
+    for (int e = 0; e < m->ne; ++e) {
+        const int *E = m->edge + 4 * e;
+        const double *p0 = X + 3 * E[0], *p1 = X + 3 * E[1], *pa = X + 3 * E[2], *pb = X + 3 * E[3];
+        double th = dihedral(p0, p1, pa, pb);
+        double dth = th - m->th0[e];
+        Eb += 0.5 * kb * dth * dth;
+        double ed[3], da[3], db[3], n1[3], n2[3], t1[3], t0[3], ta[3], tb[3];
+        sub3(p1, p0, ed); sub3(pa, p0, da); sub3(pb, p0, db);
+        cross3(ed, da, n1);
+        cross3(db, ed, n2);
+        double L = sqrt(dot3(ed, ed));
+        double q1 = dot3(n1, n1), q2 = dot3(n2, n2);
+        double pa1[3], pb1[3];
+        sub3(pa, p1, pa1); sub3(pb, p1, pb1);
+        double sa0 = dot3(pa1, ed) / L, sb0 = dot3(pb1, ed) / L; /* (pa-p1).e/L, (pb-p1).e/L */
+        double sa1 = dot3(da, ed) / L, sb1 = dot3(db, ed) / L;   /* (pa-p0).e/L, (pb-p0).e/L */
+        for (int k = 0; k < 3; ++k) {
+            ta[k] = -L * n1[k] / q1;
+            tb[k] = -L * n2[k] / q2;
+            t0[k] = -sa0 * n1[k] / q1 - sb0 * n2[k] / q2;
+            t1[k] = sa1 * n1[k] / q1 + sb1 * n2[k] / q2;
+        }
+        double c = kb * dth;
+        for (int k = 0; k < 3; ++k) {
+            F[3 * E[0] + k] -= c * t0[k];
+            F[3 * E[1] + k] -= c * t1[k];
+            F[3 * E[2] + k] -= c * ta[k];
+            F[3 * E[3] + k] -= c * tb[k];
+        }
+    }
+    /* area and volume: per cell totals, then per triangle gradients */
+    double A, V;
+    cell_area_volume(m, X, &A, &V);
+    Ea = 0.5 * m->k_area * (A - m->A0) * (A - m->A0) / (m->A0 * m->A0);
+    Ev = 0.5 * m->k_volume * (V - m->V0) * (V - m->V0) / (m->V0 * m->V0);
+    double ca = m->k_area * (A - m->A0) / (m->A0 * m->A0);
+    double cv = m->k_volume * (V - m->V0) / (m->V0 * m->V0);
+    double ctr[3] = {0, 0, 0};
+    for (int v = 0; v < m->nv; ++v) for (int d = 0; d < 3; ++d) ctr[d] += X[3 * v + d];
+    for (int d = 0; d < 3; ++d) ctr[d] /= m->nv;
+    for (int t = 0; t < m->nt; ++t) {
+        int i0 = m->tri[3 * t], i1 = m->tri[3 * t + 1], i2 = m->tri[3 * t + 2];
+        const double *x0 = X + 3 * i0, *x1 = X + 3 * i1, *x2 = X + 3 * i2;
+        double e1[3], e2[3], n[3];
+        sub3(x1, x0, e1); sub3(x2, x0, e2); cross3(e1, e2, n);
+        double nn = sqrt(dot3(n, n));
+        double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+        double d21[3], d02[3], d10[3], g0[3], g1[3], g2[3];
+        sub3(x2, x1, d21); sub3(x0, x2, d02); sub3(x1, x0, d10);
+        cross3(nh, d21, g0); cross3(nh, d02, g1); cross3(nh, d10, g2);
+        double r0[3], r1[3], r2[3], v0[3], v1[3], v2[3];
+        sub3(x0, ctr, r0); sub3(x1, ctr, r1); sub3(x2, ctr, r2);
+        cross3(r1, r2, v0); cross3(r2, r0, v1); cross3(r0, r1, v2);
+        for (int k = 0; k < 3; ++k) {
+            F[3 * i0 + k] -= ca * 0.5 * g0[k] + cv * v0[k] / 6.0;
+            F[3 * i1 + k] -= ca * 0.5 * g1[k] + cv * v1[k] / 6.0;
+            F[3 * i2 + k] -= ca * 0.5 * g2[k] + cv * v2[k] / 6.0;
+        }
+    }
+    if (E4) { E4[0] = El; E4[1] = Eb; E4[2] = Ea; E4[3] = Ev; }
+    if (Aout) *Aout = A;
+    if (Vout) *Vout = V;
+}
+
+/* Standalone membrane evaluation for one cell (pins): rest shape + params,
+ * positions X; writes forces F (nv*3, overwritten) and energies E4. */
+int ora_membrane(int nv, int nt, const int *tri, const double *rest, const double *params,
+                 const double *X, double *F, double *E4, double *AV) {
+    omesh m;
+    if (mesh_init(&m, nv, nt, tri, rest, params) < 0) { mesh_free(&m); return -1; }
+    memset(F, 0, sizeof(double) * 3 * nv);
+    double A, V;
+    membrane_forces(&m, X, F, E4, &A, &V);
+    if (AV) { AV[0] = A; AV[1] = V; AV[2] = m.A0; AV[3] = m.V0; }
+    mesh_free(&m);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* simulation                                                                */
+/* ------------------------------------------------------------------------ */
+#define MAXTYPES 8
+typedef struct {
+    int nx, ny, nz;
+    long N;
+    double tau;
+    int periodic[3];
+    unsigned char *mask;   /* N */
+    double uw[4][3];       /* wall velocity by mask id */
+    double g[3];
+    double *f, *fn;        /* N*Q */
+    double *rho_c;         /* collision density, N */
+    double *F;             /* N*3 */
+    double *u;             /* N*3 */
+    int ntypes;
+    omesh types[MAXTYPES];
+    int ncell;
+    int *cell_type, *cell_first;
+    long nvtot;
+    double *X, *Fv;        /* nvtot*3 */
+    double *X0c;           /* initial centroids, ncell*3 */
+    double discarded[3];
+} osim;
+
+void *ora_create(int nx, int ny, int nz, double tau, const int *periodic, const unsigned char *mask,
+                 const double *wall_velocity, const double *g) {
+    build_tables();
+    osim *s = (osim *)calloc(1, sizeof(osim));
+    s->nx = nx; s->ny = ny; s->nz = nz;
+    s->N = (long)nx * ny * nz;
+    s->tau = tau;
+    for (int d = 0; d < 3; ++d) s->periodic[d] = periodic[d];
+    s->mask = (unsigned char *)calloc(s->N, 1);
+    if (mask) memcpy(s->mask, mask, s->N);
+    for (int d = 0; d < 3; ++d) {
+        s->uw[0][d] = 0; s->uw[1][d] = 0;
+        s->uw[2][d] = wall_velocity ? wall_velocity[d] : 0;
+        s->uw[3][d] = wall_velocity ? wall_velocity[3 + d] : 0;
+        s->g[d] = g ? g[d] : 0;
+    }
+    s->f = (double *)malloc(sizeof(double) * Q * s->N);
+    s->fn = (double *)malloc(sizeof(double) * Q * s->N);
+    s->rho_c = (double *)malloc(sizeof(double) * s->N);
+    s->F = (double *)calloc(3 * s->N, sizeof(double));
+    s->u = (double *)calloc(3 * s->N, sizeof(double));
+    for (long n = 0; n < s->N; ++n) {
+        for (int i = 0; i < Q; ++i) s->f[n * Q + i] = W[i];
+        if (s->mask[n]) for (int d = 0; d < 3; ++d) s->u[3 * n + d] = s->uw[s->mask[n]][d];
+    }
+    return s;
+}
+
+void ora_destroy(void *p) {
+    osim *s = (osim *)p;
+    if (!s) return;
+    for (int t = 0; t < s->ntypes; ++t) mesh_free(&s->types[t]);
+    free(s->mask); free(s->f); free(s->fn); free(s->rho_c); free(s->F); free(s->u);
+    free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c);
+    free(s);
+}
+
+int ora_add_mesh(void *p, int nv, int nt, const int *tri, const double *rest, const double *params) {
+    osim *s = (osim *)p;
+    if (s->ntypes >= MAXTYPES) return -1;
+    if (mesh_init(&s->types[s->ntypes], nv, nt, tri, rest, params) < 0) return -1;
+    return s->ntypes++;
+}
+
+static void centroid(const double *X, int nv, double *c) {
+    c[0] = c[1] = c[2] = 0;
+    for (int v = 0; v < nv; ++v) for (int d = 0; d < 3; ++d) c[d] += X[3 * v + d];
+    for (int d = 0; d < 3; ++d) c[d] /= nv;
+}
+
+/* cells of one type: vertices = R * rest + center */
+int ora_add_cells(void *p, int type, int ncell, const double *centers, const double *rots, const double *rest) {
+    osim *s = (osim *)p;
+    if (type < 0 || type >= s->ntypes) return -1;
+    int nv = s->types[type].nv;
+    long old = s->nvtot;
+    s->cell_type = (int *)realloc(s->cell_type, sizeof(int) * (s->ncell + ncell));
+    s->cell_first = (int *)realloc(s->cell_first, sizeof(int) * (s->ncell + ncell));
+    s->X0c = (double *)realloc(s->X0c, sizeof(double) * 3 * (s->ncell + ncell));
+    s->X = (double *)realloc(s->X, sizeof(double) * 3 * (old + (long)ncell * nv));
+    s->Fv = (double *)realloc(s->Fv, sizeof(double) * 3 * (old + (long)ncell * nv));
+    for (int c = 0; c < ncell; ++c) {
+        int id = s->ncell + c;
+        s->cell_type[id] = type;
+        s->cell_first[id] = (int)(old + (long)c * nv);
+        const double *R = rots + 9 * c;
+        for (int v = 0; v < nv; ++v) {
+            double *x = s->X + 3 * (old + (long)c * nv + v);
+            for (int d = 0; d < 3; ++d)
+                x[d] = centers[3 * c + d] + R[3 * d] * rest[3 * v] + R[3 * d + 1] * rest[3 * v + 1] + R[3 * d + 2] * rest[3 * v + 2];
+            s->Fv[3 * (old + (long)c * nv + v)] = 0;
+            s->Fv[3 * (old + (long)c * nv + v) + 1] = 0;
+            s->Fv[3 * (old + (long)c * nv + v) + 2] = 0;
+        }
+        centroid(s->X + 3 * (old + (long)c * nv), nv, s->X0c + 3 * id);
+    }
+    s->ncell += ncell;
+    s->nvtot = old + (long)ncell * nv;
+    return 0;
+}
+
+void ora_set_vertices(void *p, const double *X) {
+    osim *s = (osim *)p;
+    memcpy(s->X, X, sizeof(double) * 3 * s->nvtot);
+}
+
+/* populations at equilibrium with rho = 1 and the given velocity field
+ * (N*3, NULL = rest) */
+void ora_set_velocity(void *p, const double *u0) {
+    osim *s = (osim *)p;
+    for (long n = 0; n < s->N; ++n) {
+        if (s->mask[n]) continue;
+        double u[3] = {0, 0, 0};
+        if (u0) { u[0] = u0[3 * n]; u[1] = u0[3 * n + 1]; u[2] = u0[3 * n + 2]; }
+        ora_equilibrium(1.0, u, s->f + n * Q);
+        for (int d = 0; d < 3; ++d) s->u[3 * n + d] = u[d];
+    }
+}
+
+/* neighbour of node (x,y,z) along c; returns -1 outside a non-periodic axis */
+static long neighbour(const osim *s, int x, int y, int z, int cx, int cy, int cz) {
+    int xx = x + cx, yy = y + cy, zz = z + cz;
+    int dims[3] = {s->nx, s->ny, s->nz};
+    int q[3] = {xx, yy, zz};
+    for (int d = 0; d < 3; ++d) {
+        if (q[d] < 0 || q[d] >= dims[d]) {
+            if (!s->periodic[d]) return -1;
+            q[d] = ((q[d] % dims[d]) + dims[d]) % dims[d];
+        }
+    }
+    return q[0] + (long)s->nx * (q[1] + (long)s->ny * q[2]);
+}
+
+/* node index of lattice coordinate j along each axis, -1 if outside */
+static long node_at(const osim *s, long jx, long jy, long jz) {
+    long q[3] = {jx, jy, jz};
+    long dims[3] = {s->nx, s->ny, s->nz};
+    for (int d = 0; d < 3; ++d) {
+        if (q[d] < 0 || q[d] >= dims[d]) {
+            if (!s->periodic[d]) return -1;
+            q[d] = ((q[d] % dims[d]) + dims[d]) % dims[d];
+        }
+    }
+    return q[0] + s->nx * (q[1] + s->ny * q[2]);
+}
+
+/* Per fluid node: bit i set when node + c_i is a wall or outside a
+ * non-periodic axis (oracle's velocity order); 0 at wall nodes. */
+void ora_wall_links(void *p, uint32_t *links) {
+    osim *s = (osim *)p;
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long n = x + (long)s->nx * (y + (long)s->ny * z);
+                uint32_t b = 0;
+                if (!s->mask[n])
+                    for (int i = 0; i < Q; ++i) {
+                        long m = neighbour(s, x, y, z, C[i][0], C[i][1], C[i][2]);
+                        if (m < 0 || s->mask[m]) b |= 1u << i;
+                    }
+                links[n] = b;
+            }
+}
+
+/* one coupled step, Sec. 2.3 order: forces at X^n, spread, collide+stream,
+ * velocity, interpolate and move */
+static void step_once(osim *s) {
+    const long N = s->N;
+    /* 1-2: membrane forces at the current positions (per cell) */
+    for (long v = 0; v < 3 * s->nvtot; ++v) s->Fv[v] = 0;
+    for (int c = 0; c < s->ncell; ++c) {
+        const omesh *m = &s->types[s->cell_type[c]];
+        long o = s->cell_first[c];
+        membrane_forces(m, s->X + 3 * o, s->Fv + 3 * o, NULL, NULL, NULL);
+    }
+    /* 3: F(x) = g + sum_v F_v delta_h(x - X_v); wall nodes discard */
+    for (long n = 0; n < N; ++n)
+        for (int d = 0; d < 3; ++d) s->F[3 * n + d] = s->mask[n] ? 0.0 : s->g[d];
+    s->discarded[0] = s->discarded[1] = s->discarded[2] = 0;
+    for (long v = 0; v < s->nvtot; ++v) {
+        const double *X = s->X + 3 * v;
+        long i0[3];
+        for (int d = 0; d < 3; ++d) i0[d] = (long)floor(X[d]);
+        for (int a = -1; a <= 2; ++a)
+            for (int b = -1; b <= 2; ++b)
+                for (int c = -1; c <= 2; ++c) {
+                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
+                    double dl = ora_phi(X[0] - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
+                    long n = node_at(s, jx, jy, jz);
+                    for (int d = 0; d < 3; ++d) {
+                        double add = s->Fv[3 * v + d] * dl;
+                        if (n >= 0 && !s->mask[n]) s->F[3 * n + d] += add;
+                        else s->discarded[d] += add;
+                    }
+                }
+    }
+    /* 4: BGK collision with the Guo forcing term (in place in f) */
+    double om = 1.0 / s->tau;
+    for (long n = 0; n < N; ++n) {
+        if (s->mask[n]) continue;
+        double *f = s->f + n * Q;
+        const double *Fn = s->F + 3 * n;
+        double rho = 0, m[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+            rho += f[i];
+            for (int d = 0; d < 3; ++d) m[d] += f[i] * C[i][d];
+        }
+        double u[3];
+        for (int d = 0; d < 3; ++d) u[d] = (m[d] + 0.5 * Fn[d]) / rho;
+        double feq[Q];
+        ora_equilibrium(rho, u, feq);
+        for (int i = 0; i < Q; ++i) {
+            double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+            double Si = 0;
+            for (int d = 0; d < 3; ++d) Si += (3.0 * (C[i][d] - u[d]) + 9.0 * cu * C[i][d]) * Fn[d];
+            Si *= (1.0 - 0.5 * om) * W[i];
+            f[i] = f[i] - om * (f[i] - feq[i]) + Si;
+        }
+        s->rho_c[n] = rho;
+    }
+    /* 5: pull streaming with halfway bounce-back */
+    for (int z = 0; z < s->nz; ++z)
+        for (int y = 0; y < s->ny; ++y)
+            for (int x = 0; x < s->nx; ++x) {
+                long n = x + (long)s->nx * (y + (long)s->ny * z);
+                if (s->mask[n]) continue;
+                for (int i = 0; i < Q; ++i) {
+                    long src = neighbour(s, x, y, z, -C[i][0], -C[i][1], -C[i][2]);
+                    if (src >= 0 && !s->mask[src]) {
+                        s->fn[n * Q + i] = s->f[src * Q + i];
+                    } else {
+                        int j = OPP[i];
+                        const double *uw = s->uw[src >= 0 ? s->mask[src] : 1];
+                        double cu = C[j][0] * uw[0] + C[j][1] * uw[1] + C[j][2] * uw[2];
+                        s->fn[n * Q + i] = s->f[n * Q + j] - 6.0 * W[j] * s->rho_c[n] * cu;
+                    }
+                }
+            }
+    double *tmp = s->f; s->f = s->fn; s->fn = tmp;
+    /* 6: velocity of the streamed populations with the applied force F/2 */
+    for (long n = 0; n < N; ++n) {
+        if (s->mask[n]) continue;
+        const double *f = s->f + n * Q;
+        double rho = 0, m[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+            rho += f[i];
+            for (int d = 0; d < 3; ++d) m[d] += f[i] * C[i][d];
+        }
+        for (int d = 0; d < 3; ++d) s->u[3 * n + d] = (m[d] + 0.5 * s->F[3 * n + d]) / rho;
+    }
+    /* 7: interpolate at X^n and move (Euler, dt = 1) */
+    for (long v = 0; v < s->nvtot; ++v) {
+        double *X = s->X + 3 * v;
+        long i0[3];
+        for (int d = 0; d < 3; ++d) i0[d] = (long)floor(X[d]);
+        double U[3] = {0, 0, 0};
+        for (int a = -1; a <= 2; ++a)
+            for (int b = -1; b <= 2; ++b)
+                for (int c = -1; c <= 2; ++c) {
+                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
+                    double dl = ora_phi(X[0] - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
+                    long n = node_at(s, jx, jy, jz);
+                    if (n < 0) continue; /* resting wall outside the domain */
+                    for (int d = 0; d < 3; ++d) U[d] += s->u[3 * n + d] * dl;
+                }
+        for (int d = 0; d < 3; ++d) X[d] += U[d];
+    }
+}
+
+void ora_step(void *p, int nsteps) {
+    osim *s = (osim *)p;
+    for (int k = 0; k < nsteps; ++k) step_once(s);
+}
+
+/* density of the current populations (N), velocity field (N*3), vertices
+ * (nvtot*3), last membrane forces (nvtot*3), per-cell stats (ncell*6:
+ * centroid, area, volume, deformation index) at the current positions. */
+static double deformation_index(const double *X, int nv);
+
+void ora_get(void *p, double *rho, double *u, double *X, double *Fv, double *cellstats, double *discarded) {
+    osim *s = (osim *)p;
+    if (rho)
+        for (long n = 0; n < s->N; ++n) {
+            double r = 0;
+            if (!s->mask[n]) for (int i = 0; i < Q; ++i) r += s->f[n * Q + i];
+            rho[n] = s->mask[n] ? 0.0 : r;
+        }
+    if (u) memcpy(u, s->u, sizeof(double) * 3 * s->N);
+    if (X) memcpy(X, s->X, sizeof(double) * 3 * s->nvtot);
+    if (Fv) memcpy(Fv, s->Fv, sizeof(double) * 3 * s->nvtot);
+    if (cellstats)
+        for (int c = 0; c < s->ncell; ++c) {
+            const omesh *m = &s->types[s->cell_type[c]];
+            const double *Xc = s->X + 3 * (long)s->cell_first[c];
+            double ctr[3], A, V;
+            centroid(Xc, m->nv, ctr);
+            cell_area_volume(m, Xc, &A, &V);
+            double *o = cellstats + 6 * c;
+            o[0] = ctr[0]; o[1] = ctr[1]; o[2] = ctr[2]; o[3] = A; o[4] = V;
+            o[5] = deformation_index(Xc, m->nv);
+        }
+    if (discarded) for (int d = 0; d < 3; ++d) discarded[d] = s->discarded[d];
+}
+
+/* raw populations, oracle order, N*Q */
+void ora_get_populations(void *p, double *f) {
+    osim *s = (osim *)p;
+    memcpy(f, s->f, sizeof(double) * Q * s->N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* coupling operators alone (pins): spread F_v -> F and interpolate u -> U   */
+/* ------------------------------------------------------------------------ */
+void ora_spread(void *p, long nv, const double *X, const double *Fv, double *F_out) {
+    osim *s = (osim *)p;
+    memset(F_out, 0, sizeof(double) * 3 * s->N);
+    for (long v = 0; v < nv; ++v) {
+        const double *x = X + 3 * v;
+        long i0[3];
+        for (int d = 0; d < 3; ++d) i0[d] = (long)floor(x[d]);
+        for (int a = -1; a <= 2; ++a)
+            for (int b = -1; b <= 2; ++b)
+                for (int c = -1; c <= 2; ++c) {
+                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
+                    double dl = ora_phi(x[0] - jx) * ora_phi(x[1] - jy) * ora_phi(x[2] - jz);
+                    long n = node_at(s, jx, jy, jz);
+                    if (n < 0 || s->mask[n]) continue;
+                    for (int d = 0; d < 3; ++d) F_out[3 * n + d] += Fv[3 * v + d] * dl;
+                }
+    }
+}
+
+void ora_interpolate(void *p, long nv, const double *X, const double *u, double *U) {
+    osim *s = (osim *)p;
+    for (long v = 0; v < nv; ++v) {
+        const double *x = X + 3 * v;
+        long i0[3];
+        for (int d = 0; d < 3; ++d) i0[d] = (long)floor(x[d]);
+        U[3 * v] = U[3 * v + 1] = U[3 * v + 2] = 0;
+        for (int a = -1; a <= 2; ++a)
+            for (int b = -1; b <= 2; ++b)
+                for (int c = -1; c <= 2; ++c) {
+                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
+                    double dl = ora_phi(x[0] - jx) * ora_phi(x[1] - jy) * ora_phi(x[2] - jz);
+                    long n = node_at(s, jx, jy, jz);
+                    if (n < 0) continue;
+                    for (int d = 0; d < 3; ++d) U[3 * v + d] += u[3 * n + d] * dl;
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* vertex binning: key = lattice block of floor(X) (wrapped on periodic     */
+/* axes, clamped otherwise); stable counting sort by key                    */
+/* ------------------------------------------------------------------------ */
+int ora_bins(void *p, long nv, const double *X, int B, int32_t *key, int32_t *perm, int32_t *start) {
+    osim *s = (osim *)p;
+    int dims[3] = {s->nx, s->ny, s->nz};
+    int nb[3];
+    for (int d = 0; d < 3; ++d) nb[d] = (dims[d] + B - 1) / B;
+    long nbins = (long)nb[0] * nb[1] * nb[2];
+    for (long v = 0; v < nv; ++v) {
+        int b[3];
+        for (int d = 0; d < 3; ++d) {
+            long j = (long)floor(X[3 * v + d]);
+            if (s->periodic[d]) j = ((j % dims[d]) + dims[d]) % dims[d];
+            else j = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
+            b[d] = (int)(j / B);
+        }
+        key[v] = (int32_t)(b[0] + (long)nb[0] * (b[1] + (long)nb[1] * b[2]));
+    }
+    for (long k = 0; k <= nbins; ++k) start[k] = 0;
+    for (long v = 0; v < nv; ++v) start[key[v] + 1]++;
+    for (long k = 0; k < nbins; ++k) start[k + 1] += start[k];
+    int32_t *cursor = (int32_t *)malloc(sizeof(int32_t) * nbins);
+    for (long k = 0; k < nbins; ++k) cursor[k] = start[k];
+    for (long v = 0; v < nv; ++v) perm[cursor[key[v]]++] = (int32_t)v;
+    free(cursor);
+    return (int)nbins;
+}
+
+/* ------------------------------------------------------------------------ */
+/* deformation loss (differentiation form)                                  */
+/* ------------------------------------------------------------------------ */
+/* eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations */
+static void sym3_eigenvalues(double a[3][3], double ev[3]) {
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; ++k) { /* columns p, q */
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - sn * akq;
+                    a[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) { /* rows p, q */
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - sn * aqk;
+                    a[q][k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    ev[0] = a[0][0]; ev[1] = a[1][1]; ev[2] = a[2][2];
+}
+
+/* Taylor deformation index from the gyration tensor G = mean (X-c)(X-c)^T:
+ * DI = (sqrt(l1) - sqrt(l3)) / (sqrt(l1) + sqrt(l3)), l1 >= l2 >= l3 */
+static double deformation_index(const double *X, int nv) {
+    double c[3];
+    centroid(X, nv, c);
+    double G[3][3] = {{0}};
+    for (int v = 0; v < nv; ++v) {
+        double r[3];
+        sub3(X + 3 * v, c, r);
+        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) G[i][j] += r[i] * r[j] / nv;
+    }
+    double ev[3];
+    sym3_eigenvalues(G, ev);
+    double lmax = ev[0], lmin = ev[0];
+    for (int i = 1; i < 3; ++i) { if (ev[i] > lmax) lmax = ev[i]; if (ev[i] < lmin) lmin = ev[i]; }
+    double a = sqrt(lmax), b = sqrt(lmin > 0 ? lmin : 0);
+    return (a - b) / (a + b);
+}
+
+double ora_deformation_index(const double *X, int nv) { return deformation_index(X, nv); }
+
+/* loss = mean_c DI_c + mean_c |centroid_c - initial centroid_c|^2 */
+double ora_loss(void *p) {
+    osim *s = (osim *)p;
+    double di = 0, drift = 0;
+    for (int c = 0; c < s->ncell; ++c) {
+        const omesh *m = &s->types[s->cell_type[c]];
+        const double *Xc = s->X + 3 * (long)s->cell_first[c];
+        double ctr[3];
+        centroid(Xc, m->nv, ctr);
+        di += deformation_index(Xc, m->nv);
+        for (int d = 0; d < 3; ++d) drift += (ctr[d] - s->X0c[3 * c + d]) * (ctr[d] - s->X0c[3 * c + d]);
+    }
+    return s->ncell ? (di + drift) / s->ncell : 0.0;
+}
+
+long ora_num_vertices(void *p) { return ((osim *)p)->nvtot; }
+int ora_num_cells(void *p) { return ((osim *)p)->ncell; }
