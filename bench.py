@@ -1,0 +1,377 @@
+"""Benchmark of the coupled LBM-IBM time step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                [--workload channel|shear|vessel|pipe]
+
+Default workload: suspension of 440 red cells (642 vertices each, 282,480
+vertices, haematocrit ~30 %) in a 64 x 64 x 256 periodic channel with walls
+at y = 0 and y = 63, body-force driven, populations stored as FP32
+deviations.  One step = the whole coupled step (membrane forces, binning,
+spreading, collide + stream, velocity, interpolation + move).  Prints one JSON
+line on rank 0.  Under torchrun every rank runs an independent replica (the
+method is not sharded: replicas only) and rank 0 reports the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_02752_gb300 import inputs as I  # noqa: E402
+
+METRIC = 'coupled LBM-IBM MLUPS & RBC vertices/s; 16-bit/FP32 vs FP64 at fixed error'
+UNIT = 'MLUPS'
+FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+def make_workload(name):
+    if name == 'channel':
+        cfg = I.channel()
+        desc = 'channel 64x64x256 (walls y=0,63), 440 RBC x 642 vertices, FP32 deviations'
+    elif name == 'shear':
+        cfg = I.shear_cell()
+        desc = 'shear box 32^3, 1 RBC x 642 vertices, FP64'
+    elif name == 'vessel':
+        cfg = I.channel(nx=128, ny=128, nz=512, ncell=4460, seed=20230502, steps=200, platelet_ratio=0.1,
+                        name='vessel', pack_iter=60)
+        desc = 'channel 128x128x512 (walls y=0,127), 4460 RBC + 446 platelets, 16-bit deviations'
+    elif name == 'pipe':
+        cfg = I.pipe(pack_iter=20)
+        desc = 'pipe 1000x208x208 (radius 100), 19600 RBC x 642 vertices'
+    else:
+        raise SystemExit(f'unknown workload {name}')
+    return cfg, desc
+
+
+def default_precision(name):
+    return {'channel': 'f32', 'shear': 'f64', 'vessel': 'bf16', 'pipe': 'f32'}[name]
+
+
+def bytes_per_node(precision):
+    """Algorithmic DRAM bytes of the collide+stream kernel per fluid node:
+    19 populations read + 19 written (38 S) plus the force density read."""
+    S = {'f64': 8, 'f32': 4, 'f16': 2, 'bf16': 2}[precision]
+    rs = 8 if precision == 'f64' else 4
+    return 38 * S + 3 * rs
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    try:
+        with open(path) as f:
+            return float(json.load(f)['hbm_gbs']), 'measured'
+    except Exception:
+        return 6800.0, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while running."""
+
+    FIELDS = ['index', 'clocks.sm', 'clocks.max.sm', 'power.draw', 'clocks_event_reasons.active',
+              'clocks_event_reasons.hw_slowdown', 'clocks_event_reasons.hw_thermal_slowdown',
+              'clocks_event_reasons.sw_thermal_slowdown', 'clocks_event_reasons.sw_power_cap']
+
+    def __init__(self, device_index):
+        self.path = tempfile.mktemp(prefix='clocks_', suffix='.csv')
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, 'w')
+            self.proc = subprocess.Popen(['nvidia-smi', f'--query-gpu={",".join(self.FIELDS)}',
+                                          '--format=csv,noheader,nounits', '-lms', '50', '-i', str(self.dev)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(1.0)
+        except Exception:
+            self.proc = None
+        self.t0 = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': [], 'samples': 0}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(',')]
+                if len(p) == len(self.FIELDS):
+                    rows.append(p)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith('active')})
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
+                'reasons': reasons, 'samples': len(rows)}
+
+
+def timed_steps(sim, torch, steps, flush, phase_every=10):
+    """Run `steps` steps, each bracketed by CUDA events on the simulation's
+    stream with an L2 flush before it; returns (total ms, per-phase ms
+    averaged over the sampled steps, kernels per step)."""
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    phase_sum, nphase, kps = None, 0, 0
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(st)
+        sim.step(1)
+        evs[k][1].record(st)
+        if phase_every and (k % phase_every == phase_every - 1 or k == steps - 1):
+            ph, kps = sim.phase_times()
+            phase_sum = ph if phase_sum is None else {a: phase_sum[a] + ph[a] for a in ph}
+            nphase += 1
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in evs)
+    phases = {a: b / nphase for a, b in phase_sum.items()} if phase_sum else {}
+    return total, phases, kps
+
+
+def run_form(cfg, precision, warmup, steps, torch, flush, u_ref=None):
+    from paper_2305_02752_gb300 import hemo
+    sim = hemo.Simulation.from_config(cfg, precision)
+    sim.set_phase_timing(True)
+    sim.step(warmup)
+    sim.sync()
+    total, phases, kps = timed_steps(sim, torch, steps, flush)
+    out = sim.get_fields(hemo.HEMO_U)
+    sim.close()
+    nf = cfg.n_fluid
+    res = {'mlups': nf * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps,
+           'collide_ms': phases.get('collide'), 'phase_ms': phases}
+    u = out['u'].astype(np.float64)
+    if u_ref is not None:
+        res['u_rel_l2_vs_f64'] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
+    return res, u
+
+
+def cpu_baseline(cfg, budget_s=15.0):
+    """The CPU oracle as it stands, single thread, on a bounded number of
+    steps of the same workload."""
+    import oracle as O
+    s = O.from_config(cfg)
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(20, budget_s / max(t1, 1e-3) - 1)))
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    s.close()
+    return {'value': cfg.n_fluid * n / dt / 1e6, 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
+            'sample': f'{n} full-lattice oracle steps (after 1 untimed) of the same workload, FP64, one thread',
+            'vertices_per_s': cfg.n_vertices * n / dt}
+
+
+def e2e_job(cfg, precision, torch):
+    """The whole job through the public C ABI from pinned host buffers:
+    create the lattice (wall mask), set the initial velocity, add the cells,
+    run the configuration's steps reading the per-cell statistics back to
+    host after every step, read the final velocity field and vertices back,
+    destroy."""
+    from paper_2305_02752_gb300 import hemo
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    mask = pin(cfg.mask.astype(np.uint8)) if cfg.mask is not None else None
+    u0 = pin(cfg.init_velocity) if cfg.init_velocity is not None else None
+    meshes = [(pin(m.rest), pin(m.tri.astype(np.int32))) for m in cfg.meshes]
+    centers = pin(cfg.centers)
+    rots = pin(cfg.rotations)
+    nc = len(cfg.centers)
+    stats = pin(np.zeros((nc, 6)))
+    u_out = pin(np.zeros((cfg.nz, cfg.ny, cfg.nx, 3), np.float64 if precision == 'f64' else np.float32))
+    X_out = pin(np.zeros((cfg.n_vertices, 3)))
+    steps = cfg.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = hemo.Simulation(cfg.nx, cfg.ny, cfg.nz, cfg.tau, precision, cfg.periodic, mask, cfg.wall_velocity,
+                          cfg.body_force)
+    if u0 is not None:
+        sim.set_velocity(u0)
+    types = np.asarray(cfg.cell_type)
+    for t in range(len(cfg.meshes)):
+        idx = np.where(types == t)[0]
+        if len(idx):
+            mt = cfg.meshes[t]
+            mt2 = I.MeshType(mt.name, meshes[t][0], meshes[t][1], mt.k_link, mt.k_bend, mt.k_area, mt.k_volume,
+                             mt.kbt, mt.persistence, mt.max_strain)
+            sim.add_cells(mt2, centers[idx], rots[idx])
+    for _ in range(steps):
+        sim.step(1)
+        sim.get_fields(hemo.HEMO_CELLSTATS, out={'cellstats': stats})
+    sim.get_fields(hemo.HEMO_U | hemo.HEMO_VERTS, out={'u': u_out, 'X': X_out})
+    sim.close()
+    dt = time.perf_counter() - t0
+    h2d = mask.nbytes if mask is not None else 0
+    h2d += (u0.nbytes if u0 is not None else 0) + centers.nbytes + rots.nbytes
+    h2d += sum(a.nbytes + b.nbytes for a, b in meshes)
+    d2h = stats.nbytes * steps + u_out.nbytes + X_out.nbytes
+    return {'value': cfg.n_fluid * steps / dt / 1e6, 'unit': UNIT, 'h2d_bytes_per_step': int(h2d // steps),
+            'd2h_bytes_per_step': int(d2h // steps), 'steps': steps,
+            'note': 'whole job from pinned host inputs: create, set velocity, add cells, steps each followed by a '
+                    'per-cell statistics read-back, final field read-back, destroy'}
+
+
+def traffic_from_profile(precision, workload):
+    """DRAM bytes per collide launch from the committed ncu summary, if the
+    kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, 'profiles', f'collide_stream_{precision}_{workload}.json')
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+        src = open(os.path.join(ROOT, 'paper_2305_02752_gb300', 'csrc', 'k_lattice.cu'), 'rb').read()
+        if prof.get('source_sha256') != hashlib.sha256(src).hexdigest():
+            return None
+        return prof.get('dram_bytes_per_launch')
+    except Exception:
+        return None
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    cfg, desc = make_workload(args.workload)
+    import oracle as O
+    s = O.from_config(cfg)
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    budget = 180.0
+    w = min(args.warmup, max(0, int(budget * 0.2 / t1)))
+    k = max(1, min(args.steps, int(budget / t1)))
+    s.step(max(0, w - 1))
+    t0 = time.perf_counter()
+    s.step(k)
+    dt = time.perf_counter() - t0
+    s.close()
+    value = cfg.n_fluid * k / dt / 1e6
+    sample = (f'{k} of the requested {args.steps} timed steps (after {w} warm-up) of the full workload, '
+              'FP64 CPU oracle, one thread')
+    line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': dt / k * 1e3, 'higher_is_better': True,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': desc, 'lattice': [cfg.nx, cfg.ny, cfg.nz], 'fluid_nodes': cfg.n_fluid,
+                       'cells': len(cfg.centers), 'vertices': cfg.n_vertices, 'parallelism': 'replicas'},
+            'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': sample},
+            'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+            'vertices_per_s': cfg.n_vertices * k / dt}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=2000)
+    ap.add_argument('--warmup', type=int, default=20)
+    ap.add_argument('--impl', default='gb300', choices=['gb300', 'reference'])
+    ap.add_argument('--workload', default='channel', choices=['channel', 'shear', 'vessel', 'pipe'])
+    ap.add_argument('--precision', default=None, choices=['f64', 'f32', 'f16', 'bf16'])
+    ap.add_argument('--no-forms', action='store_true')
+    ap.add_argument('--no-cpu', action='store_true')
+    ap.add_argument('--no-e2e', action='store_true')
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    if args.impl == 'reference':
+        return reference_arm(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+    from paper_2305_02752_gb300 import hemo
+
+    precision = args.precision or default_precision(args.workload)
+    cfg, desc = make_workload(args.workload)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device='cuda')
+    sim = hemo.Simulation.from_config(cfg, precision)
+    sim.set_phase_timing(True)
+    sim.step(args.warmup)
+    sim.sync()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, phases, kps = timed_steps(sim, torch, args.steps, flush)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    sim.sync()
+    sim.close()
+    t = torch.tensor([total_ms], dtype=torch.float64, device='cuda')
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    nf, nv = cfg.n_fluid, cfg.n_vertices
+    secs = total_ms * 1e-3
+    value = world * nf * args.steps / secs / 1e6
+    peak, peak_kind = hbm_peak()
+    bpn = bytes_per_node(precision)
+    coll = phases.get('collide')
+    achieved = nf * bpn / (coll * 1e-3) / 1e9 if coll else None
+    line = {
+        'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': total_ms / args.steps, 'higher_is_better': True,
+        'scaling': 'weak', 'vs_baseline': None, 'dtype': precision, 'data': 'synthetic',
+        'config': {'workload': desc, 'lattice': [cfg.nx, cfg.ny, cfg.nz], 'fluid_nodes': nf,
+                   'cells': len(cfg.centers), 'vertices': nv, 'parallelism': 'replicas' if world > 1 else 'single',
+                   'l2': f'flushed before every timed step ({FLUSH_BYTES >> 20} MiB write)', 'seed': cfg.seed},
+        'vertices_per_s': world * nv * args.steps / secs,
+        'phase_ms': phases,
+        'roofline': {'bound': 'hbm', 'kernel': 'collide_stream', 'achieved': achieved, 'peak': peak,
+                     'unit': 'GB/s', 'frac': (achieved / peak) if achieved else None,
+                     'traffic': traffic_from_profile(precision, args.workload),
+                     'algorithmic_bytes_per_launch': nf * bpn, 'peak_kind': f'{peak_kind} HBM copy bandwidth'},
+        'gpu_launches': kps * args.steps,
+        'clocks': clk,
+    }
+    if not args.no_forms and args.workload in ('channel', 'vessel'):
+        fsteps = min(args.steps, 200)
+        forms = {}
+        r64, u64 = run_form(cfg, 'f64', args.warmup, fsteps, torch, flush)
+        forms['f64'] = r64
+        for p in ('f32', 'f16', 'bf16'):
+            forms[p], _ = run_form(cfg, p, args.warmup, fsteps, torch, flush, u_ref=u64)
+        line['forms'] = {'steps': args.warmup + fsteps, 'timed_steps': fsteps, 'results': forms}
+    if not args.no_e2e:
+        line['e2e'] = e2e_job(cfg, precision, torch)
+    if not args.no_cpu:
+        line['cpu_baseline'] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

@@ -1,0 +1,218 @@
+/*
+ * hemo.h - C ABI of the GB300 library for the coupled lattice-Boltzmann /
+ * immersed-boundary time step of cellular blood flow (HemoCell method,
+ * Zavodszky et al., "Cellular blood flow modelling with HemoCell").
+ *
+ * One simulation = a D3Q19 BGK plasma lattice (Sec. 2.2) plus triangulated
+ * cell membranes coupled to it by the immersed-boundary method (Sec. 2.3),
+ * with periodic, resting-wall and moving-wall boundaries (Sec. 2.5) and
+ * Euler vertex integration every fluid step (Sec. 2.6).  Every step runs in
+ * this library's CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Lattice units: dx = 1, dt = 1.  Lattice arrays are indexed
+ *    n = x + nx * (y + ny * z) (x fastest); vector fields are [n][3].
+ *  - Return value: HEMO_OK (0) or a negative hemo_status; the message of the
+ *    last failure on the calling thread is returned by hemo_last_error().
+ *  - Pointers documented "host" are read or written during the call only;
+ *    pointers documented "any" may be host (pageable or pinned) or device
+ *    memory of the simulation's GPU.  The library owns every buffer it
+ *    allocates and frees them in hemo_destroy().
+ *  - All work is enqueued on the simulation's CUDA stream; a call that
+ *    returns data to the caller synchronises that stream first.
+ *  - Nothing traps or aborts on the device: device-side problems set a
+ *    status word that the host reads (see hemo_step).
+ */
+#ifndef HEMO_H
+#define HEMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hemo_sim hemo_sim;
+
+enum hemo_status {
+    HEMO_OK = 0,
+    HEMO_ERR_ARG = -1,      /* invalid argument (null, size, range)           */
+    HEMO_ERR_OOM = -2,      /* device allocation failed                        */
+    HEMO_ERR_CUDA = -3,     /* a CUDA call or kernel launch failed             */
+    HEMO_ERR_NUMERIC = -4,  /* non-finite or |u| > 0.3 velocity seen on device */
+    HEMO_ERR_DOMAIN = -5,   /* a vertex left the domain across a wall axis     */
+    HEMO_ERR_STATE = -6     /* call not valid in the simulation's state        */
+};
+
+/* Storage of the populations.  F64: FP64 everything (parity path).  F32:
+ * populations stored as FP32 deviations f_i - w_i, FP32 arithmetic.
+ * F16DEV / BF16DEV: populations stored as FP16 / BF16 deviations f_i - w_i,
+ * FP32 arithmetic.  In every mode per-cell area and volume sums and cell
+ * centroids are FP64; vertex positions are the FP64 centroid plus an offset
+ * in the arithmetic precision. */
+enum hemo_precision { HEMO_F64 = 0, HEMO_F32 = 1, HEMO_F16DEV = 2, HEMO_BF16DEV = 3 };
+
+/* Device memory provider.  alloc returns a device pointer of at least
+ * `bytes` bytes (256-byte aligned) or NULL; release frees it.  When both are
+ * NULL the library uses cudaMalloc / cudaFree. */
+typedef void *(*hemo_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*hemo_free_fn)(void *ptr, void *ctx);
+
+typedef struct {
+    int nx, ny, nz;              /* lattice size, each >= 1                        */
+    double tau;                  /* BGK relaxation time (Sec. 2.2), > 0.5;
+                                    viscosity nu = (tau - 1/2) / 3                 */
+    int precision;               /* enum hemo_precision                            */
+    int periodic[3];             /* 1 = periodic along x / y / z (Sec. 2.5);
+                                    0 = nodes beyond the edge act as resting walls */
+    const uint8_t *wall_mask;    /* host, nx*ny*nz or NULL: 0 fluid, 1 resting
+                                    wall, 2 / 3 walls moving at wall_velocity[0/1]
+                                    (halfway bounce-back, Sec. 2.5 no-slip)       */
+    double wall_velocity[2][3];  /* velocities of mask ids 2 and 3                 */
+    double body_force[3];        /* constant force density g on every fluid node   */
+    void *cuda_stream;           /* cudaStream_t for all work; NULL = default     */
+    hemo_alloc_fn alloc;         /* optional device memory provider                */
+    hemo_free_fn release;
+    void *alloc_ctx;
+} hemo_lattice_desc;
+
+/* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
+ * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
+ * F_volume, Sec. 2.3; forms chosen where the paper refers elsewhere):
+ *   link   per edge  K L0 [eps^2/2 - 1/2 ln(1 - eps^2/max_strain^2)],
+ *                    K = k_link kbt / persistence, eps = (L - L0) / L0
+ *   bend   per edge  1/2 k_bend kbt (theta - theta0)^2, theta the signed
+ *                    angle between the outward normals of the edge's triangles
+ *   area   per cell  1/2 k_area ((A - A0) / A0)^2
+ *   volume per cell  1/2 k_volume ((V - V0) / V0)^2
+ * with L0, theta0, A0, V0 taken from rest_xyz. */
+typedef struct {
+    int nv, nt;                  /* vertices and triangles; closed, oriented      */
+    const int32_t *tri;          /* host, nt*3, counter-clockwise seen from outside */
+    const double *rest_xyz;      /* host, nv*3, rest shape                        */
+    double k_link, k_bend;       /* in units of kbt                               */
+    double k_area, k_volume;     /* lattice energy units                          */
+    double kbt;                  /* k_B T in lattice energy units                 */
+    double persistence;          /* spectrin persistence length p (lattice units) */
+    double max_strain;           /* link strain at which the energy diverges      */
+} hemo_mesh_desc;
+
+/* Create a simulation: allocates the lattice, sets every fluid node to rest
+ * (f_i = w_i), builds the wall links.  *out receives the handle. */
+int hemo_create_lattice(const hemo_lattice_desc *desc, hemo_sim **out);
+
+/* Set the populations of every fluid node to the equilibrium (Sec. 2.2)
+ * with rho = 1 and the given velocity.  u: any, nx*ny*nz*3 doubles, or NULL
+ * for rest.  Only valid before the first step. */
+int hemo_set_velocity(hemo_sim *sim, const double *u);
+
+/* Add `ncells` cells of a new mesh type: vertex v of cell c is placed at
+ * rot[c] * rest_xyz[v] + centers[c] (rot row-major 3x3).  centers, rot: host.
+ * *first_cell_id (may be NULL) receives the id of the first added cell;
+ * cells and vertices are numbered in the order added.  Only valid before
+ * the first step.  Fails with HEMO_ERR_ARG if the mesh is not a closed
+ * consistently oriented 2-manifold. */
+int hemo_add_cells(hemo_sim *sim, const hemo_mesh_desc *mesh, int ncells, const double *centers,
+                   const double *rot, int *first_cell_id);
+
+/* Advance `nsteps` coupled time steps, each in the order of Sec. 2.3:
+ * membrane forces at X^n, spreading onto the lattice, BGK collision with the
+ * force term and streaming, lattice velocity, interpolation to the vertices
+ * and Euler move X^{n+1} = X^n + U (Sec. 2.6).  Asynchronous on the
+ * simulation's stream.  Returns HEMO_OK or the sticky device status
+ * (HEMO_ERR_NUMERIC / HEMO_ERR_DOMAIN) of earlier steps that has already
+ * reached the host; hemo_sync() waits for it. */
+int hemo_step(hemo_sim *sim, int nsteps);
+
+/* Wait for the stream and return the device status of all steps so far. */
+int hemo_sync(hemo_sim *sim);
+
+enum hemo_field {
+    HEMO_RHO = 1,        /* density of the current populations, [n]         */
+    HEMO_U = 2,          /* velocity (post-streaming, with F/2), [n][3]     */
+    HEMO_VERTS = 4,      /* absolute vertex positions, [v][3] double        */
+    HEMO_FORCES = 8,     /* membrane forces of the last step, [v][3] double */
+    HEMO_CELLSTATS = 16  /* per cell: centroid xyz, area, volume, Taylor
+                            deformation index, [c][6] double                */
+};
+
+/* Copy fields out (bitmask of hemo_field).  rho and u are double for
+ * HEMO_F64 and float otherwise; rho is 0 and u the wall velocity at wall
+ * nodes.  All pointers: any, caller-owned; NULL skips a field.
+ * Synchronises the stream and returns the device status. */
+int hemo_get_fields(hemo_sim *sim, unsigned what, void *rho, void *u, double *verts,
+                    double *forces, double *cellstats);
+
+/* Sizes of the simulation (any pointer may be NULL). */
+int hemo_get_sizes(const hemo_sim *sim, long long *n_nodes, long long *n_vertices, int *n_cells,
+                   int *n_bins);
+
+/* ---- inspection of integer work and raw state (tests, tools) ----------- */
+
+/* The library's D3Q19 velocity order: c (host, 19*3 int), w (host, 19). */
+int hemo_velocity_set(int32_t *c, double *w);
+
+/* Populations f_i (not deviations) in the library's velocity order, in
+ * natural layout regardless of the in-place streaming parity: any,
+ * nx*ny*nz*19 doubles indexed [n][i].  Synchronises. */
+int hemo_get_populations(hemo_sim *sim, double *f);
+
+/* Per-node wall links: bits 2i..2i+1 of links[n] give, for direction i of
+ * the library's order, 0 if node + c_i is fluid, else the wall id (1 resting,
+ * 2 / 3 moving; nodes beyond a non-periodic edge count as 1); 0 at wall
+ * nodes.  links: any, nx*ny*nz uint64.  Synchronises. */
+int hemo_get_links(hemo_sim *sim, uint64_t *links);
+
+/* Edge table of mesh type `type`: ne*4 int32 (v0, v1, a, b) with triangles
+ * (v0, v1, a) and (v1, v0, b); edges numbered in order of first appearance
+ * in the triangle list (triangles in order, edges t0t1, t1t2, t2t0).
+ * edges: host, capacity 3*nt/2*4; *ne receives the count. */
+int hemo_get_edges(hemo_sim *sim, int type, int32_t *edges, int *ne);
+
+/* Replace the absolute vertex positions (any, nv*3 double).  Only valid
+ * before the first step. */
+int hemo_set_vertices(hemo_sim *sim, const double *verts);
+
+/* Bin the current vertex positions by lattice block of `block` = 8 nodes
+ * per axis: key[v] = bx + nbx * (by + nby * bz) of floor(X) (wrapped on
+ * periodic axes), perm = vertex ids sorted stably by key, start[k] = first
+ * position of block k (nbins + 1 entries).  Same kernels as the step.
+ * key, perm: any, nv int32; start: any, nbins+1 int32.  Synchronises. */
+int hemo_get_bins(hemo_sim *sim, int32_t *key, int32_t *perm, int32_t *start);
+
+/* ---- measurement ------------------------------------------------------ */
+
+/* Phases of one step, in order. */
+enum hemo_phase {
+    HEMO_PHASE_MEMBRANE = 0,  /* re-base, area/volume, membrane forces        */
+    HEMO_PHASE_BINS = 1,      /* vertex binning and gather in bin order       */
+    HEMO_PHASE_SPREAD = 2,    /* force spreading onto the lattice             */
+    HEMO_PHASE_COLLIDE = 3,   /* fused BGK collision + streaming              */
+    HEMO_PHASE_MOMENTS = 4,   /* post-streaming velocity                      */
+    HEMO_PHASE_INTERP = 5,    /* interpolation and Euler move                 */
+    HEMO_NUM_PHASES = 6
+};
+
+/* on = 1: record a CUDA event before and after every phase of every step
+ * (event-record nodes inside the step's CUDA graph, on the stream the
+ * kernels run on); on = 0: plain step.  Takes effect at the next step. */
+int hemo_set_phase_timing(hemo_sim *sim, int on);
+
+/* Device durations in milliseconds of the phases of the most recent step
+ * (ms: host, HEMO_NUM_PHASES floats; phases a step does not run report 0),
+ * and the number of kernel launches one step makes (may be NULL).
+ * Synchronises.  HEMO_ERR_STATE if timing is off or no step ran yet. */
+int hemo_get_phase_times(hemo_sim *sim, float *ms, int *kernels_per_step);
+
+/* Release every resource of the simulation (NULL is allowed). */
+void hemo_destroy(hemo_sim *sim);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *hemo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEMO_H */

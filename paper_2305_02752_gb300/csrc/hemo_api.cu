@@ -1,0 +1,762 @@
+// Host side of the C ABI declared in include/hemo.h: simulation state,
+// device allocation, mesh preprocessing (edge tables, rest geometry), the
+// per-step kernel sequence captured once per parity as a CUDA graph, status
+// handling and read-out.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hemo_internal.cuh"
+
+using namespace hemo;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define HEMO_CU(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct HostMesh {
+    int nv = 0, nt = 0, ne = 0;
+    std::vector<int> tri, edge;
+    std::vector<double> L0, th0;
+    double A0 = 0, V0 = 0;
+    double k_link = 0, k_bend = 0, k_area = 0, k_volume = 0, kbt = 0, persistence = 1, max_strain = 1;
+};
+
+// Edge table of a closed oriented triangle mesh: edges numbered by first
+// appearance (triangles in order, directed edges t0t1, t1t2, t2t0); the first
+// triangle gives (v0, v1, a), the second (necessarily traversing v1 -> v0)
+// gives b.  Returns false if the mesh is not a consistently oriented closed
+// 2-manifold.
+bool build_edge_table(int nv, const std::vector<int> &tri, std::vector<int> &edge) {
+    const int nt = (int)tri.size() / 3;
+    std::unordered_map<long long, int> id;
+    id.reserve(3 * nt);
+    edge.clear();
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3], o = tri[3 * t + (k + 2) % 3];
+            const long long key = (long long)std::min(a, b) * nv + std::max(a, b);
+            auto it = id.find(key);
+            if (it == id.end()) {
+                id.emplace(key, (int)(edge.size() / 4));
+                edge.insert(edge.end(), {a, b, o, -1});
+            } else {
+                int *e = &edge[4 * it->second];
+                if (e[0] != b || e[1] != a || e[3] != -1) return false;
+                e[3] = o;
+            }
+        }
+    for (size_t e = 0; e < edge.size() / 4; ++e)
+        if (edge[4 * e + 3] < 0) return false;
+    return true;
+}
+
+struct D3 {
+    double x, y, z;
+};
+D3 sub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+D3 crs(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+double dt3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+}  // namespace
+
+struct hemo_sim {
+    int precision = 0;
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    int per[3] = {1, 1, 1};
+    double tau = 1, g[3] = {0, 0, 0}, uw[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    cudaStream_t stream = nullptr;
+    hemo_alloc_fn alloc = nullptr;
+    hemo_free_fn release = nullptr;
+    void *ctx = nullptr;
+    std::vector<void *> allocs;
+    // lattice
+    void *f = nullptr;
+    uint8_t *ntype = nullptr;
+    uint64_t *links = nullptr;
+    void *F = nullptr, *u = nullptr;
+    // cells (host until finalised)
+    std::vector<HostMesh> meshes;
+    std::vector<int> cell_type, cell_first, vcell;
+    std::vector<double> X0;
+    int nv = 0, ncell = 0, max_nv = 0;
+    bool finalized = false;
+    long long steps_done = 0;
+    // device cells and bins
+    double *ctr = nullptr;
+    void *off = nullptr, *Fv = nullptr;
+    int *vcell_d = nullptr, *cell_first_d = nullptr, *cell_type_d = nullptr;
+    void *meshes_d = nullptr;
+    int nb[3] = {1, 1, 1}, nbins = 1;
+    int *key = nullptr, *counts = nullptr, *start = nullptr, *cursor = nullptr, *perm_raw = nullptr, *perm = nullptr;
+    int *anc_i = nullptr, *s_i = nullptr;
+    void *anc_t = nullptr, *s_t = nullptr, *s_F = nullptr;
+    // status
+    unsigned *status = nullptr;
+    unsigned *status_host = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool ev_pending = false;
+    unsigned sticky = 0;
+    // graphs
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // staging for read-out
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+    // phase timing
+    bool timing = false;
+    cudaEvent_t tev[HEMO_NUM_PHASES + 1] = {};
+    int kernels_per_step = 0;
+};
+
+namespace {
+
+void *dalloc(hemo_sim *s, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    void *p = nullptr;
+    if (s->alloc) {
+        p = s->alloc(bytes, s->ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) s->allocs.push_back(p);
+    return p;
+}
+
+void dfree(hemo_sim *s, void *p) {
+    if (!p) return;
+    auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+    if (it != s->allocs.end()) s->allocs.erase(it);
+    if (s->release) s->release(p, s->ctx);
+    else if (!s->alloc) cudaFree(p);
+}
+
+bool is_f64(const hemo_sim *s) { return s->precision == HEMO_F64; }
+size_t rsize(const hemo_sim *s) { return is_f64(s) ? 8 : 4; }
+size_t tsize(const hemo_sim *s) {
+    switch (s->precision) {
+        case HEMO_F64: return 8;
+        case HEMO_F32: return 4;
+        default: return 2;
+    }
+}
+
+int status_code(unsigned st) {
+    if (st & ST_NUMERIC) return fail(HEMO_ERR_NUMERIC, "device status: non-finite or |u| > 0.3 velocity, or a link stretched past its maximum strain");
+    if (st & ST_DOMAIN) return fail(HEMO_ERR_DOMAIN, "device status: a vertex left the lattice across a non-periodic axis");
+    return HEMO_OK;
+}
+
+int ensure_staging(hemo_sim *s, size_t bytes) {
+    if (s->staging_bytes >= bytes) return HEMO_OK;
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    dfree(s, s->staging);
+    s->staging = dalloc(s, bytes);
+    s->staging_bytes = s->staging ? bytes : 0;
+    if (!s->staging) return fail(HEMO_ERR_OOM, "staging buffer allocation failed");
+    return HEMO_OK;
+}
+
+template <typename R>
+View<R> make_view(hemo_sim *s) {
+    View<R> v{};
+    v.nx = s->nx;
+    v.ny = s->ny;
+    v.nz = s->nz;
+    v.N = s->N;
+    for (int d = 0; d < 3; ++d) v.per[d] = s->per[d];
+    v.f = s->f;
+    v.ntype = s->ntype;
+    v.links = s->links;
+    v.F = (R *)s->F;
+    v.u = (R *)s->u;
+    v.omega = R(1.0 / s->tau);
+    for (int d = 0; d < 3; ++d) {
+        v.g[d] = R(s->g[d]);
+        v.uw[0][d] = R(0);
+        v.uw[1][d] = R(0);
+        v.uw[2][d] = R(s->uw[0][d]);
+        v.uw[3][d] = R(s->uw[1][d]);
+    }
+    v.nv = s->nv;
+    v.ncell = s->ncell;
+    v.ctr = s->ctr;
+    v.off = (R *)s->off;
+    v.Fv = (R *)s->Fv;
+    v.vcell = s->vcell_d;
+    v.cell_first = s->cell_first_d;
+    v.cell_type = s->cell_type_d;
+    v.meshes = (const MeshDev<R> *)s->meshes_d;
+    v.max_nv = s->max_nv;
+    for (int d = 0; d < 3; ++d) v.nb[d] = s->nb[d];
+    v.nbins = s->nbins;
+    v.key = s->key;
+    v.counts = s->counts;
+    v.start = s->start;
+    v.cursor = s->cursor;
+    v.perm_raw = s->perm_raw;
+    v.perm = s->perm;
+    v.anc_i = s->anc_i;
+    v.anc_t = (R *)s->anc_t;
+    v.s_i = s->s_i;
+    v.s_t = (R *)s->s_t;
+    v.s_F = (R *)s->s_F;
+    v.status = s->status;
+    return v;
+}
+
+template <typename R>
+void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
+    View<R> v = make_view<R>(s);
+    auto mark = [&](int k) {
+        if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
+    };
+    mark(HEMO_PHASE_MEMBRANE);
+    if (s->ncell) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n
+    mark(HEMO_PHASE_BINS);
+    if (s->ncell) {
+        launch_bins<R>(v, st);    // anchors, stable sort by block
+        launch_gather<R>(v, st);  // anchors and forces in bin order
+    }
+    mark(HEMO_PHASE_SPREAD);
+    if (s->ncell) launch_spread<R>(v, st);  // F = g + sum F_v delta
+    mark(HEMO_PHASE_COLLIDE);
+    launch_collide<R>(v, s->precision, parity, st);  // BGK + Guo force + AA streaming
+    mark(HEMO_PHASE_MOMENTS);
+    launch_moments<R>(v, s->precision, parity, st);  // post-streaming u (with F/2)
+    mark(HEMO_PHASE_INTERP);
+    if (s->ncell) launch_interpolate<R>(v, st);  // X^{n+1} = X^n + I[u](X^n)
+    mark(HEMO_NUM_PHASES);
+}
+
+template <typename R>
+int finalize_impl(hemo_sim *s) {
+    const size_t rs = sizeof(R);
+    const int nv = s->nv, nc = s->ncell;
+    s->ctr = (double *)dalloc(s, sizeof(double) * 3 * std::max(nc, 1));
+    s->off = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->Fv = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->vcell_d = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
+    s->cell_first_d = (int *)dalloc(s, sizeof(int) * std::max(nc, 1));
+    s->cell_type_d = (int *)dalloc(s, sizeof(int) * std::max(nc, 1));
+    s->meshes_d = dalloc(s, sizeof(MeshDev<R>) * MAX_TYPES);
+    s->key = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
+    s->perm_raw = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
+    s->perm = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
+    s->anc_i = (int *)dalloc(s, sizeof(int) * 3 * std::max(nv, 1));
+    s->s_i = (int *)dalloc(s, sizeof(int) * 3 * std::max(nv, 1));
+    s->anc_t = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->s_t = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->s_F = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->counts = (int *)dalloc(s, sizeof(int) * s->nbins);
+    s->cursor = (int *)dalloc(s, sizeof(int) * s->nbins);
+    s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
+    if (!s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
+        !s->key || !s->perm_raw || !s->perm || !s->anc_i || !s->s_i || !s->anc_t || !s->s_t || !s->s_F ||
+        !s->counts || !s->cursor || !s->start)
+        return fail(HEMO_ERR_OOM, "device allocation of cell and bin buffers failed");
+    cudaStream_t st = s->stream;
+    HEMO_CU(cudaMemsetAsync(s->start, 0, sizeof(int) * (s->nbins + 1), st));
+    HEMO_CU(cudaMemsetAsync(s->Fv, 0, rs * 3 * std::max(nv, 1), st));
+
+    // mesh tables
+    std::vector<MeshDev<R>> md(MAX_TYPES);
+    for (size_t t = 0; t < s->meshes.size(); ++t) {
+        const HostMesh &m = s->meshes[t];
+        int *dtri = (int *)dalloc(s, sizeof(int) * m.tri.size());
+        int *dedge = (int *)dalloc(s, sizeof(int) * m.edge.size());
+        R *dL0 = (R *)dalloc(s, rs * m.ne);
+        R *dth0 = (R *)dalloc(s, rs * m.ne);
+        if (!dtri || !dedge || !dL0 || !dth0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        std::vector<R> L0(m.L0.begin(), m.L0.end()), th0(m.th0.begin(), m.th0.end());
+        HEMO_CU(cudaMemcpy(dtri, m.tri.data(), sizeof(int) * m.tri.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dedge, m.edge.data(), sizeof(int) * m.edge.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dL0, L0.data(), rs * m.ne, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dth0, th0.data(), rs * m.ne, cudaMemcpyHostToDevice));
+        MeshDev<R> d{};
+        d.nv = m.nv;
+        d.nt = m.nt;
+        d.ne = m.ne;
+        d.tri = dtri;
+        d.edge = dedge;
+        d.L0 = dL0;
+        d.th0 = dth0;
+        d.A0 = m.A0;
+        d.V0 = m.V0;
+        d.K = R(m.k_link * m.kbt / m.persistence);
+        d.m2 = R(m.max_strain * m.max_strain);
+        d.kb = R(m.k_bend * m.kbt);
+        d.k_area = m.k_area;
+        d.k_volume = m.k_volume;
+        md[t] = d;
+    }
+    HEMO_CU(cudaMemcpy(s->meshes_d, md.data(), sizeof(MeshDev<R>) * MAX_TYPES, cudaMemcpyHostToDevice));
+
+    // cells: FP64 centroid (vertex mean) and offsets in R
+    if (nc) {
+        std::vector<double> ctr(3 * nc, 0.0);
+        std::vector<R> off(3 * (size_t)nv);
+        for (int c = 0; c < nc; ++c) {
+            const int n = s->meshes[s->cell_type[c]].nv, o = s->cell_first[c];
+            for (int i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d) ctr[3 * c + d] += s->X0[3 * (size_t)(o + i) + d];
+            for (int d = 0; d < 3; ++d) ctr[3 * c + d] /= n;
+            for (int i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d)
+                    off[3 * (size_t)(o + i) + d] = R(s->X0[3 * (size_t)(o + i) + d] - ctr[3 * c + d]);
+        }
+        HEMO_CU(cudaMemcpy(s->ctr, ctr.data(), sizeof(double) * 3 * nc, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(s->off, off.data(), rs * 3 * (size_t)nv, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(s->vcell_d, s->vcell.data(), sizeof(int) * nv, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(s->cell_first_d, s->cell_first.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(s->cell_type_d, s->cell_type.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+    }
+    const size_t smem = cell_smem_bytes<R>(s->max_nv);
+    if (smem > 48 * 1024) HEMO_CU(set_cell_smem_limit<R>(smem));
+    if (!nc) {  // no cells: the force field is the body force, written once
+        View<R> v = make_view<R>(s);
+        launch_spread<R>(v, st);
+    }
+    HEMO_CU(cudaGetLastError());
+    s->finalized = true;
+    return HEMO_OK;
+}
+
+int ensure_ready(hemo_sim *s) {
+    if (s->finalized) return HEMO_OK;
+    return is_f64(s) ? finalize_impl<double>(s) : finalize_impl<float>(s);
+}
+
+template <typename R>
+int capture_graphs(hemo_sim *s) {
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        HEMO_CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_step<R>(s, p, s->cap);
+        cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+        if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int kernels = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+        }
+        s->kernels_per_step = kernels;
+        e = cudaGraphInstantiate(&s->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return HEMO_OK;
+}
+
+int poll_status(hemo_sim *s) {
+    if (s->ev_pending && cudaEventQuery(s->ev) == cudaSuccess) {
+        s->sticky |= *s->status_host;
+        s->ev_pending = false;
+    }
+    cudaGetLastError();
+    return status_code(s->sticky);
+}
+
+double dihedral(D3 p0, D3 p1, D3 pa, D3 pb) {
+    const D3 e = sub(p1, p0);
+    const D3 n1 = crs(e, sub(pa, p0)), n2 = crs(sub(pb, p0), e);
+    return std::atan2(dt3(crs(n1, n2), e) / std::sqrt(dt3(e, e)), dt3(n1, n2));
+}
+
+int copy_out(hemo_sim *s, void *dst, const void *src, size_t bytes) {
+    if (!dst || !bytes) return HEMO_OK;
+    HEMO_CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s->stream));
+    return HEMO_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *hemo_last_error(void) { return g_err.c_str(); }
+
+int hemo_velocity_set(int32_t *c, double *w) {
+    if (!c || !w) return fail(HEMO_ERR_ARG, "hemo_velocity_set: null pointer");
+    for (int i = 0; i < Q; ++i) {
+        c[3 * i] = cx(i);
+        c[3 * i + 1] = cy(i);
+        c[3 * i + 2] = cz(i);
+        w[i] = wgt(i);
+    }
+    return HEMO_OK;
+}
+
+int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
+    if (!d || !out) return fail(HEMO_ERR_ARG, "hemo_create_lattice: null pointer");
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(HEMO_ERR_ARG, "lattice sizes must be >= 1");
+    const long long N = (long long)d->nx * d->ny * d->nz;
+    if (N > 0x7fffffffLL / 2) return fail(HEMO_ERR_ARG, "lattice too large (more than 2^30 nodes)");
+    if (!(d->tau > 0.5)) return fail(HEMO_ERR_ARG, "tau must exceed 1/2");
+    if (d->precision < HEMO_F64 || d->precision > HEMO_BF16DEV) return fail(HEMO_ERR_ARG, "unknown precision");
+    for (int k = 0; k < 3; ++k)
+        if (d->periodic[k] != 0 && d->periodic[k] != 1) return fail(HEMO_ERR_ARG, "periodic flags must be 0 or 1");
+    if ((d->alloc == nullptr) != (d->release == nullptr)) return fail(HEMO_ERR_ARG, "alloc and release must be given together");
+    if (d->wall_mask)
+        for (long long n = 0; n < N; ++n)
+            if (d->wall_mask[n] > 3) return fail(HEMO_ERR_ARG, "wall mask values must be 0..3");
+
+    hemo_sim *s = new hemo_sim();
+    s->precision = d->precision;
+    s->nx = d->nx;
+    s->ny = d->ny;
+    s->nz = d->nz;
+    s->N = N;
+    for (int k = 0; k < 3; ++k) {
+        s->per[k] = d->periodic[k];
+        s->g[k] = d->body_force[k];
+        s->uw[0][k] = d->wall_velocity[0][k];
+        s->uw[1][k] = d->wall_velocity[1][k];
+    }
+    s->tau = d->tau;
+    s->stream = (cudaStream_t)d->cuda_stream;
+    s->alloc = d->alloc;
+    s->release = d->release;
+    s->ctx = d->alloc_ctx;
+    s->nb[0] = (s->nx + BLK - 1) / BLK;
+    s->nb[1] = (s->ny + BLK - 1) / BLK;
+    s->nb[2] = (s->nz + BLK - 1) / BLK;
+    s->nbins = s->nb[0] * s->nb[1] * s->nb[2];
+
+    auto bail = [&](int code) {
+        hemo_destroy(s);
+        return code;
+    };
+    s->f = dalloc(s, tsize(s) * Q * (size_t)N);
+    s->ntype = (uint8_t *)dalloc(s, (size_t)N);
+    s->links = (uint64_t *)dalloc(s, 8 * (size_t)N);
+    s->F = dalloc(s, rsize(s) * 3 * (size_t)N);
+    s->u = dalloc(s, rsize(s) * 3 * (size_t)N);
+    s->status = (unsigned *)dalloc(s, sizeof(unsigned));
+    if (!s->f || !s->ntype || !s->links || !s->F || !s->u || !s->status)
+        return bail(fail(HEMO_ERR_OOM, "device allocation of the lattice failed"));
+    if (cudaHostAlloc((void **)&s->status_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(HEMO_ERR_CUDA, std::string("stream/event setup: ") + cudaGetErrorString(cudaGetLastError())));
+    *s->status_host = 0;
+    cudaStream_t st = s->stream;
+    if (cudaMemsetAsync(s->status, 0, sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(s->F, 0, rsize(s) * 3 * (size_t)N, st) != cudaSuccess)
+        return bail(fail(HEMO_ERR_CUDA, "memset failed"));
+    cudaError_t e = d->wall_mask ? cudaMemcpyAsync(s->ntype, d->wall_mask, (size_t)N, cudaMemcpyHostToDevice, st)
+                                 : cudaMemsetAsync(s->ntype, 0, (size_t)N, st);
+    if (e != cudaSuccess) return bail(fail(HEMO_ERR_CUDA, std::string("wall mask upload: ") + cudaGetErrorString(e)));
+    launch_build_links(s->nx, s->ny, s->nz, s->per, s->ntype, s->links, st);
+    if (is_f64(s)) launch_init_equilibrium<double>(make_view<double>(s), s->precision, nullptr, st);
+    else launch_init_equilibrium<float>(make_view<float>(s), s->precision, nullptr, st);
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(fail(HEMO_ERR_CUDA, std::string("lattice setup: ") + cudaGetErrorString(e)));
+    *out = s;
+    return HEMO_OK;
+}
+
+int hemo_set_velocity(hemo_sim *s, const double *u) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (s->steps_done) return fail(HEMO_ERR_STATE, "hemo_set_velocity: only before the first step");
+    const double *ud = nullptr;
+    if (u) {
+        int rc = ensure_staging(s, sizeof(double) * 3 * (size_t)s->N);
+        if (rc) return rc;
+        HEMO_CU(cudaMemcpyAsync(s->staging, u, sizeof(double) * 3 * (size_t)s->N, cudaMemcpyDefault, s->stream));
+        ud = (const double *)s->staging;
+    }
+    if (is_f64(s)) launch_init_equilibrium<double>(make_view<double>(s), s->precision, ud, s->stream);
+    else launch_init_equilibrium<float>(make_view<float>(s), s->precision, ud, s->stream);
+    HEMO_CU(cudaGetLastError());
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    return HEMO_OK;
+}
+
+int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const double *centers, const double *rot,
+                   int *first_cell_id) {
+    if (!s || !m) return fail(HEMO_ERR_ARG, "hemo_add_cells: null pointer");
+    if (s->finalized || s->steps_done) return fail(HEMO_ERR_STATE, "hemo_add_cells: only before the first step");
+    if (s->meshes.size() >= (size_t)MAX_TYPES) return fail(HEMO_ERR_ARG, "too many mesh types");
+    if (m->nv < 4 || m->nt < 4 || !m->tri || !m->rest_xyz) return fail(HEMO_ERR_ARG, "mesh needs >= 4 vertices and triangles");
+    if (ncells < 0 || (ncells > 0 && (!centers || !rot))) return fail(HEMO_ERR_ARG, "bad cell placement arguments");
+    if ((long long)s->nv + (long long)ncells * m->nv > 0x3fffffffLL) return fail(HEMO_ERR_ARG, "too many vertices");
+    if (!(m->persistence > 0) || !(m->max_strain > 0) || !(m->kbt >= 0)) return fail(HEMO_ERR_ARG, "bad membrane parameters");
+    HostMesh hm;
+    hm.nv = m->nv;
+    hm.nt = m->nt;
+    hm.tri.assign(m->tri, m->tri + 3 * (size_t)m->nt);
+    for (int x : hm.tri)
+        if (x < 0 || x >= m->nv) return fail(HEMO_ERR_ARG, "triangle index out of range");
+    if (!build_edge_table(m->nv, hm.tri, hm.edge))
+        return fail(HEMO_ERR_ARG, "mesh is not a closed, consistently oriented 2-manifold");
+    hm.ne = (int)hm.edge.size() / 4;
+    const double *r = m->rest_xyz;
+    auto P = [&](int i) { return D3{r[3 * i], r[3 * i + 1], r[3 * i + 2]}; };
+    hm.L0.resize(hm.ne);
+    hm.th0.resize(hm.ne);
+    for (int e = 0; e < hm.ne; ++e) {
+        const int *E = &hm.edge[4 * e];
+        const D3 d = sub(P(E[1]), P(E[0]));
+        hm.L0[e] = std::sqrt(dt3(d, d));
+        hm.th0[e] = dihedral(P(E[0]), P(E[1]), P(E[2]), P(E[3]));
+        if (!(hm.L0[e] > 0)) return fail(HEMO_ERR_ARG, "zero-length rest edge");
+    }
+    D3 c{0, 0, 0};
+    for (int i = 0; i < hm.nv; ++i) {
+        c.x += r[3 * i];
+        c.y += r[3 * i + 1];
+        c.z += r[3 * i + 2];
+    }
+    c = {c.x / hm.nv, c.y / hm.nv, c.z / hm.nv};
+    double A = 0, V = 0;
+    for (int t = 0; t < hm.nt; ++t) {
+        const D3 p0 = P(hm.tri[3 * t]), p1 = P(hm.tri[3 * t + 1]), p2 = P(hm.tri[3 * t + 2]);
+        const D3 n = crs(sub(p1, p0), sub(p2, p0));
+        A += 0.5 * std::sqrt(dt3(n, n));
+        V += dt3(sub(p0, c), crs(sub(p1, c), sub(p2, c))) / 6.0;
+    }
+    hm.A0 = A;
+    hm.V0 = V;
+    if (!(A > 0) || !(V > 0)) return fail(HEMO_ERR_ARG, "rest shape has non-positive area or volume (check orientation)");
+    hm.k_link = m->k_link;
+    hm.k_bend = m->k_bend;
+    hm.k_area = m->k_area;
+    hm.k_volume = m->k_volume;
+    hm.kbt = m->kbt;
+    hm.persistence = m->persistence;
+    hm.max_strain = m->max_strain;
+    const int type = (int)s->meshes.size();
+    s->meshes.push_back(hm);
+    s->max_nv = std::max(s->max_nv, hm.nv);
+    if (first_cell_id) *first_cell_id = s->ncell;
+    for (int k = 0; k < ncells; ++k) {
+        const double *R = rot + 9 * (size_t)k;
+        const double *C = centers + 3 * (size_t)k;
+        s->cell_type.push_back(type);
+        s->cell_first.push_back(s->nv);
+        for (int i = 0; i < hm.nv; ++i) {
+            for (int d = 0; d < 3; ++d)
+                s->X0.push_back(C[d] + R[3 * d] * r[3 * i] + R[3 * d + 1] * r[3 * i + 1] + R[3 * d + 2] * r[3 * i + 2]);
+            s->vcell.push_back(s->ncell);
+        }
+        s->nv += hm.nv;
+        s->ncell += 1;
+    }
+    return HEMO_OK;
+}
+
+int hemo_step(hemo_sim *s, int nsteps) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (nsteps < 0) return fail(HEMO_ERR_ARG, "nsteps must be >= 0");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    rc = poll_status(s);
+    if (rc) return rc;
+    if (nsteps == 0) return HEMO_OK;
+    if (!s->graph[0]) {
+        rc = is_f64(s) ? capture_graphs<double>(s) : capture_graphs<float>(s);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        HEMO_CU(cudaGraphLaunch(s->graph[s->steps_done & 1], s->stream));
+        ++s->steps_done;
+    }
+    HEMO_CU(cudaMemcpyAsync(s->status_host, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    HEMO_CU(cudaEventRecord(s->ev, s->stream));
+    s->ev_pending = true;
+    return HEMO_OK;
+}
+
+int hemo_sync(hemo_sim *s) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    unsigned st = 0;
+    HEMO_CU(cudaMemcpy(&st, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    s->sticky |= st;
+    s->ev_pending = false;
+    return status_code(s->sticky);
+}
+
+int hemo_get_sizes(const hemo_sim *s, long long *n_nodes, long long *n_vertices, int *n_cells, int *n_bins) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (n_nodes) *n_nodes = s->N;
+    if (n_vertices) *n_vertices = s->nv;
+    if (n_cells) *n_cells = s->ncell;
+    if (n_bins) *n_bins = s->nbins;
+    return HEMO_OK;
+}
+
+int hemo_get_fields(hemo_sim *s, unsigned what, void *rho, void *u, double *verts, double *forces,
+                    double *cellstats) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    const size_t N = (size_t)s->N, rs = rsize(s);
+    const int layout = (int)(s->steps_done & 1);
+    size_t need = std::max<size_t>({rs * 3 * N, sizeof(double) * 6 * (size_t)std::max(s->nv, 1),
+                                    sizeof(double) * 6 * (size_t)std::max(s->ncell, 1)});
+    rc = ensure_staging(s, need);
+    if (rc) return rc;
+    cudaStream_t st = s->stream;
+    if ((what & HEMO_RHO) && rho) {
+        if (is_f64(s)) launch_rho_out<double>(make_view<double>(s), s->precision, layout, (double *)s->staging, st);
+        else launch_rho_out<float>(make_view<float>(s), s->precision, layout, (float *)s->staging, st);
+        if ((rc = copy_out(s, rho, s->staging, rs * N))) return rc;
+    }
+    if ((what & HEMO_U) && u) {
+        if (is_f64(s)) launch_u_out<double>(make_view<double>(s), (double *)s->staging, st);
+        else launch_u_out<float>(make_view<float>(s), (float *)s->staging, st);
+        if ((rc = copy_out(s, u, s->staging, rs * 3 * N))) return rc;
+    }
+    if (((what & HEMO_VERTS) && verts) || ((what & HEMO_FORCES) && forces)) {
+        double *X = (double *)s->staging, *Fo = X + 3 * (size_t)s->nv;
+        if (is_f64(s)) launch_verts_out<double>(make_view<double>(s), X, Fo, st);
+        else launch_verts_out<float>(make_view<float>(s), X, Fo, st);
+        if ((what & HEMO_VERTS) && (rc = copy_out(s, verts, X, sizeof(double) * 3 * s->nv))) return rc;
+        if ((what & HEMO_FORCES) && (rc = copy_out(s, forces, Fo, sizeof(double) * 3 * s->nv))) return rc;
+    }
+    if ((what & HEMO_CELLSTATS) && cellstats && s->ncell) {
+        if (is_f64(s)) launch_cell_forces<double>(make_view<double>(s), 1, (double *)s->staging, st);
+        else launch_cell_forces<float>(make_view<float>(s), 1, (double *)s->staging, st);
+        if ((rc = copy_out(s, cellstats, s->staging, sizeof(double) * 6 * s->ncell))) return rc;
+    }
+    HEMO_CU(cudaGetLastError());
+    return hemo_sync(s);
+}
+
+int hemo_get_populations(hemo_sim *s, double *f) {
+    if (!s || !f) return fail(HEMO_ERR_ARG, "null pointer");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    rc = ensure_staging(s, sizeof(double) * Q * (size_t)s->N);
+    if (rc) return rc;
+    const int layout = (int)(s->steps_done & 1);
+    if (is_f64(s)) launch_populations_out<double>(make_view<double>(s), s->precision, layout, (double *)s->staging, s->stream);
+    else launch_populations_out<float>(make_view<float>(s), s->precision, layout, (double *)s->staging, s->stream);
+    HEMO_CU(cudaGetLastError());
+    if ((rc = copy_out(s, f, s->staging, sizeof(double) * Q * (size_t)s->N))) return rc;
+    return hemo_sync(s);
+}
+
+int hemo_get_links(hemo_sim *s, uint64_t *links) {
+    if (!s || !links) return fail(HEMO_ERR_ARG, "null pointer");
+    int rc = copy_out(s, links, s->links, 8 * (size_t)s->N);
+    if (rc) return rc;
+    return hemo_sync(s);
+}
+
+int hemo_get_edges(hemo_sim *s, int type, int32_t *edges, int *ne) {
+    if (!s || !edges || !ne) return fail(HEMO_ERR_ARG, "null pointer");
+    if (type < 0 || type >= (int)s->meshes.size()) return fail(HEMO_ERR_ARG, "no such mesh type");
+    const HostMesh &m = s->meshes[type];
+    std::memcpy(edges, m.edge.data(), sizeof(int) * m.edge.size());
+    *ne = m.ne;
+    return HEMO_OK;
+}
+
+int hemo_set_vertices(hemo_sim *s, const double *verts) {
+    if (!s || !verts) return fail(HEMO_ERR_ARG, "null pointer");
+    if (s->steps_done) return fail(HEMO_ERR_STATE, "hemo_set_vertices: only before the first step");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (!s->nv) return HEMO_OK;
+    std::vector<double> X(3 * (size_t)s->nv);
+    HEMO_CU(cudaMemcpy(X.data(), verts, sizeof(double) * X.size(), cudaMemcpyDefault));
+    std::vector<double> ctr(3 * s->ncell, 0.0);
+    for (int c = 0; c < s->ncell; ++c) {
+        const int n = s->meshes[s->cell_type[c]].nv, o = s->cell_first[c];
+        for (int i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) ctr[3 * c + d] += X[3 * (size_t)(o + i) + d];
+        for (int d = 0; d < 3; ++d) ctr[3 * c + d] /= n;
+    }
+    rc = ensure_staging(s, sizeof(double) * X.size());
+    if (rc) return rc;
+    HEMO_CU(cudaMemcpy(s->ctr, ctr.data(), sizeof(double) * ctr.size(), cudaMemcpyHostToDevice));
+    HEMO_CU(cudaMemcpy(s->staging, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice));
+    if (is_f64(s)) launch_set_vertices<double>(make_view<double>(s), (const double *)s->staging, s->stream);
+    else launch_set_vertices<float>(make_view<float>(s), (const double *)s->staging, s->stream);
+    HEMO_CU(cudaGetLastError());
+    return hemo_sync(s);
+}
+
+int hemo_get_bins(hemo_sim *s, int32_t *key, int32_t *perm, int32_t *start) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->nv) {
+        if (is_f64(s)) launch_bins<double>(make_view<double>(s), s->stream);
+        else launch_bins<float>(make_view<float>(s), s->stream);
+        HEMO_CU(cudaGetLastError());
+    }
+    if ((rc = copy_out(s, key, s->key, sizeof(int) * s->nv))) return rc;
+    if ((rc = copy_out(s, perm, s->perm, sizeof(int) * s->nv))) return rc;
+    if ((rc = copy_out(s, start, s->start, sizeof(int) * (s->nbins + 1)))) return rc;
+    return hemo_sync(s);
+}
+
+int hemo_set_phase_timing(hemo_sim *s, int on) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if ((bool)on == s->timing) return HEMO_OK;
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    if (on && !s->tev[0])
+        for (int k = 0; k <= HEMO_NUM_PHASES; ++k) HEMO_CU(cudaEventCreate(&s->tev[k]));
+    for (int p = 0; p < 2; ++p)
+        if (s->graph[p]) {
+            cudaGraphExecDestroy(s->graph[p]);
+            s->graph[p] = nullptr;
+        }
+    s->timing = on != 0;
+    return HEMO_OK;
+}
+
+int hemo_get_phase_times(hemo_sim *s, float *ms, int *kernels_per_step) {
+    if (!s || !ms) return fail(HEMO_ERR_ARG, "null pointer");
+    if (!s->timing || !s->steps_done || !s->graph[0]) return fail(HEMO_ERR_STATE, "phase timing is off or no timed step ran");
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < HEMO_NUM_PHASES; ++k) HEMO_CU(cudaEventElapsedTime(ms + k, s->tev[k], s->tev[k + 1]));
+    if (kernels_per_step) *kernels_per_step = s->kernels_per_step;
+    return HEMO_OK;
+}
+
+void hemo_destroy(hemo_sim *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (int k = 0; k <= HEMO_NUM_PHASES; ++k)
+        if (s->tev[k]) cudaEventDestroy(s->tev[k]);
+    for (int p = 0; p < 2; ++p)
+        if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
+    if (s->ev) cudaEventDestroy(s->ev);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->status_host) cudaFreeHost(s->status_host);
+    std::vector<void *> all = s->allocs;
+    for (void *p : all) dfree(s, p);
+    cudaGetLastError();
+    delete s;
+}
+
+}  // extern "C"

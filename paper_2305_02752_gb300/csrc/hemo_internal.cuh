@@ -1,0 +1,144 @@
+// Internal definitions shared by the CUDA translation units of libhemo.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hemo.h"
+
+namespace hemo {
+
+constexpr int Q = 19;
+constexpr int BLK = 8;              // lattice block edge used for vertex bins
+constexpr int MAX_TYPES = 8;        // membrane mesh types per simulation
+
+// status bits raised on the device
+constexpr unsigned ST_NUMERIC = 1u;
+constexpr unsigned ST_DOMAIN = 2u;
+constexpr float U_LIMIT2 = 0.09f;   // |u|^2 above which the step is unstable
+
+// ---------------------------------------------------------------------------
+// D3Q19 in the library's order: 0 rest; 1..6 = +x -x +y -y +z -z; 7..18 =
+// diagonal pairs, each odd index followed by its opposite.  Weights 1/3,
+// 1/18 (axis), 1/36 (diagonal); c_s^2 = 1/3 (Sec. 2.2).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) {
+    constexpr int v[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return v[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+    constexpr int v[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+    constexpr int v[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return v[i];
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// ---------------------------------------------------------------------------
+// population storage: deviations d_i = f_i - w_i in T, arithmetic in R
+// ---------------------------------------------------------------------------
+template <typename T> struct Store;
+template <> struct Store<double> {
+    static __device__ __forceinline__ double ld(double v) { return v; }
+    static __device__ __forceinline__ double st(double v) { return v; }
+};
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(float v) { return v; }
+    static __device__ __forceinline__ float st(float v) { return v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half st(float v) { return __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// device views (plain pointers, passed by value to kernels)
+// ---------------------------------------------------------------------------
+template <typename R> struct MeshDev {
+    int nv, nt, ne;
+    const int *tri;     // nt*3
+    const int *edge;    // ne*4: v0, v1, a, b
+    const R *L0;        // ne
+    const R *th0;       // ne
+    double A0, V0;
+    R K;                // k_link * kbt / persistence
+    R m2;               // max_strain^2
+    R kb;               // k_bend * kbt
+    double k_area, k_volume;
+};
+
+template <typename R> struct View {
+    // lattice
+    int nx, ny, nz;
+    long long N;
+    int per[3];
+    void *f;                   // 19*N deviations, storage type by precision
+    const uint8_t *ntype;      // N: 0 fluid, 1..3 wall id, 0x80 = fluid next to a wall
+    const uint64_t *links;     // N: 2 bits per direction (wall id of node + c_i)
+    R *F;                      // [3][N] force density
+    R *u;                      // [3][N] velocity
+    R omega;
+    R g[3];
+    R uw[4][3];                // wall velocity by id
+    // cells and vertices
+    int nv, ncell;
+    double *ctr;               // ncell*3 centroids (FP64)
+    R *off;                    // nv*3 offsets from the centroid
+    R *Fv;                     // nv*3 membrane forces
+    const int *vcell;          // nv: cell of each vertex
+    const int *cell_first;     // ncell
+    const int *cell_type;      // ncell
+    const MeshDev<R> *meshes;  // per type
+    int max_nv;                // largest vertex count of a mesh type
+    // bins
+    int nb[3];
+    int nbins;
+    int *key;                  // nv
+    int *counts;               // nbins
+    int *start;                // nbins + 1
+    int *cursor;               // nbins
+    int *perm_raw;             // nv, unsorted within bins
+    int *perm;                 // nv, stable (key, vertex id)
+    int *anc_i;                // nv*3 stencil base floor(X) (wrapped on periodic axes)
+    R *anc_t;                  // nv*3 fractions X - floor(X)
+    int *s_i;                  // nv*3 anchors in bin order
+    R *s_t;                    // nv*3
+    R *s_F;                    // nv*3 forces in bin order
+    unsigned *status;
+};
+
+// launchers (R = double for HEMO_F64, float otherwise)
+template <typename R> void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st);
+template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);
+template <typename R> void launch_init_equilibrium(const View<R> &v, int precision, const double *u_dev, cudaStream_t st);
+template <typename R> void launch_populations_out(const View<R> &v, int precision, int parity, double *out, cudaStream_t st);
+template <typename R> void launch_rho_out(const View<R> &v, int precision, int parity, R *out, cudaStream_t st);
+template <typename R> void launch_u_out(const View<R> &v, R *out, cudaStream_t st);
+void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, uint64_t *links, cudaStream_t st);
+
+template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
+template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
+template <typename R> size_t cell_smem_bytes(int max_nv) { return 6 * (size_t)max_nv * sizeof(R); }
+template <typename R> void launch_bins(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_gather(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_spread(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st);
+template <typename R> void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st);
+
+// periodic wrap of a lattice coordinate
+__host__ __device__ __forceinline__ int wrap(int j, int n) {
+    int r = j % n;
+    return r < 0 ? r + n : r;
+}
+
+}  // namespace hemo

@@ -1,0 +1,222 @@
+// Membrane mechanics, one CTA per cell (Sec. 2.3: F_total = F_link + F_bend
+// + F_area + F_volume; vertices are Lagrangian points of a triangulated
+// membrane).
+//
+// A CTA stages its cell's vertex offsets in shared memory, re-bases the cell
+// (centroid += mean offset, offsets -= mean, so the FP32 offsets stay small
+// while the FP64 centroid carries the position), sums area and volume over
+// the triangles in FP64, and accumulates the four force terms per vertex in
+// shared memory before one coalesced write.  Energies (forms documented in
+// hemo.h):
+//   link   K L0 [eps^2/2 - 1/2 ln(1 - eps^2/m^2)],   eps = (L - L0)/L0
+//   bend   1/2 kb (theta - theta0)^2, theta = signed angle between the
+//          outward normals of the two triangles of an edge
+//   area   1/2 k_area ((A - A0)/A0)^2,  volume 1/2 k_volume ((V - V0)/V0)^2
+// Forces are minus the energy gradients; the dihedral-angle gradient is the
+// standard one (Bridson et al. 2003): the wing vertices move along their
+// triangle normals with weight |e| / |n|^2, the edge vertices carry the
+// lever-rule remainder.
+#include "hemo_internal.cuh"
+
+namespace hemo {
+
+namespace {
+
+template <typename R> struct V3 {
+    R x, y, z;
+};
+template <typename R> __device__ __forceinline__ V3<R> ld3(const R *p) { return {p[0], p[1], p[2]}; }
+template <typename R> __device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ void sub_into(R *f, V3<R> a) {
+    atomicAdd(f, -a.x);
+    atomicAdd(f + 1, -a.y);
+    atomicAdd(f + 2, -a.z);
+}
+
+__device__ __forceinline__ float sqrt_r(float a) { return sqrtf(a); }
+__device__ __forceinline__ double sqrt_r(double a) { return sqrt(a); }
+__device__ __forceinline__ float atan2_r(float a, float b) { return atan2f(a, b); }
+__device__ __forceinline__ double atan2_r(double a, double b) { return atan2(a, b); }
+__device__ __forceinline__ float log_r(float a) { return logf(a); }
+__device__ __forceinline__ double log_r(double a) { return log(a); }
+
+// block-wide sum of K doubles; every thread receives the totals
+template <int K>
+__device__ void block_sum(double (&val)[K], double (*scratch)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_down_sync(0xffffffffu, val[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) scratch[k][wid] = val[k];
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        double s = 0;
+        for (int w = 0; w < nw; ++w) s += scratch[k][w];
+        val[k] = s;
+    }
+    __syncthreads();
+}
+
+// eigenvalues of a symmetric 3x3 matrix, closed form (Smith 1961)
+__device__ void sym3_eig(double a00, double a11, double a22, double a01, double a02, double a12, double &lmax,
+                         double &lmin) {
+    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    const double q = (a00 + a11 + a22) / 3.0;
+    const double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + 2.0 * p1;
+    if (p2 <= 0.0) {
+        lmax = lmin = q;
+        return;
+    }
+    const double p = sqrt(p2 / 6.0);
+    const double b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
+    const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+    double r = 0.5 * (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02));
+    r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+    const double phi = acos(r) / 3.0;
+    lmax = q + 2.0 * p * cos(phi);
+    lmin = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+}
+
+// mode 0: re-base + forces (step); mode 1: statistics only (no writes to
+// the state): stats[6c..] = centroid, area, volume, deformation index.
+template <typename R>
+__global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *stats) {
+    const int c = blockIdx.x;
+    const MeshDev<R> m = v.meshes[v.cell_type[c]];
+    const int first = v.cell_first[c];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *xs = reinterpret_cast<R *>(smem_raw);  // nv*3 positions relative to the centroid
+    R *fs = xs + 3 * m.nv;                      // nv*3 force accumulators
+    __shared__ double scratch[6][32];
+
+    // mean offset (FP64)
+    double mean[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        const R *o = v.off + 3 * (size_t)(first + i);
+        mean[0] += (double)o[0];
+        mean[1] += (double)o[1];
+        mean[2] += (double)o[2];
+    }
+    block_sum<3>(mean, scratch);
+    for (int k = 0; k < 3; ++k) mean[k] /= m.nv;
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        R *o = v.off + 3 * (size_t)(first + i);
+        for (int k = 0; k < 3; ++k) {
+            const R r = R((double)o[k] - mean[k]);
+            xs[3 * i + k] = r;
+            fs[3 * i + k] = R(0);
+            if (mode == 0) o[k] = r;
+        }
+    }
+    if (mode == 0 && threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) v.ctr[3 * c + k] += mean[k];
+    __syncthreads();
+
+    // area and volume: per-triangle terms in R, sums in FP64
+    double av[2] = {0, 0};
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const V3<R> p0 = ld3(xs + 3 * m.tri[3 * t]), p1 = ld3(xs + 3 * m.tri[3 * t + 1]), p2 = ld3(xs + 3 * m.tri[3 * t + 2]);
+        const V3<R> n = cross(p1 - p0, p2 - p0);
+        av[0] += 0.5 * (double)sqrt_r(dot(n, n));
+        av[1] += (double)dot(p0, cross(p1, p2)) / 6.0;
+    }
+    block_sum<2>(av, scratch);
+    const double A = av[0], V = av[1];
+
+    if (mode == 1) {
+        double G[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+            const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+            G[0] += x * x; G[1] += y * y; G[2] += z * z;
+            G[3] += x * y; G[4] += x * z; G[5] += y * z;
+        }
+        block_sum<6>(G, scratch);
+        if (threadIdx.x == 0) {
+            double lmax, lmin;
+            sym3_eig(G[0] / m.nv, G[1] / m.nv, G[2] / m.nv, G[3] / m.nv, G[4] / m.nv, G[5] / m.nv, lmax, lmin);
+            const double a = sqrt(lmax), b = sqrt(lmin > 0 ? lmin : 0);
+            double *o = stats + 6 * (size_t)c;
+            o[0] = v.ctr[3 * c] + mean[0];
+            o[1] = v.ctr[3 * c + 1] + mean[1];
+            o[2] = v.ctr[3 * c + 2] + mean[2];
+            o[3] = A;
+            o[4] = V;
+            o[5] = (a - b) / (a + b);
+        }
+        return;
+    }
+
+    // link and bending, one edge per thread
+    for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
+        const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
+        const V3<R> p0 = ld3(xs + 3 * i0), p1 = ld3(xs + 3 * i1), pa = ld3(xs + 3 * ia), pb = ld3(xs + 3 * ib);
+        const V3<R> ed = p1 - p0;
+        const R L = sqrt_r(dot(ed, ed));
+        const R L0 = m.L0[e];
+        const R eps = (L - L0) / L0;
+        const R den = m.m2 - eps * eps;
+        if (!(den > R(0))) atomicOr(v.status, ST_NUMERIC);
+        const R dEdL = m.K * (eps + eps / den);
+        const V3<R> fl = (dEdL / L) * ed;  // force on v0 (towards v1 when stretched)
+        sub_into(fs + 3 * i0, R(-1) * fl);
+        sub_into(fs + 3 * i1, fl);
+
+        const V3<R> da = pa - p0, db = pb - p0;
+        const V3<R> n1 = cross(ed, da), n2 = cross(db, ed);
+        const R q1 = dot(n1, n1), q2 = dot(n2, n2);
+        const R th = atan2_r(dot(cross(n1, n2), ed) / L, dot(n1, n2));
+        const R cb = m.kb * (th - m.th0[e]);
+        const V3<R> a1 = (R(1) / q1) * n1, a2 = (R(1) / q2) * n2;
+        const R sa0 = dot(pa - p1, ed) / L, sb0 = dot(pb - p1, ed) / L;
+        const R sa1 = dot(da, ed) / L, sb1 = dot(db, ed) / L;
+        sub_into(fs + 3 * ia, (-cb * L) * a1);
+        sub_into(fs + 3 * ib, (-cb * L) * a2);
+        sub_into(fs + 3 * i0, cb * (R(-1) * (sa0 * a1 + sb0 * a2)));
+        sub_into(fs + 3 * i1, cb * (sa1 * a1 + sb1 * a2));
+    }
+
+    // area and volume gradients, one triangle per thread
+    const R ca = R(m.k_area * (A - m.A0) / (m.A0 * m.A0));
+    const R cv = R(m.k_volume * (V - m.V0) / (m.V0 * m.V0));
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const int j0 = m.tri[3 * t], j1 = m.tri[3 * t + 1], j2 = m.tri[3 * t + 2];
+        const V3<R> p0 = ld3(xs + 3 * j0), p1 = ld3(xs + 3 * j1), p2 = ld3(xs + 3 * j2);
+        const V3<R> n = cross(p1 - p0, p2 - p0);
+        const V3<R> nh = (R(1) / sqrt_r(dot(n, n))) * n;
+        const R ha = R(0.5) * ca, sv = cv / R(6);
+        sub_into(fs + 3 * j0, ha * cross(nh, p2 - p1) + sv * cross(p1, p2));
+        sub_into(fs + 3 * j1, ha * cross(nh, p0 - p2) + sv * cross(p2, p0));
+        sub_into(fs + 3 * j2, ha * cross(nh, p1 - p0) + sv * cross(p0, p1));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * m.nv; k += blockDim.x) v.Fv[3 * (size_t)first + k] = fs[k];
+}
+
+}  // namespace
+
+template <typename R>
+void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st) {
+    if (v.ncell == 0) return;
+    // positions and force accumulators of the largest mesh type
+    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv), st>>>(v, mode, stats);
+}
+
+template <typename R>
+cudaError_t set_cell_smem_limit(size_t bytes) {
+    return cudaFuncSetAttribute(cell_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template void launch_cell_forces<double>(const View<double> &, int, double *, cudaStream_t);
+template void launch_cell_forces<float>(const View<float> &, int, double *, cudaStream_t);
+template cudaError_t set_cell_smem_limit<double>(size_t);
+template cudaError_t set_cell_smem_limit<float>(size_t);
+
+}  // namespace hemo

@@ -1,0 +1,300 @@
+"""Python binding of libhemo (include/hemo.h): argument marshalling only.
+
+Every step of the coupled lattice-Boltzmann / immersed-boundary time step
+runs in the library's CUDA kernels.  The library is loaded from this package
+directory; if it has not been built the import of the binding fails loudly
+(there is no CPU fallback).  PyTorch provides device memory (through the
+allocator callbacks below) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, 'libhemo.so')
+
+HEMO_OK, HEMO_ERR_ARG, HEMO_ERR_OOM, HEMO_ERR_CUDA, HEMO_ERR_NUMERIC, HEMO_ERR_DOMAIN, HEMO_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6
+PRECISIONS = {'f64': 0, 'f32': 1, 'f16': 2, 'bf16': 3}
+HEMO_RHO, HEMO_U, HEMO_VERTS, HEMO_FORCES, HEMO_CELLSTATS = 1, 2, 4, 8, 16
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class hemo_lattice_desc(C.Structure):
+    _fields_ = [('nx', C.c_int), ('ny', C.c_int), ('nz', C.c_int), ('tau', C.c_double),
+                ('precision', C.c_int), ('periodic', C.c_int * 3), ('wall_mask', C.c_void_p),
+                ('wall_velocity', (C.c_double * 3) * 2), ('body_force', C.c_double * 3),
+                ('cuda_stream', C.c_void_p), ('alloc', ALLOC_FN), ('release', FREE_FN),
+                ('alloc_ctx', C.c_void_p)]
+
+
+class hemo_mesh_desc(C.Structure):
+    _fields_ = [('nv', C.c_int), ('nt', C.c_int), ('tri', C.c_void_p), ('rest_xyz', C.c_void_p),
+                ('k_link', C.c_double), ('k_bend', C.c_double), ('k_area', C.c_double),
+                ('k_volume', C.c_double), ('kbt', C.c_double), ('persistence', C.c_double),
+                ('max_strain', C.c_double)]
+
+
+class HemoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f'hemo error {code}: {msg}')
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libhemo.so (raises if it is missing: build it with
+    `python -c "import __graft_entry__ as g; g.build()"`)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f'{LIB_PATH} is missing: the CUDA library must be built first '
+                          '(python -c "import __graft_entry__ as g; g.build()")')
+    L = C.CDLL(LIB_PATH)
+    vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
+    sig = {
+        'hemo_create_lattice': ([C.POINTER(hemo_lattice_desc), C.POINTER(vp)], i),
+        'hemo_set_velocity': ([vp, vp], i),
+        'hemo_add_cells': ([vp, C.POINTER(hemo_mesh_desc), i, vp, vp, C.POINTER(i)], i),
+        'hemo_step': ([vp, i], i),
+        'hemo_sync': ([vp], i),
+        'hemo_get_fields': ([vp, C.c_uint, vp, vp, vp, vp, vp], i),
+        'hemo_get_sizes': ([vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(i), C.POINTER(i)], i),
+        'hemo_velocity_set': ([vp, vp], i),
+        'hemo_get_populations': ([vp, vp], i),
+        'hemo_get_links': ([vp, vp], i),
+        'hemo_get_edges': ([vp, i, vp, C.POINTER(i)], i),
+        'hemo_set_vertices': ([vp, vp], i),
+        'hemo_get_bins': ([vp, vp, vp, vp], i),
+        'hemo_set_phase_timing': ([vp, i], i),
+        'hemo_get_phase_times': ([vp, vp, C.POINTER(i)], i),
+        'hemo_destroy': ([vp], None),
+        'hemo_last_error': ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the header declares (used by the load test)."""
+    return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_sync',
+            'hemo_get_fields', 'hemo_get_sizes', 'hemo_velocity_set', 'hemo_get_populations',
+            'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
+            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_destroy', 'hemo_last_error']
+
+
+def check(rc):
+    if rc != HEMO_OK:
+        raise HemoError(rc, lib().hemo_last_error().decode())
+    return rc
+
+
+def velocity_set():
+    c = np.zeros((19, 3), np.int32)
+    w = np.zeros(19)
+    check(lib().hemo_velocity_set(c.ctypes.data, w.ctypes.data))
+    return c, w
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Simulation:
+    """One coupled LBM-IBM simulation on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, tau=1.0, precision='f32', periodic=(1, 1, 1), wall_mask=None,
+                 wall_velocity=None, body_force=None, stream=None, torch_allocator=True):
+        import torch
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.precision = precision
+        self._rdtype = np.float64 if precision == 'f64' else np.float32
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        d = hemo_lattice_desc()
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.tau = tau
+        d.precision = PRECISIONS[precision]
+        for k in range(3):
+            d.periodic[k] = int(periodic[k])
+        self._mask = None
+        if wall_mask is not None:
+            self._mask = np.ascontiguousarray(wall_mask, dtype=np.uint8).reshape(-1)
+            assert self._mask.size == self.N
+            d.wall_mask = self._mask.ctypes.data
+        wv = np.zeros((2, 3)) if wall_velocity is None else np.asarray(wall_velocity, float)
+        for a in range(2):
+            for b in range(3):
+                d.wall_velocity[a][b] = wv[a, b]
+        g = np.zeros(3) if body_force is None else np.asarray(body_force, float)
+        for k in range(3):
+            d.body_force[k] = g[k]
+        d.cuda_stream = self._stream.cuda_stream
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+            stream = self._stream
+
+            def _alloc(nbytes, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except Exception:
+                    return None
+
+            def _free(ptr, ctx):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+            d.alloc = self._alloc_cb
+            d.release = self._free_cb
+        self._desc = d
+        self.handle = C.c_void_p()
+        check(lib().hemo_create_lattice(C.byref(d), C.byref(self.handle)))
+        self._meshes = []
+
+    # -- construction ------------------------------------------------------
+    @classmethod
+    def from_config(cls, cfg, precision='f32', **kw):
+        s = cls(cfg.nx, cfg.ny, cfg.nz, cfg.tau, precision, cfg.periodic, cfg.mask, cfg.wall_velocity,
+                cfg.body_force, **kw)
+        if cfg.init_velocity is not None:
+            s.set_velocity(cfg.init_velocity)
+        types = np.asarray(cfg.cell_type)
+        # cells are added in configuration order (one call per run of equal
+        # type) so the global vertex numbering is the configuration's
+        runs = []
+        for k, t in enumerate(types):
+            if runs and runs[-1][0] == t:
+                runs[-1][1].append(k)
+            else:
+                runs.append((t, [k]))
+        for t, idx in runs:
+            s.add_cells(cfg.meshes[t], cfg.centers[idx], cfg.rotations[idx])
+        if not runs:
+            for mt in cfg.meshes:
+                s.add_cells(mt, np.zeros((0, 3)), np.zeros((0, 3, 3)))
+        return s
+
+    def set_velocity(self, u):
+        if u is None:
+            check(lib().hemo_set_velocity(self.handle, None))
+        else:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            assert u.size == 3 * self.N
+            check(lib().hemo_set_velocity(self.handle, u.ctypes.data))
+
+    def add_cells(self, mesh, centers, rots):
+        """Add cells of one mesh type (an `inputs.MeshType`)."""
+        tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
+        rest = np.ascontiguousarray(mesh.rest, dtype=np.float64)
+        centers = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
+        rots = np.ascontiguousarray(rots, dtype=np.float64).reshape(-1, 3, 3)
+        m = hemo_mesh_desc(len(rest), len(tri), tri.ctypes.data, rest.ctypes.data, mesh.k_link, mesh.k_bend,
+                           mesh.k_area, mesh.k_volume, mesh.kbt, mesh.persistence, mesh.max_strain)
+        first = C.c_int(-1)
+        check(lib().hemo_add_cells(self.handle, C.byref(m), len(centers), centers.ctypes.data,
+                                   rots.ctypes.data, C.byref(first)))
+        self._meshes.append(mesh)
+        return first.value
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, n=1):
+        check(lib().hemo_step(self.handle, int(n)))
+
+    def sync(self):
+        return check(lib().hemo_sync(self.handle))
+
+    def sizes(self):
+        n, v, c, b = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_int()
+        check(lib().hemo_get_sizes(self.handle, C.byref(n), C.byref(v), C.byref(c), C.byref(b)))
+        return n.value, v.value, c.value, b.value
+
+    # -- read-out ----------------------------------------------------------
+    def get_fields(self, what=HEMO_RHO | HEMO_U | HEMO_VERTS | HEMO_FORCES | HEMO_CELLSTATS, out=None):
+        """Copy fields to host numpy arrays (or into the given host/device
+        buffers `out` = dict of arrays or tensors)."""
+        _, nv, nc, _ = self.sizes()
+        out = dict(out or {})
+        if what & HEMO_RHO and 'rho' not in out:
+            out['rho'] = np.zeros(self.shape, self._rdtype)
+        if what & HEMO_U and 'u' not in out:
+            out['u'] = np.zeros(self.shape + (3,), self._rdtype)
+        if what & HEMO_VERTS and 'X' not in out:
+            out['X'] = np.zeros((nv, 3))
+        if what & HEMO_FORCES and 'Fv' not in out:
+            out['Fv'] = np.zeros((nv, 3))
+        if what & HEMO_CELLSTATS and 'cellstats' not in out:
+            out['cellstats'] = np.zeros((nc, 6))
+        check(lib().hemo_get_fields(self.handle, what, _ptr(out.get('rho')), _ptr(out.get('u')),
+                                    _ptr(out.get('X')), _ptr(out.get('Fv')), _ptr(out.get('cellstats'))))
+        return out
+
+    def populations(self):
+        f = np.zeros(self.shape + (19,))
+        check(lib().hemo_get_populations(self.handle, f.ctypes.data))
+        return f
+
+    def links(self):
+        out = np.zeros(self.shape, np.uint64)
+        check(lib().hemo_get_links(self.handle, out.ctypes.data))
+        return out
+
+    def edges(self, type_id):
+        mesh = self._meshes[type_id]
+        buf = np.zeros(4 * (3 * len(mesh.tri) // 2 + 1), np.int32)
+        ne = C.c_int()
+        check(lib().hemo_get_edges(self.handle, int(type_id), buf.ctypes.data, C.byref(ne)))
+        return buf[:4 * ne.value].reshape(-1, 4)
+
+    def set_vertices(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        check(lib().hemo_set_vertices(self.handle, X.ctypes.data))
+
+    def bins(self):
+        _, nv, _, nb = self.sizes()
+        key = np.zeros(nv, np.int32)
+        perm = np.zeros(nv, np.int32)
+        start = np.zeros(nb + 1, np.int32)
+        check(lib().hemo_get_bins(self.handle, key.ctypes.data, perm.ctypes.data, start.ctypes.data))
+        return key, perm, start
+
+    PHASES = ('membrane', 'bins', 'spread', 'collide', 'moments', 'interp')
+
+    def set_phase_timing(self, on=True):
+        check(lib().hemo_set_phase_timing(self.handle, int(bool(on))))
+
+    def phase_times(self):
+        """Device ms of each phase of the most recent step, and the kernel
+        launches per step."""
+        ms = np.zeros(len(self.PHASES), np.float32)
+        k = C.c_int()
+        check(lib().hemo_get_phase_times(self.handle, ms.ctypes.data, C.byref(k)))
+        return dict(zip(self.PHASES, ms.astype(float))), k.value
+
+    def close(self):
+        if getattr(self, 'handle', None) and self.handle.value:
+            lib().hemo_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
