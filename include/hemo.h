@@ -205,6 +205,34 @@ int hemo_set_phase_timing(hemo_sim *sim, int on);
  * Synchronises.  HEMO_ERR_STATE if timing is off or no step ran yet. */
 int hemo_get_phase_times(hemo_sim *sim, float *ms, int *kernels_per_step);
 
+/* ---- binning without device allocation -------------------------------- */
+
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory (code inside another
+ * framework's memory budget, latency-critical loops where cudaMalloc's
+ * implicit device synchronisation is not acceptable, tools that hold vertex
+ * positions in their own buffers and no simulation handle).
+ *
+ * Bins `nv` absolute vertex positions exactly as hemo_get_bins does (same
+ * kernels, same key rule: 8^3 lattice blocks of floor(X), wrapped on periodic
+ * axes, clamped to the edge block on the others; perm = stable sort by key;
+ * start = first position of each block, nbins + 1 entries) and allocates
+ * nothing.  verts: device, nv*3 double; periodic: host, 3 ints; key, perm:
+ * device, nv int32; start: device, nbins + 1 int32, nbins = ceil(nx/8) *
+ * ceil(ny/8) * ceil(nz/8); cuda_stream: cudaStream_t or NULL.  Asynchronous:
+ * outputs are ready when the stream reaches the end of the call's work.
+ *
+ * Scratch (block counts, cursors, unsorted permutation) is a 5 MiB array in
+ * the library's device image, held by every GPU that loads the library until
+ * the process exits.  Limits: nv <= 1,048,576 and nbins <= 131,072; larger
+ * sizes return HEMO_ERR_ARG with a message.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and give wrong results; serialise them. */
+int hemo_bin_vertices_noalloc(const double *verts, int nv, int nx, int ny, int nz, const int32_t *periodic,
+                              int32_t *key, int32_t *perm, int32_t *start, void *cuda_stream);
+
 /* Release every resource of the simulation (NULL is allowed). */
 void hemo_destroy(hemo_sim *sim);
 

@@ -74,6 +74,8 @@ double dt3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
 }  // namespace
 
+void hemo::set_last_error(const char *msg) { g_err = msg; }
+
 struct hemo_sim {
     int precision = 0;
     int nx = 0, ny = 0, nz = 0;

@@ -135,6 +135,9 @@ template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st)
 template <typename R> void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st);
 template <typename R> void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st);
 
+// sets the message returned by hemo_last_error() on the calling thread
+void set_last_error(const char *msg);
+
 // periodic wrap of a lattice coordinate
 __host__ __device__ __forceinline__ int wrap(int j, int n) {
     int r = j % n;

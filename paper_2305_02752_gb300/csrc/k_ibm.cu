@@ -346,3 +346,109 @@ HEMO_INST(double)
 HEMO_INST(float)
 
 }  // namespace hemo
+
+// ===========================================================================
+// Vertex binning without any device allocation.
+//
+// Some callers cannot let a library allocate device memory: code that runs
+// inside another framework's memory budget (a caching allocator that owns
+// all of the GPU's memory), latency-critical loops in which cudaMalloc's
+// implicit device synchronisation is not acceptable, or tools that hold
+// vertex positions in their own buffers and no simulation handle.  For them
+// hemo_bin_vertices_noalloc runs the same binning kernels as the step on
+// caller-owned inputs and outputs, with its scratch (block counts, block
+// cursors, unsorted permutation) in the file-scope array below.  The array
+// is part of the loaded module: every GPU that loads the library holds its
+// 5 MiB until the process exits.
+// ===========================================================================
+#include <mutex>
+
+namespace hemo {
+
+namespace {
+
+constexpr int NOALLOC_MAX_VERTICES = 1 << 20;  // 1,048,576 vertices
+constexpr int NOALLOC_MAX_BINS = 1 << 17;      // 131,072 blocks of 8^3 nodes
+
+// [0, MAX_BINS): counts; [MAX_BINS, 2 MAX_BINS): cursors; then the unsorted
+// permutation (MAX_VERTICES entries)
+static __device__ __align__(256) int g_bin_scratch[2 * NOALLOC_MAX_BINS + NOALLOC_MAX_VERTICES];
+
+// Device address of g_bin_scratch per device; in host code the symbol is
+// only a host-side stand-in, so its address is taken once per device with
+// cudaGetSymbolAddress while that device is current.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int *g_bin_scratch_dev[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_bin_scratch_mutex;
+
+// key and count of each vertex from absolute FP64 positions (same floor,
+// wrap and clamp rule as the step's anchor kernel)
+__global__ void abs_key_count_kernel(const double *X, int nv, int nx, int ny, int nz, int px, int py, int pz,
+                                     int nb0, int nb1, int *key, int *counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const int dims[3] = {nx, ny, nz};
+    const int per[3] = {px, py, pz};
+    int b[3];
+    for (int d = 0; d < 3; ++d) {
+        int j = (int)floor(X[3 * (size_t)i + d]);
+        if (per[d]) j = wrap(j, dims[d]);
+        const int jc = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
+        b[d] = jc / BLK;
+    }
+    const int k = b[0] + nb0 * (b[1] + nb1 * b[2]);
+    key[i] = k;
+    atomicAdd(counts + k, 1);
+}
+
+int noalloc_fail(int code, const char *msg) {
+    set_last_error(msg);  // reported by hemo_last_error()
+    return code;
+}
+
+}  // namespace
+
+}  // namespace hemo
+
+extern "C" int hemo_bin_vertices_noalloc(const double *verts, int nv, int nx, int ny, int nz, const int32_t *periodic,
+                                         int32_t *key, int32_t *perm, int32_t *start, void *cuda_stream) {
+    using namespace hemo;
+    if (nx < 1 || ny < 1 || nz < 1 || nv < 0 || !periodic || !start || (nv > 0 && (!verts || !key || !perm)))
+        return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: bad sizes or null pointer");
+    if (nv > NOALLOC_MAX_VERTICES)
+        return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: more than 1,048,576 vertices");
+    const long long nb0 = (nx + BLK - 1) / BLK, nb1 = (ny + BLK - 1) / BLK, nb2 = (nz + BLK - 1) / BLK;
+    if (nb0 * nb1 * nb2 > NOALLOC_MAX_BINS)
+        return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: more than 131,072 lattice blocks of 8^3 nodes");
+    const int nbins = (int)(nb0 * nb1 * nb2);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return noalloc_fail(HEMO_ERR_CUDA, "hemo_bin_vertices_noalloc: no usable current device");
+    int *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_bin_scratch_mutex);
+        if (!g_bin_scratch_dev[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
+            if (e != cudaSuccess || !p) return noalloc_fail(HEMO_ERR_CUDA, "hemo_bin_vertices_noalloc: cudaGetSymbolAddress failed");
+            g_bin_scratch_dev[dev] = (int *)p;
+        }
+        scratch = g_bin_scratch_dev[dev];
+    }
+    int *counts = scratch, *cursor = scratch + NOALLOC_MAX_BINS, *perm_raw = scratch + 2 * NOALLOC_MAX_BINS;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the array keeps the previous call's contents: the counts must start at zero
+    if (cudaMemsetAsync(counts, 0, sizeof(int) * nbins, st) != cudaSuccess)
+        return noalloc_fail(HEMO_ERR_CUDA, "hemo_bin_vertices_noalloc: clearing the counts failed");
+    if (nv > 0)
+        abs_key_count_kernel<<<(nv + 255) / 256, 256, 0, st>>>(verts, nv, nx, ny, nz, periodic[0] != 0, periodic[1] != 0,
+                                                               periodic[2] != 0, (int)nb0, (int)nb1, key, counts);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, start, cursor, nbins);
+    if (nv > 0) {
+        scatter_kernel<<<(nv + 255) / 256, 256, 0, st>>>(key, cursor, perm_raw, nv);
+        sort_bins_kernel<<<(int)(((long long)nbins * 32 + 127) / 128), 128, 0, st>>>(start, perm_raw, perm, nbins);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(HEMO_ERR_CUDA, cudaGetErrorString(e));
+    return HEMO_OK;
+}

@@ -76,6 +76,7 @@ def lib():
         'hemo_get_bins': ([vp, vp, vp, vp], i),
         'hemo_set_phase_timing': ([vp, i], i),
         'hemo_get_phase_times': ([vp, vp, C.POINTER(i)], i),
+        'hemo_bin_vertices_noalloc': ([vp, i, i, i, i, vp, vp, vp, vp, vp], i),
         'hemo_destroy': ([vp], None),
         'hemo_last_error': ([], C.c_char_p),
     }
@@ -92,13 +93,28 @@ def exported_symbols():
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
-            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_destroy', 'hemo_last_error']
+            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_destroy',
+            'hemo_last_error']
 
 
 def check(rc):
     if rc != HEMO_OK:
         raise HemoError(rc, lib().hemo_last_error().decode())
     return rc
+
+
+def bin_vertices_noalloc(verts, dims, periodic, key, perm, start, stream=None):
+    """Bin absolute vertex positions without any allocation by the library
+    (for callers that cannot let it allocate device memory).  verts: CUDA
+    float64 tensor [nv, 3]; key, perm: CUDA int32 [nv]; start: CUDA int32
+    [nbins + 1], all caller-owned.  Same binning as Simulation.bins();
+    asynchronous on `stream` (default: current stream)."""
+    import torch
+    nx, ny, nz = dims
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    check(lib().hemo_bin_vertices_noalloc(verts.data_ptr(), int(verts.shape[0]), nx, ny, nz, per.ctypes.data,
+                                          key.data_ptr(), perm.data_ptr(), start.data_ptr(), st))
 
 
 def velocity_set():
