@@ -72,6 +72,22 @@ D3 sub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 D3 crs(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
 double dt3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// smallest stride >= n/32 + 1 that is coprime with n (1 for small n)
+int coprime_stride(int n) {
+    auto gcd = [](int a, int b) {
+        while (b) {
+            int t = a % b;
+            a = b;
+            b = t;
+        }
+        return a;
+    };
+    for (int st = n / 32 + 1; st < n; ++st)
+        if (gcd(st, n) == 1) return st;
+    return 1;
+}
+
+
 }  // namespace
 
 void hemo::set_last_error(const char *msg) { g_err = msg; }
@@ -106,8 +122,9 @@ struct hemo_sim {
     void *meshes_d = nullptr;
     int nb[3] = {1, 1, 1}, nbins = 1;
     int *key = nullptr, *counts = nullptr, *start = nullptr, *cursor = nullptr, *perm_raw = nullptr, *perm = nullptr;
-    int *anc_i = nullptr, *s_i = nullptr;
-    void *anc_t = nullptr, *s_t = nullptr, *s_F = nullptr;
+    int *anc_i = nullptr;
+    void *anc_t = nullptr;
+    void *tiles = nullptr;
     // status
     unsigned *status = nullptr;
     unsigned *status_host = nullptr;
@@ -216,9 +233,7 @@ View<R> make_view(hemo_sim *s) {
     v.perm = s->perm;
     v.anc_i = s->anc_i;
     v.anc_t = (R *)s->anc_t;
-    v.s_i = s->s_i;
-    v.s_t = (R *)s->s_t;
-    v.s_F = (R *)s->s_F;
+    v.tiles = (R *)s->tiles;
     v.status = s->status;
     return v;
 }
@@ -233,8 +248,7 @@ void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
     if (s->ncell) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n
     mark(HEMO_PHASE_BINS);
     if (s->ncell) {
-        launch_bins<R>(v, st);    // anchors, stable sort by block
-        launch_gather<R>(v, st);  // anchors and forces in bin order
+        launch_bins<R>(v, st, false);  // anchors, counting sort by block
     }
     mark(HEMO_PHASE_SPREAD);
     if (s->ncell) launch_spread<R>(v, st);  // F = g + sum F_v delta
@@ -262,15 +276,13 @@ int finalize_impl(hemo_sim *s) {
     s->perm_raw = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
     s->perm = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
     s->anc_i = (int *)dalloc(s, sizeof(int) * 3 * std::max(nv, 1));
-    s->s_i = (int *)dalloc(s, sizeof(int) * 3 * std::max(nv, 1));
     s->anc_t = dalloc(s, rs * 3 * std::max(nv, 1));
-    s->s_t = dalloc(s, rs * 3 * std::max(nv, 1));
-    s->s_F = dalloc(s, rs * 3 * std::max(nv, 1));
     s->counts = (int *)dalloc(s, sizeof(int) * s->nbins);
     s->cursor = (int *)dalloc(s, sizeof(int) * s->nbins);
     s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
-    if (!s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
-        !s->key || !s->perm_raw || !s->perm || !s->anc_i || !s->s_i || !s->anc_t || !s->s_t || !s->s_F ||
+    s->tiles = dalloc(s, rs * 3 * (size_t)(BLK + 3) * (BLK + 3) * (BLK + 3) * s->nbins);
+    if (!s->tiles || !s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
+        !s->key || !s->perm_raw || !s->perm || !s->anc_i || !s->anc_t ||
         !s->counts || !s->cursor || !s->start)
         return fail(HEMO_ERR_OOM, "device allocation of cell and bin buffers failed");
     cudaStream_t st = s->stream;
@@ -286,9 +298,23 @@ int finalize_impl(hemo_sim *s) {
         R *dL0 = (R *)dalloc(s, rs * m.ne);
         R *dth0 = (R *)dalloc(s, rs * m.ne);
         if (!dtri || !dedge || !dL0 || !dth0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
-        std::vector<R> L0(m.L0.begin(), m.L0.end()), th0(m.th0.begin(), m.th0.end());
-        HEMO_CU(cudaMemcpy(dtri, m.tri.data(), sizeof(int) * m.tri.size(), cudaMemcpyHostToDevice));
-        HEMO_CU(cudaMemcpy(dedge, m.edge.data(), sizeof(int) * m.edge.size(), cudaMemcpyHostToDevice));
+        // processing order: item q is q * stride mod n (stride coprime with
+        // n, about n/32), so a warp's lanes work on far-apart mesh parts
+        const int se = coprime_stride(m.ne), st3 = coprime_stride(m.nt);
+        std::vector<int> edge_p(4 * (size_t)m.ne), tri_p(3 * (size_t)m.nt);
+        std::vector<R> L0(m.ne), th0(m.ne);
+        for (int q = 0; q < m.ne; ++q) {
+            const int e = (int)(((long long)q * se) % m.ne);
+            for (int j = 0; j < 4; ++j) edge_p[4 * (size_t)q + j] = m.edge[4 * (size_t)e + j];
+            L0[q] = R(m.L0[e]);
+            th0[q] = R(m.th0[e]);
+        }
+        for (int q = 0; q < m.nt; ++q) {
+            const int t = (int)(((long long)q * st3) % m.nt);
+            for (int j = 0; j < 3; ++j) tri_p[3 * (size_t)q + j] = m.tri[3 * (size_t)t + j];
+        }
+        HEMO_CU(cudaMemcpy(dtri, tri_p.data(), sizeof(int) * tri_p.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dedge, edge_p.data(), sizeof(int) * edge_p.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dL0, L0.data(), rs * m.ne, cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dth0, th0.data(), rs * m.ne, cudaMemcpyHostToDevice));
         MeshDev<R> d{};
@@ -711,8 +737,8 @@ int hemo_get_bins(hemo_sim *s, int32_t *key, int32_t *perm, int32_t *start) {
     int rc = ensure_ready(s);
     if (rc) return rc;
     if (s->nv) {
-        if (is_f64(s)) launch_bins<double>(make_view<double>(s), s->stream);
-        else launch_bins<float>(make_view<float>(s), s->stream);
+        if (is_f64(s)) launch_bins<double>(make_view<double>(s), s->stream, true);
+        else launch_bins<float>(make_view<float>(s), s->stream, true);
         HEMO_CU(cudaGetLastError());
     }
     if ((rc = copy_out(s, key, s->key, sizeof(int) * s->nv))) return rc;

@@ -65,8 +65,8 @@ template <> struct Store<__nv_bfloat16> {
 // ---------------------------------------------------------------------------
 template <typename R> struct MeshDev {
     int nv, nt, ne;
-    const int *tri;     // nt*3
-    const int *edge;    // ne*4: v0, v1, a, b
+    const int *tri;     // nt*3, in processing order
+    const int *edge;    // ne*4: v0, v1, a, b, in processing order
     const R *L0;        // ne
     const R *th0;       // ne
     double A0, V0;
@@ -110,9 +110,7 @@ template <typename R> struct View {
     int *perm;                 // nv, stable (key, vertex id)
     int *anc_i;                // nv*3 stencil base floor(X) (wrapped on periodic axes)
     R *anc_t;                  // nv*3 fractions X - floor(X)
-    int *s_i;                  // nv*3 anchors in bin order
-    R *s_t;                    // nv*3
-    R *s_F;                    // nv*3 forces in bin order
+    R *tiles;                  // nbins*3*11^3 per-bin spreading tiles
     unsigned *status;
 };
 
@@ -128,8 +126,7 @@ void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, 
 template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
 template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
 template <typename R> size_t cell_smem_bytes(int max_nv) { return 6 * (size_t)max_nv * sizeof(R); }
-template <typename R> void launch_bins(const View<R> &v, cudaStream_t st);
-template <typename R> void launch_gather(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_bins(const View<R> &v, cudaStream_t st, bool stable);
 template <typename R> void launch_spread(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st);

@@ -5,17 +5,22 @@
 //
 // Binning: each vertex gets its stencil anchor (floor(X) per axis, wrapped on
 // periodic axes, and the fraction X - floor(X)) and the key of the 8^3 block
-// that holds floor(X).  Counting sort: per-block counts, exclusive scan,
-// scatter with per-block cursors, then each block's segment is ordered by
-// vertex id, which makes the permutation the stable sort by (key, id).
+// that holds floor(X).  Counting sort: per-block counts (warp-aggregated
+// atomics), exclusive scan, scatter with per-block cursors, then each block's
+// segment is ordered by vertex id, which makes the permutation the stable
+// sort by (key, id) (for read-out; the step itself does not depend on the
+// order of the vertices within a bin and skips that sort).
 //
-// Spreading is owner-computes: one CTA per lattice block gathers the
-// vertices of the (up to 27) neighbouring blocks, adds the parts of their
-// 4x4x4 stencils that fall inside its own 8^3 nodes into shared memory, and
-// writes F = g + sum for every node of the block once (no global atomics, no
-// separate clearing pass).  Interpolation: one CTA per non-empty block stages
-// the velocity of its 11^3 neighbourhood in shared memory and evaluates the
-// 64-node stencils of its own vertices from there.
+// Spreading in two phases without global atomics: each non-empty bin adds
+// its vertices' 4x4x4 stencils into an 11^3 tile in shared memory and writes
+// the tile out; then each 8^3 block (owner computes) sums the tile positions
+// of its neighbouring bins that map onto its nodes and writes F = g + sum for
+// every node once (no separate clearing pass).  Interpolation: one CTA per
+// non-empty bin stages the velocity of its 11^3 neighbourhood in shared
+// memory and evaluates the 64-node stencils of its own vertices from there,
+// reducing the per-row partial sums with warp shuffles.
+#include <type_traits>
+
 #include "hemo_internal.cuh"
 
 namespace hemo {
@@ -27,15 +32,20 @@ inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
 __device__ __forceinline__ float sqrt_r(float a) { return sqrtf(a); }
 __device__ __forceinline__ double sqrt_r(double a) { return sqrt(a); }
 
-// Peskin 4-point weights of nodes floor(X) - 1 .. floor(X) + 2 for the
-// fraction t = X - floor(X) in [0, 1); one square root serves all four.
+constexpr int TILE = BLK + 3;           // stencil reach: one node below, two above
+constexpr int TILE3 = TILE * TILE * TILE;
+// Padded shared-memory strides of an 11^3 tile: the 16 lanes (b, c) of a
+// half-warp address rows TS_Y*b + TS_Z*c, which fall in 16 distinct banks
+// (TS_Y = 12, TS_Z = 161 = 1 mod 32).
+constexpr int TS_Y = 12, TS_Z = 161;
+constexpr int TILE_SMEM = TS_Z * TILE;
+
+// origin of bin k
 template <typename R>
-__device__ __forceinline__ void peskin4(R t, R w[4]) {
-    const R q = sqrt_r(R(1) + R(4) * t - R(4) * t * t);
-    w[0] = (R(3) - R(2) * t - q) * R(0.125);
-    w[1] = (R(3) - R(2) * t + q) * R(0.125);
-    w[2] = (R(1) + R(2) * t + q) * R(0.125);
-    w[3] = (R(1) + R(2) * t - q) * R(0.125);
+__device__ __forceinline__ void bin_origin(const View<R> &v, int k, int org[3]) {
+    org[0] = (k % v.nb[0]) * BLK;
+    org[1] = ((k / v.nb[0]) % v.nb[1]) * BLK;
+    org[2] = (k / (v.nb[0] * v.nb[1])) * BLK;
 }
 
 template <typename R>
@@ -62,7 +72,10 @@ __global__ void anchor_count_kernel(View<R> v) {
     }
     const int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
     v.key[i] = key;
-    atomicAdd(v.counts + key, 1);
+    // neighbouring vertex ids mostly share a block: one atomic per group
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, key);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
 }
 
 // exclusive scan of the block counts by one CTA of 1024 threads
@@ -90,19 +103,58 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int *counts, int *star
     if (threadIdx.x == 1023) start[nbins] = part[1023];
 }
 
+// scatter with per-block cursors; lanes of a warp with the same key reserve
+// their slots with one atomic
 __global__ void scatter_kernel(const int *key, int *cursor, int *perm_raw, int nv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    perm_raw[atomicAdd(cursor + key[i], 1)] = i;
+    const int k = key[i];
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, k);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cursor + k, __popc(grp));
+    base = __shfl_sync(act, base, leader);
+    perm_raw[base + __popc(grp & ((1u << lane) - 1u))] = i;
 }
 
-// one warp per block: rank each id among the block's ids (ids are unique)
-__global__ void sort_bins_kernel(const int *start, const int *perm_raw, int *perm, int nbins) {
+// One warp per block: each id's rank among the block's ids (ids are unique)
+// is its position.  Segments of up to SORT_SMEM ids are ranked from shared
+// memory, SORT_K ids per lane at a time held in registers (one pass over the
+// segment per group); longer segments one id at a time from global memory.
+constexpr int SORT_SMEM = 1024;
+constexpr int SORT_K = 8;
+__global__ void __launch_bounds__(128) sort_bins_kernel(const int *start, const int *perm_raw, int *perm, int nbins) {
+    __shared__ int buf[4][SORT_SMEM];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (w >= nbins) return;
     const int s = start[w], n = start[w + 1] - s;
     const int *seg = perm_raw + s;
+    if (n <= SORT_SMEM) {
+        for (int a = lane; a < n; a += 32) buf[wl][a] = seg[a];
+        __syncwarp();
+        const int *sh = buf[wl];
+        for (int g0 = 0; g0 < n; g0 += 32 * SORT_K) {
+            int va[SORT_K], r[SORT_K];
+#pragma unroll
+            for (int j = 0; j < SORT_K; ++j) {
+                const int a = g0 + lane + 32 * j;
+                va[j] = a < n ? sh[a] : 0x7fffffff;
+                r[j] = 0;
+            }
+            for (int b = 0; b < n; ++b) {
+                const int x = sh[b];
+#pragma unroll
+                for (int j = 0; j < SORT_K; ++j) r[j] += x < va[j];
+            }
+#pragma unroll
+            for (int j = 0; j < SORT_K; ++j)
+                if (g0 + lane + 32 * j < n) perm[s + r[j]] = va[j];
+        }
+        return;
+    }
     for (int a = lane; a < n; a += 32) {
         const int va = seg[a];
         int r = 0;
@@ -111,16 +163,15 @@ __global__ void sort_bins_kernel(const int *start, const int *perm_raw, int *per
     }
 }
 
+// Peskin 4-point weights of nodes floor(X) - 1 .. floor(X) + 2 for the
+// fraction t = X - floor(X) in [0, 1); one square root serves all four.
 template <typename R>
-__global__ void gather_kernel(View<R> v) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= v.nv) return;
-    const int i = v.perm[p];
-    for (int d = 0; d < 3; ++d) {
-        v.s_i[3 * (size_t)p + d] = v.anc_i[3 * (size_t)i + d];
-        v.s_t[3 * (size_t)p + d] = v.anc_t[3 * (size_t)i + d];
-        v.s_F[3 * (size_t)p + d] = v.Fv[3 * (size_t)i + d];
-    }
+__device__ __forceinline__ void peskin4(R t, R *w) {
+    const R q = sqrt_r(R(1) + R(4) * t - R(4) * t * t);
+    w[0] = (R(3) - R(2) * t - q) * R(0.125);
+    w[1] = (R(3) - R(2) * t + q) * R(0.125);
+    w[2] = (R(1) + R(2) * t + q) * R(0.125);
+    w[3] = (R(1) + R(2) * t - q) * R(0.125);
 }
 
 // distinct neighbour block coordinates along one axis
@@ -137,146 +188,277 @@ __device__ __forceinline__ int neighbour_blocks(int b, int nb, int periodic, int
     return cnt;
 }
 
+// Vertex records of one chunk of a bin, staged in shared memory: one thread
+// per vertex reads its anchor through the permutation, computes its row in
+// the bin's padded tile (-1 if the anchor is outside the bin, i.e. the
+// vertex left the lattice) and its twelve Peskin weights (x0..3, y0..3,
+// z0..3), and optionally its force.  The per-vertex loops below then touch
+// shared memory only.  Chunk size by precision keeps the FP64 kernels within
+// 48 KB of static shared memory.
+template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 256; };
 template <typename R>
-__global__ void __launch_bounds__(256) spread_kernel(View<R> v) {
-    __shared__ R acc[3][BLK * BLK * BLK];
-    __shared__ int seg_s[27], seg_pre[28];
-    __shared__ int nseg;
-    const int k = blockIdx.x;
-    const int bx = k % v.nb[0], by = (k / v.nb[0]) % v.nb[1], bz = k / (v.nb[0] * v.nb[1]);
-    const int org[3] = {bx * BLK, by * BLK, bz * BLK};
-    const int dims[3] = {v.nx, v.ny, v.nz};
-    for (int q = threadIdx.x; q < BLK * BLK * BLK; q += blockDim.x) acc[0][q] = acc[1][q] = acc[2][q] = R(0);
-    if (threadIdx.x == 0) {
-        int lx[3], ly[3], lz[3];
-        const int ncx = neighbour_blocks(bx, v.nb[0], v.per[0], lx);
-        const int ncy = neighbour_blocks(by, v.nb[1], v.per[1], ly);
-        const int ncz = neighbour_blocks(bz, v.nb[2], v.per[2], lz);
-        int ns = 0, run = 0;
-        for (int a = 0; a < ncz; ++a)
-            for (int b = 0; b < ncy; ++b)
-                for (int c = 0; c < ncx; ++c) {
-                    const int kk = lx[c] + v.nb[0] * (ly[b] + v.nb[1] * lz[a]);
-                    const int s0 = v.start[kk], s1 = v.start[kk + 1];
-                    if (s1 == s0) continue;
-                    seg_s[ns] = s0;
-                    seg_pre[ns] = run;
-                    run += s1 - s0;
-                    ++ns;
-                }
-        seg_pre[ns] = run;
-        nseg = ns;
-    }
-    __syncthreads();
-    const int total = seg_pre[nseg];
-    int seg = 0;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        while (q >= seg_pre[seg + 1]) ++seg;
-        const size_t p = (size_t)seg_s[seg] + (q - seg_pre[seg]);
-        R w[3][4];
-        int l[3][4];
-        bool any = true;
-        for (int d = 0; d < 3 && any; ++d) {
-            const int i0 = v.s_i[3 * p + d];
-            peskin4(v.s_t[3 * p + d], w[d]);
-            bool hit = false;
-            for (int a = 0; a < 4; ++a) {
-                int j = i0 + a - 1;
-                if (v.per[d]) j = wrap(j, dims[d]);
-                const int lj = j - org[d];
-                const bool in = lj >= 0 && lj < BLK && j < dims[d] && j >= 0;
-                l[d][a] = in ? lj : -1;
-                hit |= in;
-            }
-            any = hit;
+__device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, const int org[3], int *srow, R *sw,
+                                            R *sF, int *sperm) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int i = v.perm[p0 + j];
+        int row = 0;
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+            const int b = v.anc_i[3 * (size_t)i + d] - org[d];
+            ok &= b >= 0 && b < BLK;
+            row += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
+            peskin4(v.anc_t[3 * (size_t)i + d], sw + 12 * j + 4 * d);
+            if (sF) sF[3 * j + d] = v.Fv[3 * (size_t)i + d];
         }
-        if (!any) continue;
-        const R Fx = v.s_F[3 * p], Fy = v.s_F[3 * p + 1], Fz = v.s_F[3 * p + 2];
-        for (int c = 0; c < 4; ++c) {
-            if (l[2][c] < 0) continue;
-            for (int b = 0; b < 4; ++b) {
-                if (l[1][b] < 0) continue;
-                const R wzy = w[2][c] * w[1][b];
-                for (int a = 0; a < 4; ++a) {
-                    if (l[0][a] < 0) continue;
-                    const R ww = wzy * w[0][a];
-                    const int idx = l[0][a] + BLK * (l[1][b] + BLK * l[2][c]);
-                    atomicAdd(&acc[0][idx], Fx * ww);
-                    atomicAdd(&acc[1][idx], Fy * ww);
-                    atomicAdd(&acc[2][idx], Fz * ww);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const size_t N = (size_t)v.N;
-    for (int q = threadIdx.x; q < BLK * BLK * BLK; q += blockDim.x) {
-        const int x = org[0] + (q % BLK), y = org[1] + (q / BLK) % BLK, z = org[2] + q / (BLK * BLK);
-        if (x >= v.nx || y >= v.ny || z >= v.nz) continue;
-        const size_t n = (size_t)x + (size_t)v.nx * ((size_t)y + (size_t)v.ny * z);
-        const bool wall = v.ntype[n] & 0x7f;
-        v.F[n] = wall ? R(0) : v.g[0] + acc[0][q];
-        v.F[N + n] = wall ? R(0) : v.g[1] + acc[1][q];
-        v.F[2 * N + n] = wall ? R(0) : v.g[2] + acc[2][q];
+        srow[j] = ok ? row : -1;
+        if (sperm) sperm[j] = i;
     }
 }
 
-constexpr int TILE = BLK + 3;  // stencil reach: one node below, two above
+// Phase 1 of spreading: one CTA per non-empty bin; a warp takes two
+// vertices, each half-warp's 16 lanes own one (y, z) row of the 4x4x4
+// stencil and add four x-neighbours into the bin's 11^3 shared tile.  The
+// tile is written out whole (compact [3][11^3]) for the owners to gather.
+//
+// FP32: the tile accumulates in 32-bit fixed point with integer shared
+// atomics (native, unaffected by address collisions, and exact: the sums do
+// not depend on the order of the vertices).  Per bin and component the
+// scale is the power of two 2^e with e = 30 - ceil(log2(max|F| * n / 8)):
+// a node's sum is at most max|F| times the sum of its n weights, each at
+// most 1/8, so |sum| * 2^e <= 2^30.  The quantum is max|F| * n * 2^-33 per
+// contribution, below FP32 rounding of sums of that size.  FP64 accumulates
+// in double.
+template <typename R> struct TileAcc {
+    using T = R;
+};
+template <> struct TileAcc<float> {
+    using T = int;
+};
 
 template <typename R>
-__global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
+__global__ void __launch_bounds__(256) spread_tile_kernel(View<R> v) {
+    using A = typename TileAcc<R>::T;
+    constexpr bool FIXED = std::is_same<A, int>::value;
+    constexpr int CAP = Stage<R>::CAP;
     const int k = blockIdx.x;
     const int s = v.start[k], e = v.start[k + 1];
     if (s == e) return;
-    __shared__ R tile[3][TILE * TILE * TILE];
-    const int bx = k % v.nb[0], by = (k / v.nb[0]) % v.nb[1], bz = k / (v.nb[0] * v.nb[1]);
-    const int org[3] = {bx * BLK, by * BLK, bz * BLK};
-    const int dims[3] = {v.nx, v.ny, v.nz};
-    const size_t N = (size_t)v.N;
-    for (int q = threadIdx.x; q < TILE * TILE * TILE; q += blockDim.x) {
-        int j[3] = {org[0] - 1 + q % TILE, org[1] - 1 + (q / TILE) % TILE, org[2] - 1 + q / (TILE * TILE)};
-        bool out = false;
-        for (int d = 0; d < 3; ++d) {
-            if (v.per[d]) j[d] = wrap(j[d], dims[d]);
-            else out |= j[d] < 0 || j[d] >= dims[d];
+    __shared__ A acc[3][TILE_SMEM];
+    __shared__ int srow[CAP];
+    __shared__ R sw[12 * CAP], sF[3 * CAP];
+    __shared__ float smax[3][8];
+    __shared__ float scale[3];
+    for (int q = threadIdx.x; q < TILE_SMEM; q += blockDim.x) acc[0][q] = acc[1][q] = acc[2][q] = A(0);
+    int org[3];
+    bin_origin(v, k, org);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
+    if (FIXED) {  // one scale per component for the whole bin
+        float m[3] = {0.f, 0.f, 0.f};
+        for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+            const int i = v.perm[j];
+            for (int d = 0; d < 3; ++d) m[d] = fmaxf(m[d], fabsf((float)v.Fv[3 * (size_t)i + d]));
         }
-        if (out) {  // beyond a non-periodic edge: resting wall
-            tile[0][q] = tile[1][q] = tile[2][q] = R(0);
-        } else {
-            const size_t n = (size_t)j[0] + (size_t)v.nx * ((size_t)j[1] + (size_t)v.ny * j[2]);
-            tile[0][q] = v.u[n];
-            tile[1][q] = v.u[N + n];
-            tile[2][q] = v.u[2 * N + n];
+        for (int d = 0; d < 3; ++d) {
+            for (int o = 16; o > 0; o >>= 1) m[d] = fmaxf(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
+            if (lane == 0) smax[d][warp] = m[d];
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            float mm = 0.f;
+            for (int w = 0; w < nw; ++w) mm = fmaxf(mm, smax[threadIdx.x][w]);
+            const float bound = mm * (float)(e - s) * 0.125f;
+            if (!(bound <= 3.0e38f)) {  // non-finite forces
+                atomicOr(v.status, ST_NUMERIC);
+                scale[threadIdx.x] = 0.f;
+            } else {
+                scale[threadIdx.x] = bound > 0.f ? ldexpf(1.f, min(29 - ilogbf(bound), 120)) : 0.f;
+            }
+        }
+    }
+    for (int p0 = s; p0 < e; p0 += CAP) {
+        const int n = min(CAP, e - p0);
+        if (p0 != s) __syncthreads();
+        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr);
+        __syncthreads();
+        for (int q = 2 * warp + h; q < n; q += 2 * nw) {
+            const int row0 = srow[q];
+            if (row0 < 0) continue;  // vertex outside the lattice (domain status already raised)
+            const R *w = sw + 12 * q;
+            const R wyz = w[4 + b] * w[8 + c];
+            R f[3] = {sF[3 * q] * wyz, sF[3 * q + 1] * wyz, sF[3 * q + 2] * wyz};
+            if (FIXED)
+                for (int d = 0; d < 3; ++d) f[d] *= (R)scale[d];
+            const int row = row0 + TS_Y * b + TS_Z * c;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const R wa = w[a];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (FIXED) atomicAdd((int *)&acc[d][row + a], __float2int_rn((float)(f[d] * wa)));
+                    else atomicAdd(&acc[d][row + a], f[d] * wa);
+                }
+            }
         }
     }
     __syncthreads();
-    for (int p = s + threadIdx.x; p < e; p += blockDim.x) {
-        R w[3][4];
-        int base[3];
-        bool ok = true;
-        for (int d = 0; d < 3; ++d) {
-            base[d] = v.s_i[3 * (size_t)p + d] - org[d];  // stencil starts at tile index base
-            ok &= base[d] >= 0 && base[d] < BLK;
-            peskin4(v.s_t[3 * (size_t)p + d], w[d]);
+    R *out = v.tiles + (size_t)k * 3 * TILE3;
+    float inv[3] = {1.f, 1.f, 1.f};
+    if (FIXED)
+        for (int d = 0; d < 3; ++d) inv[d] = scale[d] > 0.f ? 1.f / scale[d] : 0.f;
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+        const int sidx = q % TILE + TS_Y * ((q / TILE) % TILE) + TS_Z * (q / (TILE * TILE));
+        for (int d = 0; d < 3; ++d) out[d * TILE3 + q] = FIXED ? (R)((float)acc[d][sidx] * inv[d]) : (R)acc[d][sidx];
+    }
+}
+
+// Phase 2 of spreading (owner computes): one CTA per 8^3 block sums, for
+// each of its nodes, every tile position of the non-empty neighbouring bins
+// that maps onto the node (several positions when a periodic axis is shorter
+// than a tile), in a fixed order, and writes F = g + sum once.  Per axis a
+// table built once per block lists, for each local coordinate, the pairs
+// (neighbour slot, tile position) that land on it.
+constexpr int GATHER_MAXE = 2 * TILE;  // entries per (axis, local coordinate)
+template <typename R>
+__global__ void __launch_bounds__(256) spread_gather_kernel(View<R> v) {
+    __shared__ int nbin[27];  // bin of neighbour slot (sz*9 + sy*3 + sx), -1 if empty
+    __shared__ int lb[3][3], nsl[3];
+    __shared__ unsigned char cnt[3][BLK];
+    __shared__ unsigned char ent_slot[3][BLK][GATHER_MAXE], ent_pos[3][BLK][GATHER_MAXE];
+    const int k = blockIdx.x;
+    const int bc[3] = {k % v.nb[0], (k / v.nb[0]) % v.nb[1], k / (v.nb[0] * v.nb[1])};
+    const int dims[3] = {v.nx, v.ny, v.nz};
+    const int t = threadIdx.x;
+    if (t < 3) nsl[t] = neighbour_blocks(bc[t], v.nb[t], v.per[t], lb[t]);
+    __syncthreads();
+    if (t < 3 * BLK) {  // table of axis d, local coordinate l
+        const int d = t / BLK, l = t % BLK;
+        const int x = bc[d] * BLK + l;
+        int n = 0;
+        for (int sl = 0; sl < nsl[d]; ++sl) {
+            const int o = lb[d][sl] * BLK - 1;  // tile origin along d
+            if (v.per[d]) {
+                for (int p = wrap(x - o, dims[d]); p < TILE && n < GATHER_MAXE; p += dims[d]) {
+                    ent_slot[d][l][n] = (unsigned char)sl;
+                    ent_pos[d][l][n++] = (unsigned char)p;
+                }
+            } else if (x - o >= 0 && x - o < TILE) {
+                ent_slot[d][l][n] = (unsigned char)sl;
+                ent_pos[d][l][n++] = (unsigned char)(x - o);
+            }
         }
-        if (!ok) continue;  // vertex outside the lattice (domain status already raised)
-        R U[3] = {R(0), R(0), R(0)};
-        for (int c = 0; c < 4; ++c)
-            for (int b = 0; b < 4; ++b) {
-                const R wzy = w[2][c] * w[1][b];
-                const int row = (base[0]) + TILE * ((base[1] + b) + TILE * (base[2] + c));
+        cnt[d][l] = (unsigned char)n;
+    } else if (t >= 32 && t < 32 + 27) {  // neighbour slot -> bin
+        const int sl = t - 32, a = sl / 9, b = (sl / 3) % 3, c = sl % 3;
+        int kk = -1;
+        if (a < nsl[2] && b < nsl[1] && c < nsl[0]) {
+            kk = lb[0][c] + v.nb[0] * (lb[1][b] + v.nb[1] * lb[2][a]);
+            if (v.start[kk + 1] == v.start[kk]) kk = -1;
+        }
+        nbin[sl] = kk;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+    for (int q = t; q < BLK * BLK * BLK; q += blockDim.x) {
+        const int l0 = q % BLK, l1 = (q / BLK) % BLK, l2 = q / (BLK * BLK);
+        const int x = bc[0] * BLK + l0, y = bc[1] * BLK + l1, z = bc[2] * BLK + l2;
+        if (x >= v.nx || y >= v.ny || z >= v.nz) continue;
+        R f0 = R(0), f1 = R(0), f2 = R(0);
+        for (int iz = 0; iz < cnt[2][l2]; ++iz)
+            for (int iy = 0; iy < cnt[1][l1]; ++iy)
+                for (int ix = 0; ix < cnt[0][l0]; ++ix) {
+                    const int kk = nbin[9 * ent_slot[2][l2][iz] + 3 * ent_slot[1][l1][iy] + ent_slot[0][l0][ix]];
+                    if (kk < 0) continue;
+                    const R *tt = v.tiles + (size_t)kk * 3 * TILE3;
+                    const int ti = ent_pos[0][l0][ix] + TILE * (ent_pos[1][l1][iy] + TILE * ent_pos[2][l2][iz]);
+                    f0 += tt[ti];
+                    f1 += tt[TILE3 + ti];
+                    f2 += tt[2 * TILE3 + ti];
+                }
+        const size_t n = (size_t)x + (size_t)v.nx * ((size_t)y + (size_t)v.ny * z);
+        const bool wall = v.ntype[n] & 0x7f;
+        v.F[n] = wall ? R(0) : v.g[0] + f0;
+        v.F[N + n] = wall ? R(0) : v.g[1] + f1;
+        v.F[2 * N + n] = wall ? R(0) : v.g[2] + f2;
+    }
+}
+
+// Interpolation and Euler move: one CTA per non-empty bin stages u of the
+// 11^3 neighbourhood in shared memory (padded strides; lattice coordinates
+// of the tile's rows from per-axis tables built once); a warp takes two
+// vertices, each half-warp's lanes own one (y, z) stencil row, and the 16
+// partial sums are reduced with warp shuffles.
+template <typename R>
+__global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
+    constexpr int CAP = Stage<R>::CAP;
+    const int k = blockIdx.x;
+    const int s = v.start[k], e = v.start[k + 1];
+    if (s == e) return;
+    __shared__ R tile[3][TILE_SMEM];
+    __shared__ int srow[CAP], sperm[CAP];
+    __shared__ R sw[12 * CAP];
+    __shared__ int jtab[3][TILE];  // wrapped lattice coordinate, -1 beyond a non-periodic edge
+    int org[3];
+    bin_origin(v, k, org);
+    if (threadIdx.x < 3 * TILE) {
+        const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
+        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+        int j = org[d] - 1 + l;
+        if (v.per[d]) j = wrap(j, dims);
+        else if (j < 0 || j >= dims) j = -1;
+        jtab[d][l] = j;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+        const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
+        const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
+        const int sidx = l0 + TS_Y * l1 + TS_Z * l2;
+        if ((jx | jy | jz) < 0) {  // beyond a non-periodic edge: resting wall
+            tile[0][sidx] = tile[1][sidx] = tile[2][sidx] = R(0);
+        } else {
+            const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
+            tile[0][sidx] = v.u[n];
+            tile[1][sidx] = v.u[N + n];
+            tile[2][sidx] = v.u[2 * N + n];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
+    for (int c0 = s; c0 < e; c0 += CAP) {
+        const int n = min(CAP, e - c0);
+        if (c0 != s) __syncthreads();
+        stage_chunk(v, c0, n, org, srow, sw, (R *)nullptr, sperm);
+        __syncthreads();
+        for (int q0 = 2 * warp; q0 < n; q0 += 2 * nw) {  // uniform per warp: shuffles below
+            const int q = q0 + h;
+            R U0 = R(0), U1 = R(0), U2 = R(0);
+            const int row0 = q < n ? srow[q] : -1;
+            if (row0 >= 0) {
+                const R *w = sw + 12 * q;
+                const R wyz = w[4 + b] * w[8 + c];
+                const int row = row0 + TS_Y * b + TS_Z * c;
+#pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const R ww = wzy * w[0][a];
-                    U[0] += ww * tile[0][row + a];
-                    U[1] += ww * tile[1][row + a];
-                    U[2] += ww * tile[2][row + a];
+                    const R wa = wyz * w[a];
+                    U0 += wa * tile[0][row + a];
+                    U1 += wa * tile[1][row + a];
+                    U2 += wa * tile[2][row + a];
                 }
             }
-        const int vid = v.perm[p];
-        R *o = v.off + 3 * (size_t)vid;
-        o[0] += U[0];
-        o[1] += U[1];
-        o[2] += U[2];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                U0 += __shfl_xor_sync(0xffffffffu, U0, o);
+                U1 += __shfl_xor_sync(0xffffffffu, U1, o);
+                U2 += __shfl_xor_sync(0xffffffffu, U2, o);
+            }
+            if (row0 >= 0 && (lane & 15) == 0) {
+                R *o = v.off + 3 * (size_t)sperm[q];
+                o[0] += U0;
+                o[1] += U1;
+                o[2] += U2;
+            }
+        }
     }
 }
 
@@ -302,22 +484,22 @@ __global__ void set_vertices_kernel(View<R> v, const double *X) {
 }  // namespace
 
 template <typename R>
-void launch_bins(const View<R> &v, cudaStream_t st) {
+void launch_bins(const View<R> &v, cudaStream_t st, bool stable) {
     cudaMemsetAsync(v.counts, 0, sizeof(int) * v.nbins, st);
     anchor_count_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v);
     scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins);
-    scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm_raw, v.nv);
-    sort_bins_kernel<<<nblocks((long long)v.nbins * 32, 128), 128, 0, st>>>(v.start, v.perm_raw, v.perm, v.nbins);
-}
-
-template <typename R>
-void launch_gather(const View<R> &v, cudaStream_t st) {
-    gather_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v);
+    if (stable) {
+        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm_raw, v.nv);
+        sort_bins_kernel<<<nblocks((long long)v.nbins * 32, 128), 128, 0, st>>>(v.start, v.perm_raw, v.perm, v.nbins);
+    } else {
+        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv);
+    }
 }
 
 template <typename R>
 void launch_spread(const View<R> &v, cudaStream_t st) {
-    spread_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    spread_tile_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    spread_gather_kernel<R><<<v.nbins, 256, 0, st>>>(v);
 }
 
 template <typename R>
@@ -336,8 +518,7 @@ void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st) {
 }
 
 #define HEMO_INST(R)                                                                      \
-    template void launch_bins<R>(const View<R> &, cudaStream_t);                          \
-    template void launch_gather<R>(const View<R> &, cudaStream_t);                        \
+    template void launch_bins<R>(const View<R> &, cudaStream_t, bool);                    \
     template void launch_spread<R>(const View<R> &, cudaStream_t);                        \
     template void launch_interpolate<R>(const View<R> &, cudaStream_t);                   \
     template void launch_verts_out<R>(const View<R> &, double *, double *, cudaStream_t); \

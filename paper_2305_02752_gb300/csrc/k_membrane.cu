@@ -6,7 +6,10 @@
 // (centroid += mean offset, offsets -= mean, so the FP32 offsets stay small
 // while the FP64 centroid carries the position), sums area and volume over
 // the triangles in FP64, and accumulates the four force terms per vertex in
-// shared memory before one coalesced write.  Energies (forms documented in
+// shared memory before one coalesced write.  The edge and triangle tables
+// arrive in a processing order permuted on the host so that the lanes of a
+// warp work on parts of the mesh far apart (fewer colliding shared-memory
+// atomics) while the table loads stay coalesced.  Energies (forms documented in
 // hemo.h):
 //   link   K L0 [eps^2/2 - 1/2 ln(1 - eps^2/m^2)],   eps = (L - L0)/L0
 //   bend   1/2 kb (theta - theta0)^2, theta = signed angle between the
