@@ -112,7 +112,7 @@ struct hemo_sim {
     std::vector<HostMesh> meshes;
     std::vector<int> cell_type, cell_first, vcell;
     std::vector<double> X0;
-    int nv = 0, ncell = 0, max_nv = 0;
+    int nv = 0, ncell = 0, max_nv = 0, max_nt = 0;
     bool finalized = false;
     long long steps_done = 0;
     // device cells and bins
@@ -223,6 +223,7 @@ View<R> make_view(hemo_sim *s) {
     v.cell_type = s->cell_type_d;
     v.meshes = (const MeshDev<R> *)s->meshes_d;
     v.max_nv = s->max_nv;
+    v.max_nt = s->max_nt;
     for (int d = 0; d < 3; ++d) v.nb[d] = s->nb[d];
     v.nbins = s->nbins;
     v.key = s->key;
@@ -295,27 +296,39 @@ int finalize_impl(hemo_sim *s) {
         const HostMesh &m = s->meshes[t];
         int *dtri = (int *)dalloc(s, sizeof(int) * m.tri.size());
         int *dedge = (int *)dalloc(s, sizeof(int) * m.edge.size());
+        int *detri = (int *)dalloc(s, sizeof(int) * 2 * (size_t)m.ne);
         R *dL0 = (R *)dalloc(s, rs * m.ne);
         R *dth0 = (R *)dalloc(s, rs * m.ne);
-        if (!dtri || !dedge || !dL0 || !dth0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        if (!dtri || !dedge || !detri || !dL0 || !dth0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
         // processing order: item q is q * stride mod n (stride coprime with
         // n, about n/32), so a warp's lanes work on far-apart mesh parts
         const int se = coprime_stride(m.ne), st3 = coprime_stride(m.nt);
-        std::vector<int> edge_p(4 * (size_t)m.ne), tri_p(3 * (size_t)m.nt);
-        std::vector<R> L0(m.ne), th0(m.ne);
-        for (int q = 0; q < m.ne; ++q) {
-            const int e = (int)(((long long)q * se) % m.ne);
-            for (int j = 0; j < 4; ++j) edge_p[4 * (size_t)q + j] = m.edge[4 * (size_t)e + j];
-            L0[q] = R(m.L0[e]);
-            th0[q] = R(m.th0[e]);
-        }
+        std::vector<int> edge_p(4 * (size_t)m.ne), tri_p(3 * (size_t)m.nt), tpos(m.nt), etri_p(2 * (size_t)m.ne);
+        std::vector<R> invL0(m.ne), th0(m.ne);
         for (int q = 0; q < m.nt; ++q) {
             const int t = (int)(((long long)q * st3) % m.nt);
             for (int j = 0; j < 3; ++j) tri_p[3 * (size_t)q + j] = m.tri[3 * (size_t)t + j];
+            tpos[t] = q;
+        }
+        // triangle of each directed edge: (v0, v1) -> triangle containing it
+        std::unordered_map<long long, int> dir_tri;
+        dir_tri.reserve(3 * (size_t)m.nt);
+        for (int t = 0; t < m.nt; ++t)
+            for (int k = 0; k < 3; ++k)
+                dir_tri[(long long)m.tri[3 * t + k] * m.nv + m.tri[3 * t + (k + 1) % 3]] = t;
+        for (int q = 0; q < m.ne; ++q) {
+            const int e = (int)(((long long)q * se) % m.ne);
+            const int *E = &m.edge[4 * (size_t)e];
+            for (int j = 0; j < 4; ++j) edge_p[4 * (size_t)q + j] = E[j];
+            etri_p[2 * (size_t)q] = tpos[dir_tri.at((long long)E[0] * m.nv + E[1])];
+            etri_p[2 * (size_t)q + 1] = tpos[dir_tri.at((long long)E[1] * m.nv + E[0])];
+            invL0[q] = R(1.0 / m.L0[e]);
+            th0[q] = R(m.th0[e]);
         }
         HEMO_CU(cudaMemcpy(dtri, tri_p.data(), sizeof(int) * tri_p.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dedge, edge_p.data(), sizeof(int) * edge_p.size(), cudaMemcpyHostToDevice));
-        HEMO_CU(cudaMemcpy(dL0, L0.data(), rs * m.ne, cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(detri, etri_p.data(), sizeof(int) * etri_p.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dL0, invL0.data(), rs * m.ne, cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dth0, th0.data(), rs * m.ne, cudaMemcpyHostToDevice));
         MeshDev<R> d{};
         d.nv = m.nv;
@@ -323,7 +336,8 @@ int finalize_impl(hemo_sim *s) {
         d.ne = m.ne;
         d.tri = dtri;
         d.edge = dedge;
-        d.L0 = dL0;
+        d.etri = detri;
+        d.invL0 = dL0;
         d.th0 = dth0;
         d.A0 = m.A0;
         d.V0 = m.V0;
@@ -355,7 +369,7 @@ int finalize_impl(hemo_sim *s) {
         HEMO_CU(cudaMemcpy(s->cell_first_d, s->cell_first.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(s->cell_type_d, s->cell_type.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
     }
-    const size_t smem = cell_smem_bytes<R>(s->max_nv);
+    const size_t smem = cell_smem_bytes<R>(s->max_nv, s->max_nt);
     if (smem > 48 * 1024) HEMO_CU(set_cell_smem_limit<R>(smem));
     if (!nc) {  // no cells: the force field is the body force, written once
         View<R> v = make_view<R>(s);
@@ -581,6 +595,7 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     const int type = (int)s->meshes.size();
     s->meshes.push_back(hm);
     s->max_nv = std::max(s->max_nv, hm.nv);
+    s->max_nt = std::max(s->max_nt, hm.nt);
     if (first_cell_id) *first_cell_id = s->ncell;
     for (int k = 0; k < ncells; ++k) {
         const double *R = rot + 9 * (size_t)k;

@@ -67,8 +67,9 @@ template <typename R> struct MeshDev {
     int nv, nt, ne;
     const int *tri;     // nt*3, in processing order
     const int *edge;    // ne*4: v0, v1, a, b, in processing order
-    const R *L0;        // ne
-    const R *th0;       // ne
+    const int *etri;    // ne*2: the triangles (v0, v1, a) and (v1, v0, b), processing positions
+    const R *invL0;     // ne: 1 / rest length
+    const R *th0;       // ne: rest dihedral angle
     double A0, V0;
     R K;                // k_link * kbt / persistence
     R m2;               // max_strain^2
@@ -99,6 +100,7 @@ template <typename R> struct View {
     const int *cell_type;      // ncell
     const MeshDev<R> *meshes;  // per type
     int max_nv;                // largest vertex count of a mesh type
+    int max_nt;                // largest triangle count of a mesh type
     // bins
     int nb[3];
     int nbins;
@@ -125,7 +127,7 @@ void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, 
 
 template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
 template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
-template <typename R> size_t cell_smem_bytes(int max_nv) { return 6 * (size_t)max_nv * sizeof(R); }
+template <typename R> size_t cell_smem_bytes(int max_nv, int max_nt) { return (6 * (size_t)max_nv + 4 * (size_t)max_nt) * sizeof(R); }
 template <typename R> void launch_bins(const View<R> &v, cudaStream_t st, bool stable);
 template <typename R> void launch_spread(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st);

@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
     const int first = v.cell_first[c];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *xs = reinterpret_cast<R *>(smem_raw);  // nv*3 positions relative to the centroid
-    R *fs = xs + 3 * m.nv;                      // nv*3 force accumulators
+    R *fs = xs + 3 * v.max_nv;                  // nv*3 force accumulators
+    R *tn = fs + 3 * v.max_nv;                  // nt*4 triangle normal n and 1/|n|^2
     __shared__ double scratch[6][32];
 
     // mean offset (FP64)
@@ -123,15 +124,21 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
         for (int k = 0; k < 3; ++k) v.ctr[3 * c + k] += mean[k];
     __syncthreads();
 
-    // area and volume: per-triangle terms in R, sums in FP64
+    // per triangle: normal n = (x1 - x0) x (x2 - x0) kept in shared memory;
+    // area and volume terms in R, their sums in FP64
     double av[2] = {0, 0};
     for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
         const V3<R> p0 = ld3(xs + 3 * m.tri[3 * t]), p1 = ld3(xs + 3 * m.tri[3 * t + 1]), p2 = ld3(xs + 3 * m.tri[3 * t + 2]);
         const V3<R> n = cross(p1 - p0, p2 - p0);
-        av[0] += 0.5 * (double)sqrt_r(dot(n, n));
+        const R q = dot(n, n);
+        tn[4 * t] = n.x;
+        tn[4 * t + 1] = n.y;
+        tn[4 * t + 2] = n.z;
+        tn[4 * t + 3] = R(1) / q;
+        av[0] += 0.5 * (double)sqrt_r(q);
         av[1] += (double)dot(p0, cross(p1, p2)) / 6.0;
     }
-    block_sum<2>(av, scratch);
+    block_sum<2>(av, scratch);  // (synchronises: tn is complete below)
     const double A = av[0], V = av[1];
 
     if (mode == 1) {
@@ -157,29 +164,30 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
         return;
     }
 
-    // link and bending, one edge per thread
+    // link and bending, one edge per thread; the normals of the edge's two
+    // triangles (v0, v1, a) and (v1, v0, b) come from the triangle pass
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
         const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
+        const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
         const V3<R> p0 = ld3(xs + 3 * i0), p1 = ld3(xs + 3 * i1), pa = ld3(xs + 3 * ia), pb = ld3(xs + 3 * ib);
         const V3<R> ed = p1 - p0;
         const R L = sqrt_r(dot(ed, ed));
-        const R L0 = m.L0[e];
-        const R eps = (L - L0) / L0;
+        const R iL = R(1) / L;
+        const R eps = L * m.invL0[e] - R(1);
         const R den = m.m2 - eps * eps;
         if (!(den > R(0))) atomicOr(v.status, ST_NUMERIC);
         const R dEdL = m.K * (eps + eps / den);
-        const V3<R> fl = (dEdL / L) * ed;  // force on v0 (towards v1 when stretched)
+        const V3<R> fl = (dEdL * iL) * ed;  // force on v0 (towards v1 when stretched)
         sub_into(fs + 3 * i0, R(-1) * fl);
         sub_into(fs + 3 * i1, fl);
 
-        const V3<R> da = pa - p0, db = pb - p0;
-        const V3<R> n1 = cross(ed, da), n2 = cross(db, ed);
-        const R q1 = dot(n1, n1), q2 = dot(n2, n2);
-        const R th = atan2_r(dot(cross(n1, n2), ed) / L, dot(n1, n2));
+        const V3<R> n1 = ld3(tn + 4 * t1), n2 = ld3(tn + 4 * t2);
+        const V3<R> a1 = tn[4 * t1 + 3] * n1, a2 = tn[4 * t2 + 3] * n2;  // n / |n|^2
+        const R th = atan2_r(dot(cross(n1, n2), ed) * iL, dot(n1, n2));
         const R cb = m.kb * (th - m.th0[e]);
-        const V3<R> a1 = (R(1) / q1) * n1, a2 = (R(1) / q2) * n2;
-        const R sa0 = dot(pa - p1, ed) / L, sb0 = dot(pb - p1, ed) / L;
-        const R sa1 = dot(da, ed) / L, sb1 = dot(db, ed) / L;
+        const V3<R> da = pa - p0, db = pb - p0;
+        const R sa0 = dot(pa - p1, ed) * iL, sb0 = dot(pb - p1, ed) * iL;
+        const R sa1 = dot(da, ed) * iL, sb1 = dot(db, ed) * iL;
         sub_into(fs + 3 * ia, (-cb * L) * a1);
         sub_into(fs + 3 * ib, (-cb * L) * a2);
         sub_into(fs + 3 * i0, cb * (R(-1) * (sa0 * a1 + sb0 * a2)));
@@ -192,8 +200,7 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
     for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
         const int j0 = m.tri[3 * t], j1 = m.tri[3 * t + 1], j2 = m.tri[3 * t + 2];
         const V3<R> p0 = ld3(xs + 3 * j0), p1 = ld3(xs + 3 * j1), p2 = ld3(xs + 3 * j2);
-        const V3<R> n = cross(p1 - p0, p2 - p0);
-        const V3<R> nh = (R(1) / sqrt_r(dot(n, n))) * n;
+        const V3<R> nh = sqrt_r(tn[4 * t + 3]) * ld3(tn + 4 * t);  // unit normal
         const R ha = R(0.5) * ca, sv = cv / R(6);
         sub_into(fs + 3 * j0, ha * cross(nh, p2 - p1) + sv * cross(p1, p2));
         sub_into(fs + 3 * j1, ha * cross(nh, p0 - p2) + sv * cross(p2, p0));
@@ -209,7 +216,7 @@ template <typename R>
 void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st) {
     if (v.ncell == 0) return;
     // positions and force accumulators of the largest mesh type
-    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv), st>>>(v, mode, stats);
+    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv, v.max_nt), st>>>(v, mode, stats);
 }
 
 template <typename R>
