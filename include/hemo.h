@@ -181,6 +181,41 @@ int hemo_set_vertices(hemo_sim *sim, const double *verts);
  * key, perm: any, nv int32; start: any, nbins+1 int32.  Synchronises. */
 int hemo_get_bins(hemo_sim *sim, int32_t *key, int32_t *perm, int32_t *start);
 
+/* ---- differentiation form --------------------------------------------- */
+
+/* Start recording for hemo_backward: checkpoint the full state (populations,
+ * centroids, vertex offsets) now and every `checkpoint_every` steps after
+ * (even, >= 2), and take the current cell centroids as the reference of the
+ * loss's drift term.  The current step count must be even.  Checkpoints are
+ * device memory owned by the library: (steps / checkpoint_every + 1) copies
+ * of the state. */
+int hemo_record(hemo_sim *sim, int checkpoint_every);
+
+/* Deformation loss of the current vertices (its own definition; the paper
+ * gives none): the mean over cells of the Taylor deformation index
+ * (sqrt(l1) - sqrt(l3)) / (sqrt(l1) + sqrt(l3)) of the gyration tensor
+ * G = mean_v (X_v - c)(X_v - c)^T (eigenvalues l1 >= l2 >= l3) plus
+ * |c - c_ref|^2 (c_ref: centroids at hemo_record, else at the first call).
+ * loss: host, 1 double; dL_dverts: any, nv*3 doubles, or NULL.
+ * Synchronises. */
+int hemo_deformation_loss(hemo_sim *sim, double *loss, double *dL_dverts);
+
+/* Reverse-mode gradient of a loss of the final vertex positions, given
+ * dL_dverts = dL/dX at the current step (any, nv*3 doubles), with respect to
+ * the parameters of the steps recorded since hemo_record: grad (host,
+ * ngrad >= 4 * mesh types + 4 doubles) receives, per mesh type t in the
+ * order added, dL/dk_link, dL/dk_bend, dL/dk_area, dL/dk_volume at
+ * 4t..4t+3, then dL/ds for a common scale s of both wall velocities, then
+ * dL/dg (3).  Each step is differentiated exactly as computed: the
+ * adjoint of the interpolation and Euler move, of the post-streaming
+ * velocity, of streaming with bounce-back, of the BGK collision with the
+ * force term, of the spreading, and of the membrane forces (a Hessian-vector
+ * product).  Segments between checkpoints are recomputed forward, keeping
+ * each step's populations and positions, then swept backwards; gradients
+ * accumulate in FP64.  The state after the call is the state before it.
+ * Synchronises. */
+int hemo_backward(hemo_sim *sim, const double *dL_dverts, double *grad, int ngrad);
+
 /* ---- measurement ------------------------------------------------------ */
 
 /* Phases of one step, in order. */

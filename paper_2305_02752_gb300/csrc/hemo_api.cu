@@ -92,6 +92,16 @@ int coprime_stride(int n) {
 
 void hemo::set_last_error(const char *msg) { g_err = msg; }
 
+// device buffers of the reverse sweep (grown on demand, kept for reuse)
+struct AdjBuffers {
+    void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr, *up = nullptr, *rhop = nullptr;
+    void *lamX = nullptr, *lamFv = nullptr, *grad = nullptr, *seg_f = nullptr, *seg_ctr = nullptr, *seg_off = nullptr;
+    void *fin_f = nullptr, *fin_u = nullptr, *fin_ctr = nullptr, *fin_off = nullptr, *cell_loss = nullptr, *dldx = nullptr;
+    size_t sz_lamf_in = 0, sz_lamf_out = 0, sz_lamu = 0, sz_lamF = 0, sz_up = 0, sz_rhop = 0, sz_lamX = 0, sz_lamFv = 0;
+    size_t sz_grad = 0, sz_seg_f = 0, sz_seg_ctr = 0, sz_seg_off = 0, sz_fin_f = 0, sz_fin_u = 0, sz_fin_ctr = 0;
+    size_t sz_fin_off = 0, sz_cell_loss = 0, sz_dldx = 0;
+};
+
 struct hemo_sim {
     int precision = 0;
     int nx = 0, ny = 0, nz = 0;
@@ -141,6 +151,13 @@ struct hemo_sim {
     bool timing = false;
     cudaEvent_t tev[HEMO_NUM_PHASES + 1] = {};
     int kernels_per_step = 0;
+    // differentiation form
+    bool rec = false;
+    int ck_every = 0;
+    long long rec_start = 0;
+    std::vector<void *> ck_f, ck_ctr, ck_off;
+    double *c0 = nullptr;
+    AdjBuffers adj;
 };
 
 namespace {
@@ -346,6 +363,10 @@ int finalize_impl(hemo_sim *s) {
         d.kb = R(m.k_bend * m.kbt);
         d.k_area = m.k_area;
         d.k_volume = m.k_volume;
+        d.Ku = R(m.kbt / m.persistence);
+        d.kbu = R(m.kbt);
+        d.k_link = R(m.k_link);
+        d.k_bend = R(m.k_bend);
         md[t] = d;
     }
     HEMO_CU(cudaMemcpy(s->meshes_d, md.data(), sizeof(MeshDev<R>) * MAX_TYPES, cudaMemcpyHostToDevice));
@@ -371,6 +392,8 @@ int finalize_impl(hemo_sim *s) {
     }
     const size_t smem = cell_smem_bytes<R>(s->max_nv, s->max_nt);
     if (smem > 48 * 1024) HEMO_CU(set_cell_smem_limit<R>(smem));
+    const size_t smem_adj = cell_adjoint_smem_bytes<R>(s->max_nv, s->max_nt);
+    if (smem_adj > 48 * 1024) HEMO_CU(set_cell_adjoint_smem_limit<R>(smem_adj));
     if (!nc) {  // no cells: the force field is the body force, written once
         View<R> v = make_view<R>(s);
         launch_spread<R>(v, st);
@@ -432,6 +455,254 @@ int copy_out(hemo_sim *s, void *dst, const void *src, size_t bytes) {
 }
 
 }  // namespace
+
+
+// ---------------------------------------------------------------------------
+// differentiation form: checkpoints, loss, reverse sweep
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A *in, B *out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (B)in[i];
+}
+
+template <typename A, typename B>
+void convert(const A *in, B *out, size_t n, cudaStream_t st) {
+    if (n) convert_kernel<A, B><<<(int)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+}
+
+size_t lat_bytes(const hemo_sim *s) { return rsize(s) * Q * (size_t)s->N; }
+
+// reference centroids of the loss's drift term := current centroids
+template <typename R>
+int set_reference_centroids(hemo_sim *s) {
+    if (!s->ncell) return HEMO_OK;
+    int rc = ensure_staging(s, sizeof(double) * 6 * (size_t)s->ncell);
+    if (rc) return rc;
+    launch_cell_forces<R>(make_view<R>(s), 1, (double *)s->staging, s->stream);
+    std::vector<double> st(6 * (size_t)s->ncell), c0(3 * (size_t)s->ncell);
+    HEMO_CU(cudaMemcpyAsync(st.data(), s->staging, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, s->stream));
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < s->ncell; ++c)
+        for (int k = 0; k < 3; ++k) c0[3 * c + k] = st[6 * c + k];
+    if (!s->c0) s->c0 = (double *)dalloc(s, sizeof(double) * c0.size());
+    if (!s->c0) return fail(HEMO_ERR_OOM, "allocation of reference centroids failed");
+    HEMO_CU(cudaMemcpy(s->c0, c0.data(), sizeof(double) * c0.size(), cudaMemcpyHostToDevice));
+    return HEMO_OK;
+}
+
+template <typename R>
+int save_checkpoint(hemo_sim *s) {
+    const size_t k = (size_t)((s->steps_done - s->rec_start) / s->ck_every);
+    while (s->ck_f.size() <= k) {
+        void *f = dalloc(s, lat_bytes(s));
+        void *c = dalloc(s, sizeof(double) * 3 * std::max(s->ncell, 1));
+        void *o = dalloc(s, rsize(s) * 3 * std::max(s->nv, 1));
+        if (!f || !c || !o) return fail(HEMO_ERR_OOM, "checkpoint allocation failed");
+        s->ck_f.push_back(f);
+        s->ck_ctr.push_back(c);
+        s->ck_off.push_back(o);
+    }
+    View<R> v = make_view<R>(s);
+    launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), (R *)s->ck_f[k], s->stream);
+    HEMO_CU(cudaMemcpyAsync(s->ck_ctr[k], s->ctr, sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, s->stream));
+    HEMO_CU(cudaMemcpyAsync(s->ck_off[k], s->off, rsize(s) * 3 * s->nv, cudaMemcpyDeviceToDevice, s->stream));
+    HEMO_CU(cudaGetLastError());
+    return HEMO_OK;
+}
+
+void *grow(hemo_sim *s, void *&p, size_t &have, size_t need) {
+    if (have >= need && p) return p;
+    dfree(s, p);
+    p = dalloc(s, need);
+    have = p ? need : 0;
+    return p;
+}
+
+template <typename R>
+int backward_impl(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad) {
+    const int nt = (int)s->meshes.size();
+    const int ng = 4 * nt + 4;
+    const long long t_end = s->steps_done;
+    const int K = s->ck_every;
+    const size_t N = (size_t)s->N, nv = (size_t)s->nv, rs = sizeof(R);
+    cudaStream_t st = s->stream;
+    int rc;
+    HEMO_CU(cudaStreamSynchronize(st));
+    // buffers (kept for reuse)
+    AdjBuffers &b = s->adj;
+    if (!grow(s, b.lamf_in, b.sz_lamf_in, rs * Q * N) || !grow(s, b.lamf_out, b.sz_lamf_out, rs * Q * N) ||
+        !grow(s, b.lamu, b.sz_lamu, rs * 3 * N) || !grow(s, b.lamF, b.sz_lamF, rs * 3 * N) ||
+        !grow(s, b.up, b.sz_up, rs * 3 * N) || !grow(s, b.rhop, b.sz_rhop, rs * N) ||
+        !grow(s, b.lamX, b.sz_lamX, rs * 3 * std::max<size_t>(nv, 1)) ||
+        !grow(s, b.lamFv, b.sz_lamFv, rs * 3 * std::max<size_t>(nv, 1)) ||
+        !grow(s, b.grad, b.sz_grad, sizeof(double) * ng) ||
+        !grow(s, b.seg_f, b.sz_seg_f, rs * Q * N * (size_t)(K + 1)) ||
+        !grow(s, b.seg_ctr, b.sz_seg_ctr, sizeof(double) * 3 * std::max(s->ncell, 1) * (size_t)K) ||
+        !grow(s, b.seg_off, b.sz_seg_off, rs * 3 * std::max<size_t>(nv, 1) * (size_t)K) ||
+        !grow(s, b.fin_f, b.sz_fin_f, rs * Q * N) || !grow(s, b.fin_u, b.sz_fin_u, rs * 3 * N) ||
+        !grow(s, b.fin_ctr, b.sz_fin_ctr, sizeof(double) * 3 * std::max(s->ncell, 1)) ||
+        !grow(s, b.fin_off, b.sz_fin_off, rs * 3 * std::max<size_t>(nv, 1)))
+        return fail(HEMO_ERR_OOM, "allocation of adjoint buffers failed");
+    View<R> v = make_view<R>(s);
+    // final state, restored at the end
+    launch_copy_natural<R>(v, s->precision, (int)(t_end & 1), (R *)b.fin_f, st);
+    HEMO_CU(cudaMemcpyAsync(b.fin_u, s->u, rs * 3 * N, cudaMemcpyDeviceToDevice, st));
+    HEMO_CU(cudaMemcpyAsync(b.fin_ctr, s->ctr, sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, st));
+    HEMO_CU(cudaMemcpyAsync(b.fin_off, s->off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
+    // adjoint of the final state: dL/dX_T given, dL/df_T = 0
+    if (nv) {
+        if ((rc = ensure_staging(s, sizeof(double) * 3 * nv))) return rc;
+        HEMO_CU(cudaMemcpyAsync(s->staging, dL_dverts, sizeof(double) * 3 * nv, cudaMemcpyDefault, st));
+        convert<double, R>((const double *)s->staging, (R *)b.lamX, 3 * nv, st);
+    }
+    HEMO_CU(cudaMemsetAsync(b.lamf_in, 0, rs * Q * N, st));
+    HEMO_CU(cudaMemsetAsync(b.grad, 0, sizeof(double) * ng, st));
+    HEMO_CU(cudaMemcpyAsync(b.up, s->u, rs * 3 * N, cudaMemcpyDeviceToDevice, st));  // wall velocity at walls
+    AdjView<R> a{};
+    a.lamf_in = (R *)b.lamf_in;
+    a.lamf_out = (R *)b.lamf_out;
+    a.lamu = (R *)b.lamu;
+    a.lamF = (R *)b.lamF;
+    a.up = (R *)b.up;
+    a.rhop = (R *)b.rhop;
+    a.lamX = (R *)b.lamX;
+    a.lamFv = (R *)b.lamFv;
+    a.grad = (double *)b.grad;
+    a.ntypes = nt;
+    View<R> vl = v;  // spreading of lamX into lamu at every node
+    vl.Fv = a.lamX;
+    vl.F = a.lamu;
+    vl.g[0] = vl.g[1] = vl.g[2] = R(0);
+    vl.spread_all_nodes = 1;
+    const long long nseg = (t_end - s->rec_start + K - 1) / K;
+    R *segf = (R *)b.seg_f;
+    for (long long seg = nseg - 1; seg >= 0; --seg) {
+        const long long s0 = s->rec_start + seg * K, s1 = std::min<long long>(s0 + K, t_end);
+        const int len = (int)(s1 - s0);
+        // forward recomputation of the segment from its checkpoint
+        launch_restore_natural<R>(v, s->precision, 0, (const R *)s->ck_f[seg], st);
+        HEMO_CU(cudaMemcpyAsync(s->ctr, s->ck_ctr[seg], sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, st));
+        HEMO_CU(cudaMemcpyAsync(s->off, s->ck_off[seg], rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
+        s->steps_done = s0;
+        for (int j = 0; j < len; ++j) {
+            HEMO_CU(cudaMemcpyAsync((double *)b.seg_ctr + 3 * (size_t)s->ncell * j, s->ctr, sizeof(double) * 3 * s->ncell,
+                                    cudaMemcpyDeviceToDevice, st));
+            HEMO_CU(cudaMemcpyAsync((R *)b.seg_off + 3 * nv * j, s->off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
+            launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), segf + Q * N * j, st);
+            HEMO_CU(cudaGraphLaunch(s->graph[s->steps_done & 1], st));
+            ++s->steps_done;
+        }
+        launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), segf + Q * N * len, st);
+        // reverse sweep over the segment
+        for (int j = len - 1; j >= 0; --j) {
+            HEMO_CU(cudaMemcpyAsync(s->ctr, (double *)b.seg_ctr + 3 * (size_t)s->ncell * j, sizeof(double) * 3 * s->ncell,
+                                    cudaMemcpyDeviceToDevice, st));
+            HEMO_CU(cudaMemcpyAsync(s->off, (R *)b.seg_off + 3 * nv * j, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
+            a.fn = segf + Q * N * j;
+            a.fn1 = segf + Q * N * (j + 1);
+            if (s->ncell) {
+                launch_cell_forces<R>(v, 0, nullptr, st);  // F_v at X_n
+                launch_bins<R>(v, st, false);
+                launch_spread<R>(v, st);                   // F_n
+            }
+            launch_adj_rho_u<R>(v, a, st);                 // rho', u' of f_{n+1} with F_n
+            if (s->ncell) {
+                launch_spread<R>(vl, st);                                  // lamu = S lamX
+                launch_vertex_field<R>(v, a.up, a.lamX, a.lamX, nullptr, st);  // + (u' . lamX) grad w
+            } else {
+                HEMO_CU(cudaMemsetAsync(a.lamu, 0, rs * 3 * N, st));
+            }
+            launch_adj_moments<R>(v, a, st);
+            launch_adj_collide<R>(v, a, st);
+            if (s->ncell) {
+                launch_vertex_field<R>(v, a.lamF, v.Fv, a.lamX, a.lamFv, st);  // lamFv = I lamF; + (F_v . lamF) grad w
+                launch_cell_adjoint<R>(v, a, st);                              // + Hessian lamFv; moduli
+            }
+            std::swap(a.lamf_in, a.lamf_out);
+        }
+        HEMO_CU(cudaGetLastError());
+    }
+    // restore the final state
+    launch_restore_natural<R>(v, s->precision, (int)(t_end & 1), (const R *)b.fin_f, st);
+    HEMO_CU(cudaMemcpyAsync(s->u, b.fin_u, rs * 3 * N, cudaMemcpyDeviceToDevice, st));
+    HEMO_CU(cudaMemcpyAsync(s->ctr, b.fin_ctr, sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, st));
+    HEMO_CU(cudaMemcpyAsync(s->off, b.fin_off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
+    s->steps_done = t_end;
+    std::vector<double> g(ng);
+    HEMO_CU(cudaMemcpyAsync(g.data(), b.grad, sizeof(double) * ng, cudaMemcpyDeviceToHost, st));
+    HEMO_CU(cudaStreamSynchronize(st));
+    HEMO_CU(cudaGetLastError());
+    for (int k = 0; k < std::min(ng, ngrad); ++k) grad[k] = g[k];
+    return status_code(s->sticky);
+}
+
+template <typename R>
+int loss_impl(hemo_sim *s, double *loss, double *dL_dverts) {
+    const size_t nv = (size_t)s->nv;
+    int rc;
+    if (!s->c0 && (rc = set_reference_centroids<R>(s))) return rc;
+    AdjBuffers &b = s->adj;
+    if (!grow(s, b.cell_loss, b.sz_cell_loss, sizeof(double) * std::max(s->ncell, 1)) ||
+        !grow(s, b.dldx, b.sz_dldx, sizeof(R) * 3 * std::max<size_t>(nv, 1)))
+        return fail(HEMO_ERR_OOM, "allocation of loss buffers failed");
+    if ((rc = ensure_staging(s, sizeof(double) * 3 * std::max<size_t>(nv, 1)))) return rc;
+    launch_deformation_loss<R>(make_view<R>(s), s->c0, (double *)b.cell_loss, (R *)b.dldx, s->stream);
+    std::vector<double> cl(s->ncell);
+    HEMO_CU(cudaMemcpyAsync(cl.data(), b.cell_loss, sizeof(double) * cl.size(), cudaMemcpyDeviceToHost, s->stream));
+    if (dL_dverts && nv) {
+        convert<R, double>((const R *)b.dldx, (double *)s->staging, 3 * nv, s->stream);
+        HEMO_CU(cudaMemcpyAsync(dL_dverts, s->staging, sizeof(double) * 3 * nv, cudaMemcpyDefault, s->stream));
+    }
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    HEMO_CU(cudaGetLastError());
+    double L = 0;
+    for (double x : cl) L += x;
+    if (loss) *loss = s->ncell ? L / s->ncell : 0.0;
+    return HEMO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hemo_record(hemo_sim *s, int checkpoint_every) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (checkpoint_every < 2 || (checkpoint_every & 1)) return fail(HEMO_ERR_ARG, "checkpoint_every must be even and >= 2");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->steps_done & 1) return fail(HEMO_ERR_STATE, "hemo_record: start at an even step count");
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    s->rec = true;
+    s->ck_every = checkpoint_every;
+    s->rec_start = s->steps_done;
+    rc = is_f64(s) ? set_reference_centroids<double>(s) : set_reference_centroids<float>(s);
+    if (rc) return rc;
+    rc = is_f64(s) ? save_checkpoint<double>(s) : save_checkpoint<float>(s);
+    if (rc) return rc;
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    return HEMO_OK;
+}
+
+int hemo_deformation_loss(hemo_sim *s, double *loss, double *dL_dverts) {
+    if (!s || !loss) return fail(HEMO_ERR_ARG, "null pointer");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    return is_f64(s) ? loss_impl<double>(s, loss, dL_dverts) : loss_impl<float>(s, loss, dL_dverts);
+}
+
+int hemo_backward(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad) {
+    if (!s || !grad || (s->nv && !dL_dverts)) return fail(HEMO_ERR_ARG, "null pointer");
+    if (ngrad < 4 * (int)s->meshes.size() + 4) return fail(HEMO_ERR_ARG, "grad needs 4 * mesh types + 4 entries");
+    if (!s->rec || s->steps_done <= s->rec_start) return fail(HEMO_ERR_STATE, "hemo_backward: nothing recorded (hemo_record, then hemo_step)");
+    int rc = poll_status(s);
+    if (rc) return rc;
+    return is_f64(s) ? backward_impl<double>(s, dL_dverts, grad, ngrad) : backward_impl<float>(s, dL_dverts, grad, ngrad);
+}
+
+}  // extern "C"
 
 // ===========================================================================
 // C ABI
@@ -628,6 +899,10 @@ int hemo_step(hemo_sim *s, int nsteps) {
     for (int k = 0; k < nsteps; ++k) {
         HEMO_CU(cudaGraphLaunch(s->graph[s->steps_done & 1], s->stream));
         ++s->steps_done;
+        if (s->rec && (s->steps_done - s->rec_start) % s->ck_every == 0) {
+            rc = is_f64(s) ? save_checkpoint<double>(s) : save_checkpoint<float>(s);
+            if (rc) return rc;
+        }
     }
     HEMO_CU(cudaMemcpyAsync(s->status_host, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
     HEMO_CU(cudaEventRecord(s->ev, s->stream));

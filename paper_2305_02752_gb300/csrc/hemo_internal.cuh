@@ -75,6 +75,9 @@ template <typename R> struct MeshDev {
     R m2;               // max_strain^2
     R kb;               // k_bend * kbt
     double k_area, k_volume;
+    R Ku;               // kbt / persistence (link coefficient per unit k_link)
+    R kbu;              // kbt (bending coefficient per unit k_bend)
+    R k_link, k_bend;
 };
 
 template <typename R> struct View {
@@ -113,7 +116,26 @@ template <typename R> struct View {
     int *anc_i;                // nv*3 stencil base floor(X) (wrapped on periodic axes)
     R *anc_t;                  // nv*3 fractions X - floor(X)
     R *tiles;                  // nbins*3*11^3 per-bin spreading tiles
+    int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
+};
+
+// Adjoint (reverse-mode) state of one step; all lattice arrays natural
+// layout, SoA, in R.  Gradient slots: per mesh type t: 4t + (k_link, k_bend,
+// k_area, k_volume); then wall-velocity scale, g_x, g_y, g_z.
+template <typename R> struct AdjView {
+    const R *fn;      // 19*N deviations of f_n (natural layout)
+    const R *fn1;     // 19*N deviations of f_{n+1}
+    R *lamf_in;       // 19*N adjoint of f_{n+1} (updated in place by the moments transpose)
+    R *lamf_out;      // 19*N adjoint of f_n
+    R *lamu;          // [3][N] adjoint of u_{n+1}
+    R *lamF;          // [3][N] adjoint of F_n
+    R *up;            // [3][N] u_{n+1} (wall velocity at wall nodes)
+    R *rhop;          // N rho_{n+1}
+    R *lamX;          // nv*3 adjoint of the vertex positions
+    R *lamFv;         // nv*3 adjoint of the membrane forces
+    double *grad;     // gradient accumulators (device)
+    int ntypes;
 };
 
 // launchers (R = double for HEMO_F64, float otherwise)
@@ -134,8 +156,51 @@ template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st)
 template <typename R> void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st);
 template <typename R> void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st);
 
+// adjoint step (natural-layout arrays) and checkpoints
+template <typename R> void launch_copy_natural(const View<R> &v, int precision, int layout, R *out, cudaStream_t st);
+template <typename R> void launch_restore_natural(const View<R> &v, int precision, int layout, const R *in, cudaStream_t st);
+template <typename R> void launch_adj_rho_u(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
+template <typename R> void launch_adj_moments(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
+template <typename R> void launch_adj_collide(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
+template <typename R> void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
+template <typename R> cudaError_t set_cell_adjoint_smem_limit(size_t bytes);
+template <typename R> size_t cell_adjoint_smem_bytes(int max_nv, int max_nt) { return (9 * (size_t)max_nv + 8 * (size_t)max_nt) * sizeof(R); }
+template <typename R>
+void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_grad, R *out_interp, cudaStream_t st);
+template <typename R>
+void launch_deformation_loss(const View<R> &v, const double *c0, double *cell_loss, R *dLdX, cudaStream_t st);
+
 // sets the message returned by hemo_last_error() on the calling thread
 void set_last_error(const char *msg);
+
+// index offsets of a node's +/- neighbours per axis (periodic wrap built in;
+// offsets across a non-periodic edge are never used: those links are walls)
+struct Nbr {
+    int xp, xm, yp, ym, zp, zm;  // index offsets to the +/- neighbour per axis (wrapped)
+    __device__ __forceinline__ int of(int ccx, int ccy, int ccz) const {
+        return (ccx > 0 ? xp : (ccx < 0 ? xm : 0)) + (ccy > 0 ? yp : (ccy < 0 ? ym : 0)) +
+               (ccz > 0 ? zp : (ccz < 0 ? zm : 0));
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
+    int x = n % v.nx;
+    int r = n / v.nx;
+    int y = r % v.ny;
+    int z = r / v.ny;
+    int sxy = v.nx * v.ny;
+    Nbr o;
+    o.xp = (x == v.nx - 1) ? -(v.nx - 1) : 1;
+    o.xm = (x == 0) ? (v.nx - 1) : -1;
+    o.yp = (y == v.ny - 1) ? -(v.ny - 1) * v.nx : v.nx;
+    o.ym = (y == 0) ? (v.ny - 1) * v.nx : -v.nx;
+    o.zp = (z == v.nz - 1) ? -(v.nz - 1) * sxy : sxy;
+    o.zm = (z == 0) ? (v.nz - 1) * sxy : -sxy;
+    return o;
+}
+
+__device__ __forceinline__ int link_code(uint64_t lk, int i) { return (int)((lk >> (2 * i)) & 3u); }
 
 // periodic wrap of a lattice coordinate
 __host__ __device__ __forceinline__ int wrap(int j, int n) {

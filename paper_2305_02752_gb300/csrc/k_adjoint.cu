@@ -1,0 +1,200 @@
+// Reverse mode (adjoint) of the lattice part of the coupled step, for the
+// differentiation form: gradients of a loss of the final vertex positions
+// with respect to the membrane moduli, the wall velocity and the body force.
+//
+// Forward step n on the lattice (Sec. 2.2, 2.3, 2.5), natural layout:
+//   collision at a fluid node: rho = sum f, u = (sum f c + F/2) / rho,
+//     f*_i = (1 - w) f_i + w f^eq_i(rho, u) + S_i(u, F)            (BGK + Guo)
+//   streaming: f'_i(x) = f*_i(x - c_i), or at a wall x - c_i:
+//     f'_i(x) = f*_opp(i)(x) - 6 w_i rho(x) (c_opp(i) . u_wall)   (bounce-back)
+//   velocity: u'(x) = (sum f' c + F/2) / rho'(x); u' = u_wall at wall nodes.
+// The adjoint runs these backwards: the moments transpose adds
+// lambda_u (c - u') / rho' to lambda_f' and lambda_u / (2 rho') to lambda_F;
+// the streaming transpose pulls lambda_f* from the node each population
+// streamed to (bounce-back: from the node itself); the collision transpose
+// goes through (rho, u):
+//   lambda_f_j = (1 - w) lambda*_j + g_rho + (c_j - u) . g_u / rho + lambda_rho,
+//   g_rho = w sum_i lambda*_i f^eq_i / rho,
+//   g_u = sum_i lambda*_i (w df^eq_i/du + dS_i/du),
+//   lambda_F += sum_i lambda*_i dS_i/dF + g_u / (2 rho).
+// Gradients accumulate in FP64: wall-velocity scale s (u_wall = s u_given):
+// sum over wall nodes of lambda_u . u_wall plus the bounce-back terms;
+// body force g: sum over fluid nodes of lambda_F.
+#include <type_traits>
+
+#include "hemo_internal.cuh"
+
+namespace hemo {
+
+namespace {
+
+inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
+
+// block-wide sum of K doubles into acc (one atomic per block and value)
+template <int K>
+__device__ void block_add(double (&val)[K], double *acc) {
+    __shared__ double part[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_down_sync(0xffffffffu, val[k], o);
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) part[k][wid] = val[k];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0;
+        for (int w = 0; w < nw; ++w) s += part[threadIdx.x][w];
+        if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+    }
+}
+
+// rho' and u' of the stored post-streaming populations f_{n+1} with F_n
+template <typename R>
+__global__ void adj_rho_u_kernel(View<R> v, AdjView<R> a) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= v.N || (v.ntype[n] & 0x7f)) return;
+    const size_t N = (size_t)v.N;
+    R rho = R(1), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R d = a.fn1[(size_t)i * N + n];
+        rho += d;
+        m[0] += R(cx(i)) * d;
+        m[1] += R(cy(i)) * d;
+        m[2] += R(cz(i)) * d;
+    }
+    a.rhop[n] = rho;
+    for (int k = 0; k < 3; ++k) a.up[k * N + n] = (m[k] + R(0.5) * v.F[k * N + n]) / rho;
+}
+
+// transpose of u' = (sum f' c + F/2) / rho' (fluid) and u' = u_wall (walls)
+template <typename R>
+__global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> a) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double ds[1] = {0.0};
+    if (n < v.N) {
+        const size_t N = (size_t)v.N;
+        const R lu[3] = {a.lamu[n], a.lamu[N + n], a.lamu[2 * N + n]};
+        const int id = v.ntype[n] & 0x7f;
+        if (id) {
+            if (id >= 2) ds[0] = (double)(lu[0] * v.uw[id][0] + lu[1] * v.uw[id][1] + lu[2] * v.uw[id][2]);
+            for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0);
+        } else {
+            const R rho = a.rhop[n];
+            const R u[3] = {a.up[n], a.up[N + n], a.up[2 * N + n]};
+            const R lu_u = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
+            const R ir = R(1) / rho;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const R lc = R(cx(i)) * lu[0] + R(cy(i)) * lu[1] + R(cz(i)) * lu[2];
+                a.lamf_in[(size_t)i * N + n] += (lc - lu_u) * ir;
+            }
+            for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0.5) * lu[k] * ir;
+        }
+    }
+    block_add<1>(ds, a.grad + 4 * a.ntypes);
+}
+
+// transpose of streaming (pull) and of the collision at fluid node n
+template <typename R>
+__global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> a) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // wall-velocity scale, g_x, g_y, g_z
+    if (n < v.N && !(v.ntype[n] & 0x7f)) {
+        const size_t N = (size_t)v.N;
+        const uint8_t nt = v.ntype[n];
+        const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
+        const Nbr o = make_nbr(v, n);
+        // forward collision quantities
+        R d[Q];
+        R rho = R(1), m[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            d[i] = a.fn[(size_t)i * N + n];
+            rho += d[i];
+            m[0] += R(cx(i)) * d[i];
+            m[1] += R(cy(i)) * d[i];
+            m[2] += R(cz(i)) * d[i];
+        }
+        const R F[3] = {v.F[n], v.F[N + n], v.F[2 * N + n]};
+        const R ir = R(1) / rho;
+        const R u[3] = {(m[0] + R(0.5) * F[0]) * ir, (m[1] + R(0.5) * F[1]) * ir, (m[2] + R(0.5) * F[2]) * ir};
+        const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const R om = v.omega, s0 = R(1) - R(0.5) * om;
+        // pulled adjoint of the post-collision populations
+        R ls[Q];
+        R lrho = R(0);
+        double dsw = 0.0;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int code = link_code(lk, j);
+            if (code) {
+                const R lj = a.lamf_in[(size_t)opp(j) * N + n];
+                ls[j] = lj;
+                const R cw = R(cx(j)) * v.uw[code][0] + R(cy(j)) * v.uw[code][1] + R(cz(j)) * v.uw[code][2];
+                lrho -= R(6) * R(wgt(j)) * cw * lj;
+                dsw -= 6.0 * wgt(j) * (double)rho * (double)cw * (double)lj;
+            } else {
+                ls[j] = a.lamf_in[(size_t)j * N + n + o.of(cx(j), cy(j), cz(j))];
+            }
+        }
+        R grho = R(0), gu[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const R w = R(wgt(i));
+            const R ci[3] = {R(cx(i)), R(cy(i)), R(cz(i))};
+            const R cu = ci[0] * u[0] + ci[1] * u[1] + ci[2] * u[2];
+            const R cF = ci[0] * F[0] + ci[1] * F[1] + ci[2] * F[2];
+            const R feq = w * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+            grho += ls[i] * feq;
+            for (int k = 0; k < 3; ++k) {
+                const R dfeq = w * rho * (R(3) * ci[k] + R(9) * cu * ci[k] - R(3) * u[k]);
+                const R dS = s0 * w * (R(-3) * F[k] + R(9) * cF * ci[k]);
+                gu[k] += ls[i] * (om * dfeq + dS);
+                lF[k] += ls[i] * s0 * w * (R(3) * (ci[k] - u[k]) + R(9) * cu * ci[k]);
+            }
+        }
+        grho *= om * ir;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const R cgu = (R(cx(j)) - u[0]) * gu[0] + (R(cy(j)) - u[1]) * gu[1] + (R(cz(j)) - u[2]) * gu[2];
+            a.lamf_out[(size_t)j * N + n] = (R(1) - om) * ls[j] + grho + cgu * ir + lrho;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const R tot = a.lamF[k * N + n] + lF[k] + R(0.5) * gu[k] * ir;
+            a.lamF[k * N + n] = tot;
+            acc[1 + k] = (double)tot;
+        }
+        acc[0] = dsw;
+    } else if (n < v.N) {
+        const size_t N = (size_t)v.N;
+        for (int j = 0; j < Q; ++j) a.lamf_out[(size_t)j * N + n] = R(0);
+    }
+    block_add<4>(acc, a.grad + 4 * a.ntypes);
+}
+
+}  // namespace
+
+template <typename R>
+void launch_adj_rho_u(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
+    adj_rho_u_kernel<R><<<nblocks(v.N, 256), 256, 0, st>>>(v, a);
+}
+
+template <typename R>
+void launch_adj_moments(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
+    adj_moments_kernel<R><<<nblocks(v.N, 256), 256, 0, st>>>(v, a);
+}
+
+template <typename R>
+void launch_adj_collide(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
+    adj_collide_kernel<R><<<nblocks(v.N, 256), 256, 0, st>>>(v, a);
+}
+
+#define HEMO_INST(R)                                                                  \
+    template void launch_adj_rho_u<R>(const View<R> &, const AdjView<R> &, cudaStream_t);   \
+    template void launch_adj_moments<R>(const View<R> &, const AdjView<R> &, cudaStream_t); \
+    template void launch_adj_collide<R>(const View<R> &, const AdjView<R> &, cudaStream_t);
+HEMO_INST(double)
+HEMO_INST(float)
+
+}  // namespace hemo

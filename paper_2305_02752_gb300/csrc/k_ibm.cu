@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) spread_gather_kernel(View<R> v) {
                     f2 += tt[2 * TILE3 + ti];
                 }
         const size_t n = (size_t)x + (size_t)v.nx * ((size_t)y + (size_t)v.ny * z);
-        const bool wall = v.ntype[n] & 0x7f;
+        const bool wall = !v.spread_all_nodes && (v.ntype[n] & 0x7f);
         v.F[n] = wall ? R(0) : v.g[0] + f0;
         v.F[N + n] = wall ? R(0) : v.g[1] + f1;
         v.F[2 * N + n] = wall ? R(0) : v.g[2] + f2;
@@ -462,6 +462,125 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
     }
 }
 
+// Peskin weights and their derivatives d/dt for the fraction t
+template <typename R>
+__device__ __forceinline__ void peskin4_d(R t, R *w, R *dw) {
+    const R q = sqrt_r(R(1) + R(4) * t - R(4) * t * t);
+    const R qp = (R(2) - R(4) * t) / q;
+    w[0] = (R(3) - R(2) * t - q) * R(0.125);
+    w[1] = (R(3) - R(2) * t + q) * R(0.125);
+    w[2] = (R(1) + R(2) * t + q) * R(0.125);
+    w[3] = (R(1) + R(2) * t - q) * R(0.125);
+    dw[0] = (R(-2) - qp) * R(0.125);
+    dw[1] = (R(-2) + qp) * R(0.125);
+    dw[2] = (R(2) + qp) * R(0.125);
+    dw[3] = (R(2) - qp) * R(0.125);
+}
+
+// Adjoint of the coupling operators at the vertices (differentiation form):
+// for each vertex v of a bin, with the lattice field A staged like the
+// velocity in interpolate_kernel,
+//   out_interp[v]  = sum_x w(X_v, x) A(x)                  (interpolation)
+//   out_grad[v]   += sum_x (A(x) . B[v]) grad_X w(X_v, x)  (position derivative)
+// grad_X w = (w'_x w_y w_z, w_x w'_y w_z, w_x w_y w'_z).  Either output may
+// be null (B is then unused).  out_grad may alias B: a vertex reads B[v]
+// before its own write.
+template <typename R> struct VfStage { static constexpr int CAP = sizeof(R) == 8 ? 16 : 128; };
+template <typename R>
+__global__ void __launch_bounds__(256) vertex_field_kernel(View<R> v, const R *A, const R *B, R *out_grad,
+                                                           R *out_interp) {
+    constexpr int CAP = VfStage<R>::CAP;
+    const int k = blockIdx.x;
+    const int s = v.start[k], e = v.start[k + 1];
+    if (s == e) return;
+    __shared__ R tile[3][TILE_SMEM];
+    __shared__ int srow[CAP], sperm[CAP];
+    __shared__ R sw[24 * CAP], sB[3 * CAP];
+    __shared__ int jtab[3][TILE];
+    int org[3];
+    bin_origin(v, k, org);
+    if (threadIdx.x < 3 * TILE) {
+        const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
+        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+        int j = org[d] - 1 + l;
+        if (v.per[d]) j = wrap(j, dims);
+        else if (j < 0 || j >= dims) j = -1;
+        jtab[d][l] = j;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+        const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
+        const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
+        const int sidx = l0 + TS_Y * l1 + TS_Z * l2;
+        if ((jx | jy | jz) < 0) {
+            tile[0][sidx] = tile[1][sidx] = tile[2][sidx] = R(0);
+        } else {
+            const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
+            tile[0][sidx] = A[n];
+            tile[1][sidx] = A[N + n];
+            tile[2][sidx] = A[2 * N + n];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
+    for (int c0 = s; c0 < e; c0 += CAP) {
+        const int n = min(CAP, e - c0);
+        if (c0 != s) __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int i = v.perm[c0 + j];
+            int row = 0;
+            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+                const int bb = v.anc_i[3 * (size_t)i + d] - org[d];
+                ok &= bb >= 0 && bb < BLK;
+                row += bb * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
+                peskin4_d(v.anc_t[3 * (size_t)i + d], sw + 24 * j + 4 * d, sw + 24 * j + 12 + 4 * d);
+                sB[3 * j + d] = B ? B[3 * (size_t)i + d] : R(0);
+            }
+            srow[j] = ok ? row : -1;
+            sperm[j] = i;
+        }
+        __syncthreads();
+        for (int q0 = 2 * warp; q0 < n; q0 += 2 * nw) {  // uniform per warp: shuffles below
+            const int q = q0 + h;
+            R U[3] = {R(0), R(0), R(0)}, G[3] = {R(0), R(0), R(0)};
+            const int row0 = q < n ? srow[q] : -1;
+            if (row0 >= 0) {
+                const R *w = sw + 24 * q, *dw = w + 12;
+                const R Bv[3] = {sB[3 * q], sB[3 * q + 1], sB[3 * q + 2]};
+                const R wy = w[4 + b], wz = w[8 + c], dwy = dw[4 + b], dwz = dw[8 + c];
+                const int row = row0 + TS_Y * b + TS_Z * c;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const R A0 = tile[0][row + a], A1 = tile[1][row + a], A2 = tile[2][row + a];
+                    const R wxyz = w[a] * wy * wz;
+                    U[0] += wxyz * A0;
+                    U[1] += wxyz * A1;
+                    U[2] += wxyz * A2;
+                    const R sAB = A0 * Bv[0] + A1 * Bv[1] + A2 * Bv[2];
+                    G[0] += sAB * dw[a] * wy * wz;
+                    G[1] += sAB * w[a] * dwy * wz;
+                    G[2] += sAB * w[a] * wy * dwz;
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1)
+                for (int d = 0; d < 3; ++d) {
+                    U[d] += __shfl_xor_sync(0xffffffffu, U[d], o);
+                    G[d] += __shfl_xor_sync(0xffffffffu, G[d], o);
+                }
+            if (row0 >= 0 && (lane & 15) == 0) {
+                const size_t vid = (size_t)sperm[q];
+                for (int d = 0; d < 3; ++d) {
+                    if (out_interp) out_interp[3 * vid + d] = U[d];
+                    if (out_grad) out_grad[3 * vid + d] += G[d];
+                }
+            }
+        }
+    }
+}
+
 template <typename R>
 __global__ void verts_out_kernel(View<R> v, double *X, double *F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -508,6 +627,11 @@ void launch_interpolate(const View<R> &v, cudaStream_t st) {
 }
 
 template <typename R>
+void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_grad, R *out_interp, cudaStream_t st) {
+    vertex_field_kernel<R><<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
+}
+
+template <typename R>
 void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st) {
     if (v.nv) verts_out_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v, X, F);
 }
@@ -522,6 +646,7 @@ void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st) {
     template void launch_spread<R>(const View<R> &, cudaStream_t);                        \
     template void launch_interpolate<R>(const View<R> &, cudaStream_t);                   \
     template void launch_verts_out<R>(const View<R> &, double *, double *, cudaStream_t); \
+    template void launch_vertex_field<R>(const View<R> &, const R *, const R *, R *, R *, cudaStream_t); \
     template void launch_set_vertices<R>(const View<R> &, const double *, cudaStream_t);
 HEMO_INST(double)
 HEMO_INST(float)

@@ -25,33 +25,6 @@ namespace hemo {
 
 namespace {
 
-struct Nbr {
-    int xp, xm, yp, ym, zp, zm;  // index offsets to the +/- neighbour per axis (wrapped)
-    __device__ __forceinline__ int of(int ccx, int ccy, int ccz) const {
-        return (ccx > 0 ? xp : (ccx < 0 ? xm : 0)) + (ccy > 0 ? yp : (ccy < 0 ? ym : 0)) +
-               (ccz > 0 ? zp : (ccz < 0 ? zm : 0));
-    }
-};
-
-template <typename R>
-__device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
-    int x = n % v.nx;
-    int r = n / v.nx;
-    int y = r % v.ny;
-    int z = r / v.ny;
-    int sxy = v.nx * v.ny;
-    Nbr o;
-    o.xp = (x == v.nx - 1) ? -(v.nx - 1) : 1;
-    o.xm = (x == 0) ? (v.nx - 1) : -1;
-    o.yp = (y == v.ny - 1) ? -(v.ny - 1) * v.nx : v.nx;
-    o.ym = (y == 0) ? (v.ny - 1) * v.nx : -v.nx;
-    o.zp = (z == v.nz - 1) ? -(v.nz - 1) * sxy : sxy;
-    o.zm = (z == 0) ? (v.nz - 1) * sxy : -sxy;
-    return o;
-}
-
-__device__ __forceinline__ int link_code(uint64_t lk, int i) { return (int)((lk >> (2 * i)) & 3u); }
-
 // Read the 19 populations arriving at node n.  LAYOUT 0: natural order (slot
 // i of n).  LAYOUT 1: after an even step (slot opp(i) of n - c_i, or slot i
 // of n when n - c_i is a wall).
@@ -275,6 +248,47 @@ __global__ void mark_near_wall_kernel(int N, uint8_t *ntype, const uint64_t *lin
     if (ntype[n] == 0 && links[n] != 0) ntype[n] = 0x80;
 }
 
+// Natural-layout copy of the deviations (R, SoA [i][n]); wall nodes get 0.
+template <typename T, typename R, int LAYOUT>
+__global__ void copy_natural_kernel(View<R> v, R *out) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= v.N) return;
+    const size_t N = (size_t)v.N;
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) {
+        for (int i = 0; i < Q; ++i) out[(size_t)i * N + n] = R(0);
+        return;
+    }
+    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
+    const Nbr o = make_nbr(v, n);
+    R d[Q];
+    load_pops<T, R, LAYOUT>(v, n, lk, o, d);
+    for (int i = 0; i < Q; ++i) out[(size_t)i * N + n] = d[i];
+}
+
+// Inverse of copy_natural: writes natural-layout deviations into the
+// in-place array in the layout of the given parity (0 natural; 1 the layout
+// after an even step, where population i of node x sits in slot opp(i) of
+// x - c_i, or in slot i of x when x - c_i is a wall).  Each slot is written
+// by exactly one thread.
+template <typename T, typename R, int LAYOUT>
+__global__ void restore_natural_kernel(View<R> v, const R *in) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= v.N) return;
+    const size_t N = (size_t)v.N;
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) return;
+    T *f = (T *)v.f;
+    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
+    const Nbr o = make_nbr(v, n);
+    for (int i = 0; i < Q; ++i) {
+        const T val = Store<T>::st(in[(size_t)i * N + n]);
+        if (LAYOUT == 0 || i == 0) f[(size_t)i * N + n] = val;
+        else if (link_code(lk, opp(i))) f[(size_t)i * N + n] = val;
+        else f[(size_t)opp(i) * N + n + o.of(-cx(i), -cy(i), -cz(i))] = val;
+    }
+}
+
 inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
@@ -354,13 +368,33 @@ void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, 
     mark_near_wall_kernel<<<nblocks(N, 256), 256, 0, st>>>((int)N, ntype, links);
 }
 
+template <typename R>
+void launch_copy_natural(const View<R> &v, int precision, int layout, R *out, cudaStream_t st) {
+    const int g = nblocks(v.N, 256);
+    if (layout == 0)
+        HEMO_DISPATCH_T(precision, R, (copy_natural_kernel<T, R, 0><<<g, 256, 0, st>>>(v, out)));
+    else
+        HEMO_DISPATCH_T(precision, R, (copy_natural_kernel<T, R, 1><<<g, 256, 0, st>>>(v, out)));
+}
+
+template <typename R>
+void launch_restore_natural(const View<R> &v, int precision, int layout, const R *in, cudaStream_t st) {
+    const int g = nblocks(v.N, 256);
+    if (layout == 0)
+        HEMO_DISPATCH_T(precision, R, (restore_natural_kernel<T, R, 0><<<g, 256, 0, st>>>(v, in)));
+    else
+        HEMO_DISPATCH_T(precision, R, (restore_natural_kernel<T, R, 1><<<g, 256, 0, st>>>(v, in)));
+}
+
 #define HEMO_INST(R)                                                                              \
     template void launch_collide<R>(const View<R> &, int, int, cudaStream_t);                     \
     template void launch_moments<R>(const View<R> &, int, int, cudaStream_t);                     \
     template void launch_init_equilibrium<R>(const View<R> &, int, const double *, cudaStream_t); \
     template void launch_populations_out<R>(const View<R> &, int, int, double *, cudaStream_t);   \
     template void launch_rho_out<R>(const View<R> &, int, int, R *, cudaStream_t);                \
-    template void launch_u_out<R>(const View<R> &, R *, cudaStream_t);
+    template void launch_u_out<R>(const View<R> &, R *, cudaStream_t);                           \
+    template void launch_copy_natural<R>(const View<R> &, int, int, R *, cudaStream_t);           \
+    template void launch_restore_natural<R>(const View<R> &, int, int, const R *, cudaStream_t);
 HEMO_INST(double)
 HEMO_INST(float)
 

@@ -210,6 +210,224 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
     for (int k = threadIdx.x; k < 3 * m.nv; k += blockDim.x) v.Fv[3 * (size_t)first + k] = fs[k];
 }
 
+// ---------------------------------------------------------------------------
+// Differentiation form
+// ---------------------------------------------------------------------------
+// Forward-mode dual number: value and derivative along one direction.
+template <typename R> struct Dual {
+    R v, t;
+};
+template <typename R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return {a.v + b.v, a.t + b.t}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return {a.v - b.v, a.t - b.t}; }
+template <typename R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) {
+    return {a.v * b.v, a.v * b.t + a.t * b.v};
+}
+template <typename R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, Dual<R> b) {
+    return {a.v / b.v, (a.t * b.v - a.v * b.t) / (b.v * b.v)};
+}
+template <typename R> __device__ __forceinline__ Dual<R> dconst(R x) { return {x, R(0)}; }
+template <typename R> __device__ __forceinline__ Dual<R> dsqrt(Dual<R> a) {
+    const R s = sqrt_r(a.v);
+    return {s, a.t / (R(2) * s)};
+}
+template <typename R> __device__ __forceinline__ Dual<R> datan2(Dual<R> y, Dual<R> x) {
+    return {atan2_r(y.v, x.v), (x.v * y.t - y.v * x.t) / (x.v * x.v + y.v * y.v)};
+}
+template <typename R> __device__ __forceinline__ V3<Dual<R>> dld3(const R *pv, const R *pt) {
+    return {{pv[0], pt[0]}, {pv[1], pt[1]}, {pv[2], pt[2]}};
+}
+template <typename R> __device__ __forceinline__ V3<R> vals(V3<Dual<R>> a) { return {a.x.v, a.y.v, a.z.v}; }
+template <typename R> __device__ __forceinline__ V3<R> tans(V3<Dual<R>> a) { return {a.x.t, a.y.t, a.z.t}; }
+template <typename R> __device__ __forceinline__ void add_into(R *f, R s, V3<R> a) {
+    atomicAdd(f, s * a.x);
+    atomicAdd(f + 1, s * a.y);
+    atomicAdd(f + 2, s * a.z);
+}
+
+// Adjoint of the membrane forces of one cell (one CTA per cell), at the
+// positions X_n left by the forward recomputation (cell_kernel mode 0):
+//   lamX += (dF/dX) lamFv  -- F = -grad E, so dF/dX = -Hessian is symmetric
+//                            and its product with lamFv is the derivative
+//                            of F along lamFv, taken with dual numbers;
+//   grad[4 type + k] += lamFv . F_k / modulus_k for the four terms (each is
+//                            linear in its modulus).
+template <typename R>
+__global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R> a) {
+    using D = Dual<R>;
+    const int c = blockIdx.x;
+    const int type = v.cell_type[c];
+    const MeshDev<R> m = v.meshes[type];
+    const int first = v.cell_first[c];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *xs = reinterpret_cast<R *>(smem_raw);  // positions (relative to the centroid)
+    R *xt = xs + 3 * v.max_nv;                  // direction: lamFv
+    R *ft = xt + 3 * v.max_nv;                  // derivative of the forces along lamFv
+    R *tn = ft + 3 * v.max_nv;                  // per triangle: n (3), dn (3), 1/|n|^2, its derivative
+    __shared__ double scratch[6][32];
+    for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) {
+        xs[i] = v.off[3 * (size_t)first + i];
+        xt[i] = a.lamFv[3 * (size_t)first + i];
+        ft[i] = R(0);
+    }
+    __syncthreads();
+
+    double av[4] = {0, 0, 0, 0};  // A, dA, V, dV
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const int j0 = m.tri[3 * t], j1 = m.tri[3 * t + 1], j2 = m.tri[3 * t + 2];
+        const V3<D> p0 = dld3(xs + 3 * j0, xt + 3 * j0), p1 = dld3(xs + 3 * j1, xt + 3 * j1),
+                    p2 = dld3(xs + 3 * j2, xt + 3 * j2);
+        const V3<D> n = cross(p1 - p0, p2 - p0);
+        const D q = dot(n, n);
+        const D iq = dconst(R(1)) / q;
+        R *o = tn + 8 * t;
+        o[0] = n.x.v; o[1] = n.y.v; o[2] = n.z.v;
+        o[3] = n.x.t; o[4] = n.y.t; o[5] = n.z.t;
+        o[6] = iq.v; o[7] = iq.t;
+        const D ar = dconst(R(0.5)) * dsqrt(q);
+        const D vo = dot(p0, cross(p1, p2));
+        av[0] += (double)ar.v;
+        av[1] += (double)ar.t;
+        av[2] += (double)vo.v / 6.0;
+        av[3] += (double)vo.t / 6.0;
+    }
+    block_sum<4>(av, scratch);
+    const D ua = {R((av[0] - m.A0) / (m.A0 * m.A0)), R(av[1] / (m.A0 * m.A0))};
+    const D uv = {R((av[2] - m.V0) / (m.V0 * m.V0)), R(av[3] / (m.V0 * m.V0))};
+
+    double th[4] = {0, 0, 0, 0};  // lamFv . unit-modulus forces: link, bend, area, volume
+    for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
+        const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
+        const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
+        const V3<D> p0 = dld3(xs + 3 * i0, xt + 3 * i0), p1 = dld3(xs + 3 * i1, xt + 3 * i1);
+        const V3<D> pa = dld3(xs + 3 * ia, xt + 3 * ia), pb = dld3(xs + 3 * ib, xt + 3 * ib);
+        const V3<R> l0 = ld3(xt + 3 * i0), l1 = ld3(xt + 3 * i1), la = ld3(xt + 3 * ia), lb = ld3(xt + 3 * ib);
+        const V3<D> ed = p1 - p0;
+        const D L = dsqrt(dot(ed, ed));
+        const D iL = dconst(R(1)) / L;
+        const D eps = L * dconst(m.invL0[e]) - dconst(R(1));
+        const D den = dconst(m.m2) - eps * eps;
+        const D dEdL = dconst(m.Ku) * (eps + eps / den);
+        const V3<D> u0 = (dEdL * iL) * ed;  // unit link force on v0; -u0 on v1
+        add_into(ft + 3 * i0, m.k_link, tans(u0));
+        add_into(ft + 3 * i1, -m.k_link, tans(u0));
+        th[0] += (double)(dot(l0, vals(u0)) - dot(l1, vals(u0)));
+
+        const V3<D> n1 = dld3(tn + 8 * t1, tn + 8 * t1 + 3), n2 = dld3(tn + 8 * t2, tn + 8 * t2 + 3);
+        const D iq1 = {tn[8 * t1 + 6], tn[8 * t1 + 7]}, iq2 = {tn[8 * t2 + 6], tn[8 * t2 + 7]};
+        const V3<D> a1 = iq1 * n1, a2 = iq2 * n2;
+        const D thd = datan2(dot(cross(n1, n2), ed) * iL, dot(n1, n2));
+        const D cb = dconst(m.kbu) * (thd - dconst(m.th0[e]));
+        const D sa0 = dot(pa - p1, ed) * iL, sb0 = dot(pb - p1, ed) * iL;
+        const D sa1 = dot(pa - p0, ed) * iL, sb1 = dot(pb - p0, ed) * iL;
+        const V3<D> fa = (cb * L) * a1, fb = (cb * L) * a2;
+        const V3<D> f0 = cb * (sa0 * a1 + sb0 * a2);
+        const V3<D> f1 = (dconst(R(0)) - cb) * (sa1 * a1 + sb1 * a2);
+        add_into(ft + 3 * ia, m.k_bend, tans(fa));
+        add_into(ft + 3 * ib, m.k_bend, tans(fb));
+        add_into(ft + 3 * i0, m.k_bend, tans(f0));
+        add_into(ft + 3 * i1, m.k_bend, tans(f1));
+        th[1] += (double)(dot(la, vals(fa)) + dot(lb, vals(fb)) + dot(l0, vals(f0)) + dot(l1, vals(f1)));
+    }
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const int j[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
+        const V3<D> p[3] = {dld3(xs + 3 * j[0], xt + 3 * j[0]), dld3(xs + 3 * j[1], xt + 3 * j[1]),
+                            dld3(xs + 3 * j[2], xt + 3 * j[2])};
+        const D iq = {tn[8 * t + 6], tn[8 * t + 7]};
+        const V3<D> nh = dsqrt(iq) * dld3(tn + 8 * t, tn + 8 * t + 3);
+        for (int k = 0; k < 3; ++k) {
+            const V3<D> &pk1 = p[(k + 1) % 3], &pk2 = p[(k + 2) % 3];
+            const V3<D> fa = (dconst(R(-0.5)) * ua) * cross(nh, pk2 - pk1);
+            const V3<D> fv = (dconst(R(-1) / R(6)) * uv) * cross(pk1, pk2);
+            add_into(ft + 3 * j[k], R(m.k_area), tans(fa));
+            add_into(ft + 3 * j[k], R(m.k_volume), tans(fv));
+            const V3<R> lk = ld3(xt + 3 * j[k]);
+            th[2] += (double)dot(lk, vals(fa));
+            th[3] += (double)dot(lk, vals(fv));
+        }
+    }
+    block_sum<4>(th, scratch);
+    if (threadIdx.x < 4) atomicAdd(a.grad + 4 * type + threadIdx.x, th[threadIdx.x]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) a.lamX[3 * (size_t)first + i] += ft[i];
+}
+
+// eigenvector of the symmetric 3x3 matrix g (xx, yy, zz, xy, xz, yz) for
+// the eigenvalue lam: the longest cross product of two rows of g - lam I
+__device__ void sym3_vec(const double *g, double lam, double *e) {
+    const double r[3][3] = {{g[0] - lam, g[3], g[4]}, {g[3], g[1] - lam, g[5]}, {g[4], g[5], g[2] - lam}};
+    double best = -1.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+            const double c[3] = {r[a][1] * r[b][2] - r[a][2] * r[b][1], r[a][2] * r[b][0] - r[a][0] * r[b][2],
+                                 r[a][0] * r[b][1] - r[a][1] * r[b][0]};
+            const double n2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+            if (n2 > best) {
+                best = n2;
+                const double s = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+                e[0] = c[0] * s;
+                e[1] = c[1] * s;
+                e[2] = c[2] * s;
+            }
+        }
+}
+
+// Deformation loss of each cell, DI + |centroid - c0|^2, with
+// DI = (sqrt(l1) - sqrt(l3)) / (sqrt(l1) + sqrt(l3)) from the gyration tensor
+// G = mean (X - c)(X - c)^T, and its gradient divided by the number of cells
+// (the loss is the mean over cells): d l_k / dX_v = (2/n)(e_k . r_v) e_k.
+template <typename R>
+__global__ void __launch_bounds__(256) deformation_loss_kernel(View<R> v, const double *c0, double *cell_loss, R *dLdX) {
+    const int c = blockIdx.x;
+    const MeshDev<R> m = v.meshes[v.cell_type[c]];
+    const int first = v.cell_first[c];
+    __shared__ double scratch[6][32];
+    __shared__ double coef[9];  // k1, k3, e1 (3), e3 (3), unused
+    double mean[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) mean[k] += (double)v.off[3 * (size_t)(first + i) + k];
+    block_sum<3>(mean, scratch);
+    for (int k = 0; k < 3; ++k) mean[k] /= m.nv;
+    double G[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        const double x = (double)v.off[3 * (size_t)(first + i)] - mean[0];
+        const double y = (double)v.off[3 * (size_t)(first + i) + 1] - mean[1];
+        const double z = (double)v.off[3 * (size_t)(first + i) + 2] - mean[2];
+        G[0] += x * x; G[1] += y * y; G[2] += z * z;
+        G[3] += x * y; G[4] += x * z; G[5] += y * z;
+    }
+    block_sum<6>(G, scratch);
+    for (int k = 0; k < 6; ++k) G[k] /= m.nv;
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = v.ctr[3 * c + k] + mean[k] - c0[3 * c + k];
+    if (threadIdx.x == 0) {
+        double l1, l3;
+        sym3_eig(G[0], G[1], G[2], G[3], G[4], G[5], l1, l3);
+        const double aa = sqrt(l1), bb = sqrt(l3 > 0 ? l3 : 0);
+        const double DI = (aa - bb) / (aa + bb);
+        cell_loss[c] = DI + d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double k1 = 0, k3 = 0;
+        if (aa - bb > 1e-12 * aa && bb > 0) {  // DI is not differentiable at isotropy
+            k1 = 2.0 / m.nv * bb / (aa * (aa + bb) * (aa + bb));
+            k3 = -2.0 / m.nv * aa / (bb * (aa + bb) * (aa + bb));
+        }
+        coef[0] = k1;
+        coef[1] = k3;
+        sym3_vec(G, l1, coef + 2);
+        sym3_vec(G, l3, coef + 5);
+    }
+    __syncthreads();
+    const double inv_nc = 1.0 / v.ncell;
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = (double)v.off[3 * (size_t)(first + i) + k] - mean[k];
+        const double p1 = r[0] * coef[2] + r[1] * coef[3] + r[2] * coef[4];
+        const double p3 = r[0] * coef[5] + r[1] * coef[6] + r[2] * coef[7];
+        for (int k = 0; k < 3; ++k)
+            dLdX[3 * (size_t)(first + i) + k] =
+                R(inv_nc * (coef[0] * p1 * coef[2 + k] + coef[1] * p3 * coef[5 + k] + 2.0 * d[k] / m.nv));
+    }
+}
+
 }  // namespace
 
 template <typename R>
@@ -224,6 +442,29 @@ cudaError_t set_cell_smem_limit(size_t bytes) {
     return cudaFuncSetAttribute(cell_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename R>
+void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
+    if (v.ncell == 0) return;
+    cell_adjoint_kernel<R><<<v.ncell, 256, cell_adjoint_smem_bytes<R>(v.max_nv, v.max_nt), st>>>(v, a);
+}
+
+template <typename R>
+cudaError_t set_cell_adjoint_smem_limit(size_t bytes) {
+    return cudaFuncSetAttribute(cell_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+void launch_deformation_loss(const View<R> &v, const double *c0, double *cell_loss, R *dLdX, cudaStream_t st) {
+    if (v.ncell == 0) return;
+    deformation_loss_kernel<R><<<v.ncell, 256, 0, st>>>(v, c0, cell_loss, dLdX);
+}
+
+template void launch_cell_adjoint<double>(const View<double> &, const AdjView<double> &, cudaStream_t);
+template void launch_cell_adjoint<float>(const View<float> &, const AdjView<float> &, cudaStream_t);
+template cudaError_t set_cell_adjoint_smem_limit<double>(size_t);
+template cudaError_t set_cell_adjoint_smem_limit<float>(size_t);
+template void launch_deformation_loss<double>(const View<double> &, const double *, double *, double *, cudaStream_t);
+template void launch_deformation_loss<float>(const View<float> &, const double *, double *, float *, cudaStream_t);
 template void launch_cell_forces<double>(const View<double> &, int, double *, cudaStream_t);
 template void launch_cell_forces<float>(const View<float> &, int, double *, cudaStream_t);
 template cudaError_t set_cell_smem_limit<double>(size_t);

@@ -77,6 +77,9 @@ def lib():
         'hemo_set_phase_timing': ([vp, i], i),
         'hemo_get_phase_times': ([vp, vp, C.POINTER(i)], i),
         'hemo_bin_vertices_noalloc': ([vp, i, i, i, i, vp, vp, vp, vp, vp], i),
+        'hemo_record': ([vp, i], i),
+        'hemo_deformation_loss': ([vp, vp, vp], i),
+        'hemo_backward': ([vp, vp, vp, i], i),
         'hemo_destroy': ([vp], None),
         'hemo_last_error': ([], C.c_char_p),
     }
@@ -93,8 +96,8 @@ def exported_symbols():
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
-            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_destroy',
-            'hemo_last_error']
+            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
+            'hemo_deformation_loss', 'hemo_backward', 'hemo_destroy', 'hemo_last_error']
 
 
 def check(rc):
@@ -291,6 +294,28 @@ class Simulation:
         check(lib().hemo_get_bins(self.handle, key.ctypes.data, perm.ctypes.data, start.ctypes.data))
         return key, perm, start
 
+    # -- differentiation form --------------------------------------------
+    def record(self, checkpoint_every=100):
+        check(lib().hemo_record(self.handle, int(checkpoint_every)))
+
+    def deformation_loss(self):
+        """(loss, dL/dX [nv, 3]) of the current vertices."""
+        _, nv, _, _ = self.sizes()
+        loss = np.zeros(1)
+        g = np.zeros((nv, 3))
+        check(lib().hemo_deformation_loss(self.handle, loss.ctypes.data, g.ctypes.data))
+        return float(loss[0]), g
+
+    def backward(self, dL_dX):
+        """Gradient of a loss of the current vertices with respect to the
+        recorded steps' parameters: per mesh type (k_link, k_bend, k_area,
+        k_volume), then the wall-velocity scale and g (3)."""
+        dL = np.ascontiguousarray(dL_dX, dtype=np.float64)
+        ng = 4 * len(self._meshes) + 4
+        out = np.zeros(ng)
+        check(lib().hemo_backward(self.handle, dL.ctypes.data, out.ctypes.data, ng))
+        return out
+
     PHASES = ('membrane', 'bins', 'spread', 'collide', 'moments', 'interp')
 
     def set_phase_timing(self, on=True):
@@ -314,3 +339,54 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# torch.autograd wrapper
+# ---------------------------------------------------------------------------
+def parameter_vector(cfg):
+    """Parameters in the order of the gradient: per mesh type (k_link,
+    k_bend, k_area, k_volume), wall-velocity scale (1), body force (3)."""
+    vals = []
+    for mt in cfg.meshes:
+        vals += [mt.k_link, mt.k_bend, mt.k_area, mt.k_volume]
+    return np.array(vals + [1.0] + list(np.asarray(cfg.body_force, float)))
+
+
+def config_with(cfg, params):
+    """Copy of an input configuration with the parameters replaced."""
+    import copy
+    c = copy.deepcopy(cfg)
+    p = np.asarray(params, float)
+    for t, mt in enumerate(c.meshes):
+        mt.k_link, mt.k_bend, mt.k_area, mt.k_volume = (float(x) for x in p[4 * t:4 * t + 4])
+    k = 4 * len(c.meshes)
+    c.wall_velocity = np.asarray(cfg.wall_velocity, float) * p[k]
+    c.body_force = p[k + 1:k + 4].copy()
+    return c
+
+
+def coupled_run(cfg, steps, precision='f64', checkpoint_every=100):
+    """A torch.autograd.Function mapping the parameter vector (see
+    parameter_vector) to the final vertex positions after `steps` coupled
+    steps; backward runs hemo_backward."""
+    import torch
+
+    class CoupledRun(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params):
+            sim = Simulation.from_config(config_with(cfg, params.detach().cpu().numpy()), precision)
+            sim.record(checkpoint_every)
+            sim.step(steps)
+            X = sim.get_fields(HEMO_VERTS)['X']
+            ctx.sim = sim
+            ctx.device = params.device
+            return torch.from_numpy(X).to(params.device)
+
+        @staticmethod
+        def backward(ctx, dX):
+            g = ctx.sim.backward(dX.detach().cpu().numpy())
+            ctx.sim.close()
+            return torch.from_numpy(g).to(ctx.device)
+
+    return CoupledRun.apply

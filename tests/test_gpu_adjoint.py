@@ -1,0 +1,178 @@
+"""Differentiation form: the hand-written adjoint of the coupled step
+(through the C ABI) against central finite differences of the forward runs
+(GPU FP64 and the CPU oracle), relative error <= 1e-4 in FP64."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_02752_gb300 import hemo
+from paper_2305_02752_gb300 import inputs as I
+from tests.helpers import rel_l2, small_cell_shear
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+def small_case(steps=40):
+    """A 24^3 sheared box with one 162-vertex cell, a body force (so the cell
+    drifts) and moduli chosen so that every term moves the loss."""
+    cfg = small_cell_shear(n=24, steps=steps, seed=9)
+    mt = cfg.meshes[0]
+    mt.k_link, mt.k_bend, mt.k_area, mt.k_volume = 15.0, 8000.0, 5.0, 20.0
+    cfg.body_force = np.array([2e-6, 0.0, 1e-6])
+    return cfg
+
+
+def gpu_loss(cfg, params, steps, precision='f64'):
+    sim = hemo.Simulation.from_config(hemo.config_with(cfg, params), precision)
+    sim.deformation_loss()  # reference centroids: the initial placement
+    sim.step(steps)
+    L, _ = sim.deformation_loss()
+    sim.close()
+    return L
+
+
+def gpu_adjoint(cfg, steps, every, precision='f64'):
+    sim = hemo.Simulation.from_config(cfg, precision)
+    sim.record(every)
+    sim.step(steps)
+    L, dLdX = sim.deformation_loss()
+    g = sim.backward(dLdX)
+    sim.close()
+    return L, g
+
+
+def central_fd(loss_fn, p0, rel):
+    """Central differences with steps rel * |p| (rel * 1e-5 where p = 0: the
+    zero parameters are body-force components, 1e-5 a body-force scale).
+
+    The modulus gradients of the deformation loss are 1e-8 .. 1e-11 while
+    the loss is O(0.4): with steps of 1e-5 relative the loss moves by less
+    than its FP64 rounding noise (and the order of floating-point atomics),
+    so the strict checks use steps of 1e-2 .. 1e-3 relative, where the
+    differences converge (their truncation error is below 1e-5)."""
+    h = np.where(np.abs(p0) > 0, rel * np.abs(p0), rel * 1e-5)
+    g = np.zeros_like(p0)
+    for k in range(len(p0)):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h[k]
+        pm[k] -= h[k]
+        g[k] = (loss_fn(pp) - loss_fn(pm)) / (2 * h[k])
+    return g
+
+
+def assert_grad_close(adj, fd, tol=GRAD_TOL):
+    for k, (a, f) in enumerate(zip(adj, fd)):
+        assert abs(a - f) <= tol * abs(f), (k, a, f, list(adj), list(fd))
+
+
+def test_loss_gradient_matches_finite_differences():
+    cfg = small_case()
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    sim.deformation_loss()
+    rng = np.random.default_rng(1)
+    X = I.cell_vertices(cfg) + 0.3 * rng.normal(size=(cfg.n_vertices, 3)) * [1.5, 0.7, 0.4] + [0.4, -0.2, 0.3]
+    sim.set_vertices(X)
+    L, g = sim.deformation_loss()
+    idx = rng.choice(len(X), 10, replace=False)
+    for i in idx:
+        for d in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[i, d] += 1e-6
+            Xm[i, d] -= 1e-6
+            sim.set_vertices(Xp)
+            Lp, _ = sim.deformation_loss()
+            sim.set_vertices(Xm)
+            Lm, _ = sim.deformation_loss()
+            assert abs(g[i, d] - (Lp - Lm) / 2e-6) <= 1e-6 * np.abs(g).max() + 1e-6 * abs(g[i, d])
+    sim.set_vertices(X)
+    sim.close()
+    # the oracle computes the same loss on the same positions
+    ref = O.from_config(cfg)
+    ref.set_vertices(X)
+    assert abs(ref.loss() - L) < 1e-12 * max(1.0, abs(L))
+
+
+def test_adjoint_matches_gpu_finite_differences_f64():
+    cfg = small_case(steps=40)
+    p0 = hemo.parameter_vector(cfg)
+    _, g = gpu_adjoint(cfg, 40, every=10)
+    fd = central_fd(lambda p: gpu_loss(cfg, p, 40), p0, rel=1e-2)
+    assert_grad_close(g, fd)
+
+
+def test_adjoint_matches_oracle_finite_differences_f64():
+    """Reference gradient from the CPU oracle: central differences of its own
+    forward runs with the same parameters."""
+    cfg = small_case(steps=30)
+    p0 = hemo.parameter_vector(cfg)
+    _, g = gpu_adjoint(cfg, 30, every=10)
+
+    def oracle_loss(p):
+        s = O.from_config(hemo.config_with(cfg, p))
+        s.step(30)
+        return s.loss()
+
+    fd = central_fd(oracle_loss, p0, rel=1e-2)
+    assert_grad_close(g, fd)
+
+
+def test_adjoint_c3_config_f64():
+    """Config: 48^3 shear, 4 red cells, 2000 steps, checkpoints every 100;
+    gradient of mean DI + drift w.r.t. (k_link, k_bend, k_area, k_volume,
+    wall velocity).  Central differences with the configured h = 1e-6
+    relative resolve the wall-velocity component; the moduli are checked at
+    h = 1e-3 relative (see central_fd)."""
+    cfg = I.shear_cell(n=48, ncell=4, seed=20230503, steps=2000)
+    p0 = hemo.parameter_vector(cfg)
+    L, g = gpu_adjoint(cfg, 2000, every=100)
+    assert np.isfinite(L) and np.all(np.isfinite(g))
+
+    def loss5(q):
+        p = p0.copy()
+        p[:5] = q
+        return gpu_loss(cfg, p, 2000)
+
+    fd6 = central_fd(loss5, p0[:5].copy(), rel=1e-6)
+    assert abs(g[4] - fd6[4]) <= GRAD_TOL * abs(fd6[4])
+    fd3 = central_fd(loss5, p0[:5].copy(), rel=1e-3)
+    assert_grad_close(g[:5], fd3)
+
+
+def test_backward_restores_the_state():
+    cfg = small_case(steps=12)
+    a = hemo.Simulation.from_config(cfg, 'f64')
+    b = hemo.Simulation.from_config(cfg, 'f64')
+    a.record(4)
+    a.step(11)
+    b.step(11)
+    _, dL = a.deformation_loss()
+    a.backward(dL)
+    a.step(5)
+    b.step(5)
+    fa, fb = a.get_fields(), b.get_fields()
+    for k in ('u', 'X', 'rho'):
+        assert rel_l2(fa[k], fb[k]) < 1e-13, k
+    a.close()
+    b.close()
+
+
+def test_autograd_function():
+    import torch
+    cfg = small_case(steps=20)
+    run = hemo.coupled_run(cfg, 20, 'f64', checkpoint_every=10)
+    p = torch.tensor(hemo.parameter_vector(cfg), dtype=torch.float64, requires_grad=True)
+    X = run(p)
+    loss = (X[:, 0] ** 2).sum() * 1e-3 + X[:, 2].mean()
+    loss.backward()
+    # same gradient through the C ABI directly
+    dL = np.zeros((cfg.n_vertices, 3))
+    dL[:, 0] = 2e-3 * X.detach().numpy()[:, 0]
+    dL[:, 2] = 1.0 / cfg.n_vertices
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    sim.record(10)
+    sim.step(20)
+    g = sim.backward(dL)
+    sim.close()
+    assert np.allclose(p.grad.numpy(), g, rtol=1e-8, atol=1e-10 * np.abs(g).max())
