@@ -178,6 +178,37 @@ def run_form(cfg, precision, warmup, steps, torch, flush, u_ref=None):
     return res, u
 
 
+def adjoint_cost(torch, steps=200, every=100):
+    """Differentiation form on the 48^3 shear box with 4 red cells: device
+    time per recorded forward step and per step of the reverse sweep
+    (hemo_backward: checkpoint recomputation + adjoint), FP64 and FP32."""
+    from paper_2305_02752_gb300 import hemo
+    cfg = I.shear_cell(n=48, ncell=4, seed=20230503, steps=steps)
+    out = {'workload': 'shear 48^3, 4 RBC x 642 vertices', 'steps': steps, 'checkpoint_every': every}
+    st = torch.cuda.current_stream()
+    for prec in ('f64', 'f32'):
+        sim = hemo.Simulation.from_config(cfg, prec)
+        sim.step(2)
+        sim.sync()
+        sim.record(every)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        sim.step(steps)
+        e1.record(st)
+        L, dL = sim.deformation_loss()
+        e1b = torch.cuda.Event(enable_timing=True)
+        e1b.record(st)
+        g = sim.backward(dL)
+        e2.record(st)
+        torch.cuda.synchronize()
+        fwd = e0.elapsed_time(e1) / steps
+        bwd = e1b.elapsed_time(e2) / steps
+        sim.close()
+        out[prec] = {'forward_ms_per_step': fwd, 'backward_ms_per_step': bwd, 'ratio': bwd / fwd,
+                     'loss': L, 'grad': [float(x) for x in g]}
+    return out
+
+
 def cpu_baseline(cfg, budget_s=15.0):
     """The CPU oracle as it stands, single thread, on a bounded number of
     steps of the same workload."""
@@ -303,6 +334,7 @@ def main():
     ap.add_argument('--no-forms', action='store_true')
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-adjoint', action='store_true')
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -381,6 +413,8 @@ def main():
         line['forms'] = {'steps': args.warmup + fsteps, 'timed_steps': fsteps, 'results': forms}
     if not args.no_e2e:
         line['e2e'] = e2e_job(cfg, precision, torch)
+    if not args.no_adjoint:
+        line['adjoint'] = adjoint_cost(torch)
     if not args.no_cpu:
         line['cpu_baseline'] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

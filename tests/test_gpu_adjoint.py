@@ -176,3 +176,16 @@ def test_autograd_function():
     g = sim.backward(dL)
     sim.close()
     assert np.allclose(p.grad.numpy(), g, rtol=1e-8, atol=1e-10 * np.abs(g).max())
+
+
+def test_adjoint_f32_close_to_f64():
+    """FP32 storage and arithmetic (FP64 gradient accumulation): the
+    gradient agrees with the FP64 adjoint to 3e-2 relative per component.
+    Near the rest shape the area and volume terms scale with (A - A0) and
+    (V - V0), whose FP32 rounding (per-triangle terms in FP32) is about 1 %
+    of the small deformation after 40 steps."""
+    cfg = small_case(steps=40)
+    _, g64 = gpu_adjoint(cfg, 40, every=10, precision='f64')
+    _, g32 = gpu_adjoint(cfg, 40, every=10, precision='f32')
+    for k, (a, b) in enumerate(zip(g32, g64)):
+        assert abs(a - b) <= 3e-2 * abs(b), (k, a, b)
