@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -94,10 +95,13 @@ void hemo::set_last_error(const char *msg) { g_err = msg; }
 
 // device buffers of the reverse sweep (grown on demand, kept for reuse)
 struct AdjBuffers {
-    void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr, *up = nullptr, *rhop = nullptr;
+    void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr;
     void *lamX = nullptr, *lamFv = nullptr, *grad = nullptr, *seg_f = nullptr, *seg_ctr = nullptr, *seg_off = nullptr;
     void *fin_f = nullptr, *fin_u = nullptr, *fin_ctr = nullptr, *fin_off = nullptr, *cell_loss = nullptr, *dldx = nullptr;
-    size_t sz_lamf_in = 0, sz_lamf_out = 0, sz_lamu = 0, sz_lamF = 0, sz_up = 0, sz_rhop = 0, sz_lamX = 0, sz_lamFv = 0;
+    void *seg_F = nullptr, *seg_u = nullptr, *seg_Fv = nullptr, *seg_anc_i = nullptr, *seg_anc_t = nullptr;
+    void *seg_perm = nullptr, *seg_start = nullptr;
+    size_t sz_seg_F = 0, sz_seg_u = 0, sz_seg_Fv = 0, sz_seg_anc_i = 0, sz_seg_anc_t = 0, sz_seg_perm = 0, sz_seg_start = 0;
+    size_t sz_lamf_in = 0, sz_lamf_out = 0, sz_lamu = 0, sz_lamF = 0, sz_lamX = 0, sz_lamFv = 0;
     size_t sz_grad = 0, sz_seg_f = 0, sz_seg_ctr = 0, sz_seg_off = 0, sz_fin_f = 0, sz_fin_u = 0, sz_fin_ctr = 0;
     size_t sz_fin_off = 0, sz_cell_loss = 0, sz_dldx = 0;
 };
@@ -158,6 +162,7 @@ struct hemo_sim {
     std::vector<void *> ck_f, ck_ctr, ck_off;
     double *c0 = nullptr;
     AdjBuffers adj;
+    std::map<long long, cudaGraphExec_t> seg_graphs;  // reverse-sweep segments by (length, buffer parity)
 };
 
 namespace {
@@ -513,12 +518,79 @@ int save_checkpoint(hemo_sim *s) {
     return HEMO_OK;
 }
 
+void clear_segment_graphs(hemo_sim *s) {
+    for (auto &kv : s->seg_graphs) cudaGraphExecDestroy(kv.second);
+    s->seg_graphs.clear();
+}
+
 void *grow(hemo_sim *s, void *&p, size_t &have, size_t need) {
     if (have >= need && p) return p;
     dfree(s, p);
     p = dalloc(s, need);
     have = p ? need : 0;
     return p;
+}
+
+// Enqueues one checkpoint segment of the reverse sweep: forward recomputation
+// of `len` steps from the state already restored (recording per step the
+// natural-layout populations, positions, force field, velocity, membrane
+// forces, anchors and bins), then the adjoint steps in reverse.  The
+// adjoint-of-f buffers alternate; `a` holds them in the order at entry.
+template <typename R>
+void enqueue_segment(hemo_sim *s, AdjView<R> a, int len, cudaStream_t st) {
+    AdjBuffers &b = s->adj;
+    const size_t N = (size_t)s->N, nv = (size_t)s->nv, nc = (size_t)s->ncell, rs = sizeof(R);
+    const size_t nb1 = (size_t)s->nbins + 1;
+    View<R> v = make_view<R>(s);
+    R *segf = (R *)b.seg_f;
+    for (int j = 0; j < len; ++j) {
+        cudaMemcpyAsync((double *)b.seg_ctr + 3 * nc * j, s->ctr, sizeof(double) * 3 * nc, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync((R *)b.seg_off + 3 * nv * j, s->off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
+        launch_copy_natural<R>(v, s->precision, j & 1, segf + Q * N * j, st);
+        enqueue_step<R>(s, j & 1, st);
+        cudaMemcpyAsync((R *)b.seg_F + 3 * N * j, s->F, rs * 3 * N, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync((R *)b.seg_u + 3 * N * j, s->u, rs * 3 * N, cudaMemcpyDeviceToDevice, st);
+        if (nv) {
+            cudaMemcpyAsync((R *)b.seg_Fv + 3 * nv * j, s->Fv, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync((int *)b.seg_anc_i + 3 * nv * j, s->anc_i, sizeof(int) * 3 * nv, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync((R *)b.seg_anc_t + 3 * nv * j, s->anc_t, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync((int *)b.seg_perm + nv * j, s->perm, sizeof(int) * nv, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync((int *)b.seg_start + nb1 * j, s->start, sizeof(int) * nb1, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    launch_copy_natural<R>(v, s->precision, len & 1, segf + Q * N * len, st);
+    for (int j = len - 1; j >= 0; --j) {
+        View<R> vj = v;  // the forward quantities of step n = s0 + j
+        vj.F = (R *)b.seg_F + 3 * N * j;
+        vj.Fv = (R *)b.seg_Fv + 3 * nv * j;
+        vj.off = (R *)b.seg_off + 3 * nv * j;
+        vj.ctr = (double *)b.seg_ctr + 3 * nc * j;
+        vj.anc_i = (int *)b.seg_anc_i + 3 * nv * j;
+        vj.anc_t = (R *)b.seg_anc_t + 3 * nv * j;
+        vj.perm = (int *)b.seg_perm + nv * j;
+        vj.start = (int *)b.seg_start + nb1 * j;
+        a.fn = segf + Q * N * j;
+        a.fn1 = segf + Q * N * (j + 1);
+        a.up = (R *)b.seg_u + 3 * N * j;
+        if (nv) {
+            View<R> vl = vj;  // spreading of lamX into lamu at every node
+            vl.Fv = a.lamX;
+            vl.F = a.lamu;
+            vl.g[0] = vl.g[1] = vl.g[2] = R(0);
+            vl.spread_all_nodes = 1;
+            launch_spread<R>(vl, st);                                       // lamu = S lamX
+            launch_vertex_field<R>(vj, a.up, a.lamX, a.lamX, nullptr, st);  // + (u' . lamX) grad w
+        } else {
+            cudaMemsetAsync(a.lamu, 0, rs * 3 * N, st);
+        }
+        launch_adj_moments<R>(vj, a, st);
+        launch_adj_collide<R>(vj, a, st);
+        if (nv) {
+            launch_vertex_field<R>(vj, a.lamF, vj.Fv, a.lamX, a.lamFv, st);  // lamFv = I lamF; + (F_v . lamF) grad w
+            launch_cell_adjoint<R>(vj, a, st);                               // + Hessian lamFv; moduli
+        }
+        std::swap(a.lamf_in, a.lamf_out);
+    }
 }
 
 template <typename R>
@@ -528,24 +600,35 @@ int backward_impl(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad)
     const long long t_end = s->steps_done;
     const int K = s->ck_every;
     const size_t N = (size_t)s->N, nv = (size_t)s->nv, rs = sizeof(R);
+    const size_t nv1 = std::max<size_t>(nv, 1), nc1 = (size_t)std::max(s->ncell, 1), nb1 = (size_t)s->nbins + 1;
     cudaStream_t st = s->stream;
     int rc;
     HEMO_CU(cudaStreamSynchronize(st));
-    // buffers (kept for reuse)
     AdjBuffers &b = s->adj;
-    if (!grow(s, b.lamf_in, b.sz_lamf_in, rs * Q * N) || !grow(s, b.lamf_out, b.sz_lamf_out, rs * Q * N) ||
-        !grow(s, b.lamu, b.sz_lamu, rs * 3 * N) || !grow(s, b.lamF, b.sz_lamF, rs * 3 * N) ||
-        !grow(s, b.up, b.sz_up, rs * 3 * N) || !grow(s, b.rhop, b.sz_rhop, rs * N) ||
-        !grow(s, b.lamX, b.sz_lamX, rs * 3 * std::max<size_t>(nv, 1)) ||
-        !grow(s, b.lamFv, b.sz_lamFv, rs * 3 * std::max<size_t>(nv, 1)) ||
-        !grow(s, b.grad, b.sz_grad, sizeof(double) * ng) ||
-        !grow(s, b.seg_f, b.sz_seg_f, rs * Q * N * (size_t)(K + 1)) ||
-        !grow(s, b.seg_ctr, b.sz_seg_ctr, sizeof(double) * 3 * std::max(s->ncell, 1) * (size_t)K) ||
-        !grow(s, b.seg_off, b.sz_seg_off, rs * 3 * std::max<size_t>(nv, 1) * (size_t)K) ||
-        !grow(s, b.fin_f, b.sz_fin_f, rs * Q * N) || !grow(s, b.fin_u, b.sz_fin_u, rs * 3 * N) ||
-        !grow(s, b.fin_ctr, b.sz_fin_ctr, sizeof(double) * 3 * std::max(s->ncell, 1)) ||
-        !grow(s, b.fin_off, b.sz_fin_off, rs * 3 * std::max<size_t>(nv, 1)))
+    bool moved = false;
+    auto need = [&](void *&p, size_t &have, size_t bytes) {
+        const void *old = p;
+        const bool ok = grow(s, p, have, bytes) != nullptr;
+        moved |= p != old;
+        return ok;
+    };
+    if (!need(b.lamf_in, b.sz_lamf_in, rs * Q * N) || !need(b.lamf_out, b.sz_lamf_out, rs * Q * N) ||
+        !need(b.lamu, b.sz_lamu, rs * 3 * N) || !need(b.lamF, b.sz_lamF, rs * 3 * N) ||
+        !need(b.lamX, b.sz_lamX, rs * 3 * nv1) || !need(b.lamFv, b.sz_lamFv, rs * 3 * nv1) ||
+        !need(b.grad, b.sz_grad, sizeof(double) * ng) ||
+        !need(b.seg_f, b.sz_seg_f, rs * Q * N * (size_t)(K + 1)) ||
+        !need(b.seg_F, b.sz_seg_F, rs * 3 * N * (size_t)K) || !need(b.seg_u, b.sz_seg_u, rs * 3 * N * (size_t)K) ||
+        !need(b.seg_ctr, b.sz_seg_ctr, sizeof(double) * 3 * nc1 * (size_t)K) ||
+        !need(b.seg_off, b.sz_seg_off, rs * 3 * nv1 * (size_t)K) ||
+        !need(b.seg_Fv, b.sz_seg_Fv, rs * 3 * nv1 * (size_t)K) ||
+        !need(b.seg_anc_i, b.sz_seg_anc_i, sizeof(int) * 3 * nv1 * (size_t)K) ||
+        !need(b.seg_anc_t, b.sz_seg_anc_t, rs * 3 * nv1 * (size_t)K) ||
+        !need(b.seg_perm, b.sz_seg_perm, sizeof(int) * nv1 * (size_t)K) ||
+        !need(b.seg_start, b.sz_seg_start, sizeof(int) * nb1 * (size_t)K) ||
+        !need(b.fin_f, b.sz_fin_f, rs * Q * N) || !need(b.fin_u, b.sz_fin_u, rs * 3 * N) ||
+        !need(b.fin_ctr, b.sz_fin_ctr, sizeof(double) * 3 * nc1) || !need(b.fin_off, b.sz_fin_off, rs * 3 * nv1))
         return fail(HEMO_ERR_OOM, "allocation of adjoint buffers failed");
+    if (moved) clear_segment_graphs(s);  // captured pointers are stale
     View<R> v = make_view<R>(s);
     // final state, restored at the end
     launch_copy_natural<R>(v, s->precision, (int)(t_end & 1), (R *)b.fin_f, st);
@@ -560,70 +643,43 @@ int backward_impl(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad)
     }
     HEMO_CU(cudaMemsetAsync(b.lamf_in, 0, rs * Q * N, st));
     HEMO_CU(cudaMemsetAsync(b.grad, 0, sizeof(double) * ng, st));
-    HEMO_CU(cudaMemcpyAsync(b.up, s->u, rs * 3 * N, cudaMemcpyDeviceToDevice, st));  // wall velocity at walls
     AdjView<R> a{};
-    a.lamf_in = (R *)b.lamf_in;
-    a.lamf_out = (R *)b.lamf_out;
     a.lamu = (R *)b.lamu;
     a.lamF = (R *)b.lamF;
-    a.up = (R *)b.up;
-    a.rhop = (R *)b.rhop;
     a.lamX = (R *)b.lamX;
     a.lamFv = (R *)b.lamFv;
     a.grad = (double *)b.grad;
     a.ntypes = nt;
-    View<R> vl = v;  // spreading of lamX into lamu at every node
-    vl.Fv = a.lamX;
-    vl.F = a.lamu;
-    vl.g[0] = vl.g[1] = vl.g[2] = R(0);
-    vl.spread_all_nodes = 1;
+    int in_first = 0;  // which buffer holds the adjoint of f at the current step
     const long long nseg = (t_end - s->rec_start + K - 1) / K;
-    R *segf = (R *)b.seg_f;
     for (long long seg = nseg - 1; seg >= 0; --seg) {
         const long long s0 = s->rec_start + seg * K, s1 = std::min<long long>(s0 + K, t_end);
         const int len = (int)(s1 - s0);
-        // forward recomputation of the segment from its checkpoint
         launch_restore_natural<R>(v, s->precision, 0, (const R *)s->ck_f[seg], st);
         HEMO_CU(cudaMemcpyAsync(s->ctr, s->ck_ctr[seg], sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, st));
         HEMO_CU(cudaMemcpyAsync(s->off, s->ck_off[seg], rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
-        s->steps_done = s0;
-        for (int j = 0; j < len; ++j) {
-            HEMO_CU(cudaMemcpyAsync((double *)b.seg_ctr + 3 * (size_t)s->ncell * j, s->ctr, sizeof(double) * 3 * s->ncell,
-                                    cudaMemcpyDeviceToDevice, st));
-            HEMO_CU(cudaMemcpyAsync((R *)b.seg_off + 3 * nv * j, s->off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
-            launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), segf + Q * N * j, st);
-            HEMO_CU(cudaGraphLaunch(s->graph[s->steps_done & 1], st));
-            ++s->steps_done;
+        a.lamf_in = (R *)(in_first ? b.lamf_out : b.lamf_in);
+        a.lamf_out = (R *)(in_first ? b.lamf_in : b.lamf_out);
+        const long long key = 2LL * len + in_first;
+        auto it = s->seg_graphs.find(key);
+        if (it == s->seg_graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            const bool timing = s->timing;  // no phase-event nodes in the reverse sweep
+            s->timing = false;
+            HEMO_CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+            enqueue_segment<R>(s, a, len, s->cap);
+            cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+            s->timing = timing;
+            if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("segment capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("segment instantiate: ") + cudaGetErrorString(e));
+            it = s->seg_graphs.emplace(key, ge).first;
         }
-        launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), segf + Q * N * len, st);
-        // reverse sweep over the segment
-        for (int j = len - 1; j >= 0; --j) {
-            HEMO_CU(cudaMemcpyAsync(s->ctr, (double *)b.seg_ctr + 3 * (size_t)s->ncell * j, sizeof(double) * 3 * s->ncell,
-                                    cudaMemcpyDeviceToDevice, st));
-            HEMO_CU(cudaMemcpyAsync(s->off, (R *)b.seg_off + 3 * nv * j, rs * 3 * nv, cudaMemcpyDeviceToDevice, st));
-            a.fn = segf + Q * N * j;
-            a.fn1 = segf + Q * N * (j + 1);
-            if (s->ncell) {
-                launch_cell_forces<R>(v, 0, nullptr, st);  // F_v at X_n
-                launch_bins<R>(v, st, false);
-                launch_spread<R>(v, st);                   // F_n
-            }
-            launch_adj_rho_u<R>(v, a, st);                 // rho', u' of f_{n+1} with F_n
-            if (s->ncell) {
-                launch_spread<R>(vl, st);                                  // lamu = S lamX
-                launch_vertex_field<R>(v, a.up, a.lamX, a.lamX, nullptr, st);  // + (u' . lamX) grad w
-            } else {
-                HEMO_CU(cudaMemsetAsync(a.lamu, 0, rs * 3 * N, st));
-            }
-            launch_adj_moments<R>(v, a, st);
-            launch_adj_collide<R>(v, a, st);
-            if (s->ncell) {
-                launch_vertex_field<R>(v, a.lamF, v.Fv, a.lamX, a.lamFv, st);  // lamFv = I lamF; + (F_v . lamF) grad w
-                launch_cell_adjoint<R>(v, a, st);                              // + Hessian lamFv; moduli
-            }
-            std::swap(a.lamf_in, a.lamf_out);
-        }
-        HEMO_CU(cudaGetLastError());
+        HEMO_CU(cudaGraphLaunch(it->second, st));
+        if (len & 1) in_first ^= 1;
+        s->steps_done = s1;
     }
     // restore the final state
     launch_restore_natural<R>(v, s->precision, (int)(t_end & 1), (const R *)b.fin_f, st);
@@ -1064,6 +1120,7 @@ int hemo_get_phase_times(hemo_sim *s, float *ms, int *kernels_per_step) {
 void hemo_destroy(hemo_sim *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    clear_segment_graphs(s);
     for (int k = 0; k <= HEMO_NUM_PHASES; ++k)
         if (s->tev[k]) cudaEventDestroy(s->tev[k]);
     for (int p = 0; p < 2; ++p)

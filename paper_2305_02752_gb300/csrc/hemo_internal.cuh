@@ -130,8 +130,7 @@ template <typename R> struct AdjView {
     R *lamf_out;      // 19*N adjoint of f_n
     R *lamu;          // [3][N] adjoint of u_{n+1}
     R *lamF;          // [3][N] adjoint of F_n
-    R *up;            // [3][N] u_{n+1} (wall velocity at wall nodes)
-    R *rhop;          // N rho_{n+1}
+    R *up;            // [3][N] u_{n+1} as the forward step wrote it (wall velocity at walls)
     R *lamX;          // nv*3 adjoint of the vertex positions
     R *lamFv;         // nv*3 adjoint of the membrane forces
     double *grad;     // gradient accumulators (device)
@@ -159,7 +158,6 @@ template <typename R> void launch_set_vertices(const View<R> &v, const double *X
 // adjoint step (natural-layout arrays) and checkpoints
 template <typename R> void launch_copy_natural(const View<R> &v, int precision, int layout, R *out, cudaStream_t st);
 template <typename R> void launch_restore_natural(const View<R> &v, int precision, int layout, const R *in, cudaStream_t st);
-template <typename R> void launch_adj_rho_u(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
 template <typename R> void launch_adj_moments(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
 template <typename R> void launch_adj_collide(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
 template <typename R> void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st);

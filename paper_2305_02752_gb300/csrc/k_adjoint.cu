@@ -48,26 +48,8 @@ __device__ void block_add(double (&val)[K], double *acc) {
     }
 }
 
-// rho' and u' of the stored post-streaming populations f_{n+1} with F_n
-template <typename R>
-__global__ void adj_rho_u_kernel(View<R> v, AdjView<R> a) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= v.N || (v.ntype[n] & 0x7f)) return;
-    const size_t N = (size_t)v.N;
-    R rho = R(1), m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const R d = a.fn1[(size_t)i * N + n];
-        rho += d;
-        m[0] += R(cx(i)) * d;
-        m[1] += R(cy(i)) * d;
-        m[2] += R(cz(i)) * d;
-    }
-    a.rhop[n] = rho;
-    for (int k = 0; k < 3; ++k) a.up[k * N + n] = (m[k] + R(0.5) * v.F[k * N + n]) / rho;
-}
-
-// transpose of u' = (sum f' c + F/2) / rho' (fluid) and u' = u_wall (walls)
+// transpose of u' = (sum f' c + F/2) / rho' (fluid) and u' = u_wall (walls);
+// rho' from the stored post-streaming populations, u' as the forward wrote it
 template <typename R>
 __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -80,7 +62,9 @@ __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> 
             if (id >= 2) ds[0] = (double)(lu[0] * v.uw[id][0] + lu[1] * v.uw[id][1] + lu[2] * v.uw[id][2]);
             for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0);
         } else {
-            const R rho = a.rhop[n];
+            R rho = R(1);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rho += a.fn1[(size_t)i * N + n];
             const R u[3] = {a.up[n], a.up[N + n], a.up[2 * N + n]};
             const R lu_u = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
             const R ir = R(1) / rho;
@@ -176,11 +160,6 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
 }  // namespace
 
 template <typename R>
-void launch_adj_rho_u(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
-    adj_rho_u_kernel<R><<<nblocks(v.N, 256), 256, 0, st>>>(v, a);
-}
-
-template <typename R>
 void launch_adj_moments(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
     adj_moments_kernel<R><<<nblocks(v.N, 256), 256, 0, st>>>(v, a);
 }
@@ -191,7 +170,6 @@ void launch_adj_collide(const View<R> &v, const AdjView<R> &a, cudaStream_t st) 
 }
 
 #define HEMO_INST(R)                                                                  \
-    template void launch_adj_rho_u<R>(const View<R> &, const AdjView<R> &, cudaStream_t);   \
     template void launch_adj_moments<R>(const View<R> &, const AdjView<R> &, cudaStream_t); \
     template void launch_adj_collide<R>(const View<R> &, const AdjView<R> &, cudaStream_t);
 HEMO_INST(double)

@@ -180,12 +180,19 @@ def test_autograd_function():
 
 def test_adjoint_f32_close_to_f64():
     """FP32 storage and arithmetic (FP64 gradient accumulation): the
-    gradient agrees with the FP64 adjoint to 3e-2 relative per component.
-    Near the rest shape the area and volume terms scale with (A - A0) and
-    (V - V0), whose FP32 rounding (per-triangle terms in FP32) is about 1 %
-    of the small deformation after 40 steps."""
+    gradient agrees with the FP64 adjoint to 1e-2 relative per component.
+    The cell starts inflated by 1 % (placement map 1.01 I) so that the area
+    and volume moduli act on strains of a few percent: from the rest shape
+    (V - V0) / V0 stays near 2e-6 over 40 steps, which FP32 positions
+    (relative rounding 6e-8 per coordinate and step) resolve only to several
+    percent, in the forward run as much as in its adjoint."""
     cfg = small_case(steps=40)
+    cfg.rotations = cfg.rotations * 1.01
     _, g64 = gpu_adjoint(cfg, 40, every=10, precision='f64')
     _, g32 = gpu_adjoint(cfg, 40, every=10, precision='f32')
-    for k, (a, b) in enumerate(zip(g32, g64)):
-        assert abs(a - b) <= 3e-2 * abs(b), (k, a, b)
+    info = (list(g32), list(g64))
+    for k in range(5):  # moduli and wall-velocity scale
+        assert abs(g32[k] - g64[k]) <= 1e-2 * abs(g64[k]), (k,) + info
+    # body force: one vector, compared as such (its y component is a sum
+    # over the domain that cancels to 1e-4 of the x component)
+    assert np.linalg.norm(g32[5:] - g64[5:]) <= 1e-2 * np.linalg.norm(g64[5:]), info
