@@ -95,15 +95,16 @@ void hemo::set_last_error(const char *msg) { g_err = msg; }
 
 // device buffers of the reverse sweep (grown on demand, kept for reuse)
 struct AdjBuffers {
-    void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr;
-    void *lamX = nullptr, *lamFv = nullptr, *grad = nullptr, *seg_f = nullptr, *seg_ctr = nullptr, *seg_off = nullptr;
+    void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr, *amom = nullptr;
+    void *lamX = nullptr, *lamFv = nullptr, *grad = nullptr;
     void *fin_f = nullptr, *fin_u = nullptr, *fin_ctr = nullptr, *fin_off = nullptr, *cell_loss = nullptr, *dldx = nullptr;
-    void *seg_F = nullptr, *seg_u = nullptr, *seg_Fv = nullptr, *seg_anc_i = nullptr, *seg_anc_t = nullptr;
-    void *seg_perm = nullptr, *seg_start = nullptr;
-    size_t sz_seg_F = 0, sz_seg_u = 0, sz_seg_Fv = 0, sz_seg_anc_i = 0, sz_seg_anc_t = 0, sz_seg_perm = 0, sz_seg_start = 0;
-    size_t sz_lamf_in = 0, sz_lamf_out = 0, sz_lamu = 0, sz_lamF = 0, sz_lamX = 0, sz_lamFv = 0;
-    size_t sz_grad = 0, sz_seg_f = 0, sz_seg_ctr = 0, sz_seg_off = 0, sz_fin_f = 0, sz_fin_u = 0, sz_fin_ctr = 0;
-    size_t sz_fin_off = 0, sz_cell_loss = 0, sz_dldx = 0;
+    // per step of a segment
+    void *seg_rec = nullptr, *seg_F = nullptr, *seg_u = nullptr, *seg_off = nullptr, *seg_Fv = nullptr;
+    void *seg_anc_i = nullptr, *seg_anc_t = nullptr, *seg_perm = nullptr, *seg_start = nullptr;
+    size_t sz_lamf_in = 0, sz_lamf_out = 0, sz_lamu = 0, sz_lamF = 0, sz_amom = 0, sz_lamX = 0, sz_lamFv = 0, sz_grad = 0;
+    size_t sz_fin_f = 0, sz_fin_u = 0, sz_fin_ctr = 0, sz_fin_off = 0, sz_cell_loss = 0, sz_dldx = 0;
+    size_t sz_seg_rec = 0, sz_seg_F = 0, sz_seg_u = 0, sz_seg_off = 0, sz_seg_Fv = 0;
+    size_t sz_seg_anc_i = 0, sz_seg_anc_t = 0, sz_seg_perm = 0, sz_seg_start = 0;
 };
 
 struct hemo_sim {
@@ -262,8 +263,7 @@ View<R> make_view(hemo_sim *s) {
 }
 
 template <typename R>
-void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
-    View<R> v = make_view<R>(s);
+void enqueue_step(hemo_sim *s, const View<R> &v, int parity, cudaStream_t st) {
     auto mark = [&](int k) {
         if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
     };
@@ -282,6 +282,11 @@ void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
     mark(HEMO_PHASE_INTERP);
     if (s->ncell) launch_interpolate<R>(v, st);  // X^{n+1} = X^n + I[u](X^n)
     mark(HEMO_NUM_PHASES);
+}
+
+template <typename R>
+void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
+    enqueue_step<R>(s, make_view<R>(s), parity, st);
 }
 
 template <typename R>
@@ -532,47 +537,44 @@ void *grow(hemo_sim *s, void *&p, size_t &have, size_t need) {
 }
 
 // Enqueues one checkpoint segment of the reverse sweep: forward recomputation
-// of `len` steps from the state already restored (recording per step the
-// natural-layout populations, positions, force field, velocity, membrane
-// forces, anchors and bins), then the adjoint steps in reverse.  The
-// adjoint-of-f buffers alternate; `a` holds them in the order at entry.
+// of `len` steps from the state already restored, each step writing its force
+// field, velocity, membrane forces, anchors, bins, re-based offsets and the
+// collision density and velocity into the step's own slots, then the adjoint
+// steps in reverse.  The adjoint-of-f buffers alternate; `a` holds them in
+// the order at entry.
 template <typename R>
 void enqueue_segment(hemo_sim *s, AdjView<R> a, int len, cudaStream_t st) {
     AdjBuffers &b = s->adj;
-    const size_t N = (size_t)s->N, nv = (size_t)s->nv, nc = (size_t)s->ncell, rs = sizeof(R);
+    const size_t N = (size_t)s->N, nv = (size_t)s->nv;
     const size_t nb1 = (size_t)s->nbins + 1;
-    View<R> v = make_view<R>(s);
-    R *segf = (R *)b.seg_f;
-    for (int j = 0; j < len; ++j) {
-        cudaMemcpyAsync((double *)b.seg_ctr + 3 * nc * j, s->ctr, sizeof(double) * 3 * nc, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync((R *)b.seg_off + 3 * nv * j, s->off, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
-        launch_copy_natural<R>(v, s->precision, j & 1, segf + Q * N * j, st);
-        enqueue_step<R>(s, j & 1, st);
-        cudaMemcpyAsync((R *)b.seg_F + 3 * N * j, s->F, rs * 3 * N, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync((R *)b.seg_u + 3 * N * j, s->u, rs * 3 * N, cudaMemcpyDeviceToDevice, st);
-        if (nv) {
-            cudaMemcpyAsync((R *)b.seg_Fv + 3 * nv * j, s->Fv, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync((int *)b.seg_anc_i + 3 * nv * j, s->anc_i, sizeof(int) * 3 * nv, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync((R *)b.seg_anc_t + 3 * nv * j, s->anc_t, rs * 3 * nv, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync((int *)b.seg_perm + nv * j, s->perm, sizeof(int) * nv, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync((int *)b.seg_start + nb1 * j, s->start, sizeof(int) * nb1, cudaMemcpyDeviceToDevice, st);
+    const View<R> v = make_view<R>(s);
+    R *rec = (R *)b.seg_rec;
+    auto slot = [&](int j) {  // the quantities of step s0 + j
+        View<R> vj = v;
+        vj.u = (R *)b.seg_u + 3 * N * j;
+        vj.rec = rec + 4 * N * j;
+        if (s->ncell) {
+            vj.F = (R *)b.seg_F + 3 * N * j;
+            vj.Fv = (R *)b.seg_Fv + 3 * nv * j;
+            vj.anc_i = (int *)b.seg_anc_i + 3 * nv * j;
+            vj.anc_t = (R *)b.seg_anc_t + 3 * nv * j;
+            vj.perm = (int *)b.seg_perm + nv * j;
+            vj.start = (int *)b.seg_start + nb1 * j;
+            vj.off_rec = (R *)b.seg_off + 3 * nv * j;
         }
-    }
-    launch_copy_natural<R>(v, s->precision, len & 1, segf + Q * N * len, st);
+        return vj;
+    };
+    for (int j = 0; j < len; ++j) enqueue_step<R>(s, slot(j), j & 1, st);
+    launch_rho_out<R>(v, s->precision, len & 1, rec + 4 * N * len, st);  // density after the segment
     for (int j = len - 1; j >= 0; --j) {
-        View<R> vj = v;  // the forward quantities of step n = s0 + j
-        vj.F = (R *)b.seg_F + 3 * N * j;
-        vj.Fv = (R *)b.seg_Fv + 3 * nv * j;
+        View<R> vj = slot(j);
+        vj.rec = nullptr;
+        vj.off_rec = nullptr;
         vj.off = (R *)b.seg_off + 3 * nv * j;
-        vj.ctr = (double *)b.seg_ctr + 3 * nc * j;
-        vj.anc_i = (int *)b.seg_anc_i + 3 * nv * j;
-        vj.anc_t = (R *)b.seg_anc_t + 3 * nv * j;
-        vj.perm = (int *)b.seg_perm + nv * j;
-        vj.start = (int *)b.seg_start + nb1 * j;
-        a.fn = segf + Q * N * j;
-        a.fn1 = segf + Q * N * (j + 1);
-        a.up = (R *)b.seg_u + 3 * N * j;
-        if (nv) {
+        a.rec = rec + 4 * N * j;
+        a.rho1 = rec + 4 * N * (j + 1);
+        a.up = vj.u;
+        if (s->ncell) {
             View<R> vl = vj;  // spreading of lamX into lamu at every node
             vl.Fv = a.lamX;
             vl.F = a.lamu;
@@ -581,11 +583,11 @@ void enqueue_segment(hemo_sim *s, AdjView<R> a, int len, cudaStream_t st) {
             launch_spread<R>(vl, st);                                       // lamu = S lamX
             launch_vertex_field<R>(vj, a.up, a.lamX, a.lamX, nullptr, st);  // + (u' . lamX) grad w
         } else {
-            cudaMemsetAsync(a.lamu, 0, rs * 3 * N, st);
+            cudaMemsetAsync(a.lamu, 0, sizeof(R) * 3 * N, st);
         }
         launch_adj_moments<R>(vj, a, st);
         launch_adj_collide<R>(vj, a, st);
-        if (nv) {
+        if (s->ncell) {
             launch_vertex_field<R>(vj, a.lamF, vj.Fv, a.lamX, a.lamFv, st);  // lamFv = I lamF; + (F_v . lamF) grad w
             launch_cell_adjoint<R>(vj, a, st);                               // + Hessian lamFv; moduli
         }
@@ -615,10 +617,10 @@ int backward_impl(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad)
     if (!need(b.lamf_in, b.sz_lamf_in, rs * Q * N) || !need(b.lamf_out, b.sz_lamf_out, rs * Q * N) ||
         !need(b.lamu, b.sz_lamu, rs * 3 * N) || !need(b.lamF, b.sz_lamF, rs * 3 * N) ||
         !need(b.lamX, b.sz_lamX, rs * 3 * nv1) || !need(b.lamFv, b.sz_lamFv, rs * 3 * nv1) ||
-        !need(b.grad, b.sz_grad, sizeof(double) * ng) ||
-        !need(b.seg_f, b.sz_seg_f, rs * Q * N * (size_t)(K + 1)) ||
-        !need(b.seg_F, b.sz_seg_F, rs * 3 * N * (size_t)K) || !need(b.seg_u, b.sz_seg_u, rs * 3 * N * (size_t)K) ||
-        !need(b.seg_ctr, b.sz_seg_ctr, sizeof(double) * 3 * nc1 * (size_t)K) ||
+        !need(b.grad, b.sz_grad, sizeof(double) * ng) || !need(b.amom, b.sz_amom, rs * 4 * N) ||
+        !need(b.seg_rec, b.sz_seg_rec, rs * 4 * N * (size_t)(K + 1)) ||
+        !need(b.seg_F, b.sz_seg_F, rs * 3 * N * (size_t)(s->ncell ? K : 1)) ||
+        !need(b.seg_u, b.sz_seg_u, rs * 3 * N * (size_t)K) ||
         !need(b.seg_off, b.sz_seg_off, rs * 3 * nv1 * (size_t)K) ||
         !need(b.seg_Fv, b.sz_seg_Fv, rs * 3 * nv1 * (size_t)K) ||
         !need(b.seg_anc_i, b.sz_seg_anc_i, sizeof(int) * 3 * nv1 * (size_t)K) ||
@@ -646,6 +648,7 @@ int backward_impl(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad)
     AdjView<R> a{};
     a.lamu = (R *)b.lamu;
     a.lamF = (R *)b.lamF;
+    a.amom = (R *)b.amom;
     a.lamX = (R *)b.lamX;
     a.lamFv = (R *)b.lamFv;
     a.grad = (double *)b.grad;

@@ -118,19 +118,24 @@ template <typename R> struct View {
     R *tiles;                  // nbins*3*11^3 per-bin spreading tiles
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
+    // recording for the reverse sweep (null in plain steps)
+    R *rec;                    // [4][N] collision density and velocity at fluid nodes; when set the
+                               // moments kernel also writes the wall velocity into u at wall nodes
+    R *off_rec;                // nv*3 re-based offsets as the membrane forces saw them
 };
 
 // Adjoint (reverse-mode) state of one step; all lattice arrays natural
 // layout, SoA, in R.  Gradient slots: per mesh type t: 4t + (k_link, k_bend,
 // k_area, k_volume); then wall-velocity scale, g_x, g_y, g_z.
 template <typename R> struct AdjView {
-    const R *fn;      // 19*N deviations of f_n (natural layout)
-    const R *fn1;     // 19*N deviations of f_{n+1}
-    R *lamf_in;       // 19*N adjoint of f_{n+1} (updated in place by the moments transpose)
+    const R *rec;     // [4][N] collision density and velocity of step n (fluid nodes)
+    const R *rho1;    // N: density of f_{n+1} (fluid nodes)
+    const R *up;      // [3][N] u_{n+1} as the forward step wrote it (wall velocity at walls)
+    R *amom;          // [4][N] moments transpose per node: lamu / rho' (3), -(lamu . u') / rho'
+    R *lamf_in;       // 19*N adjoint of f_{n+1}, without the moments term
     R *lamf_out;      // 19*N adjoint of f_n
     R *lamu;          // [3][N] adjoint of u_{n+1}
     R *lamF;          // [3][N] adjoint of F_n
-    R *up;            // [3][N] u_{n+1} as the forward step wrote it (wall velocity at walls)
     R *lamX;          // nv*3 adjoint of the vertex positions
     R *lamFv;         // nv*3 adjoint of the membrane forces
     double *grad;     // gradient accumulators (device)

@@ -10,6 +10,8 @@
 //   velocity: u'(x) = (sum f' c + F/2) / rho'(x); u' = u_wall at wall nodes.
 // The adjoint runs these backwards: the moments transpose adds
 // lambda_u (c - u') / rho' to lambda_f' and lambda_u / (2 rho') to lambda_F;
+// the forward step records rho and the collision velocity at each fluid node
+// so that the collision transpose needs no populations;
 // the streaming transpose pulls lambda_f* from the node each population
 // streamed to (bounce-back: from the node itself); the collision transpose
 // goes through (rho, u):
@@ -48,8 +50,10 @@ __device__ void block_add(double (&val)[K], double *acc) {
     }
 }
 
-// transpose of u' = (sum f' c + F/2) / rho' (fluid) and u' = u_wall (walls);
-// rho' from the stored post-streaming populations, u' as the forward wrote it
+// transpose of u' = (sum f' c + F/2) / rho' (fluid) and u' = u_wall (walls).
+// The contribution to the adjoint of f'_i at a fluid node is
+// (c_i . lamu - lamu . u') / rho'; it is kept per node as four numbers and
+// added by the streaming transpose when it pulls the population.
 template <typename R>
 __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,25 +65,22 @@ __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> 
         if (id) {
             if (id >= 2) ds[0] = (double)(lu[0] * v.uw[id][0] + lu[1] * v.uw[id][1] + lu[2] * v.uw[id][2]);
             for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0);
+            for (int k = 0; k < 4; ++k) a.amom[k * N + n] = R(0);
         } else {
-            R rho = R(1);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) rho += a.fn1[(size_t)i * N + n];
-            const R u[3] = {a.up[n], a.up[N + n], a.up[2 * N + n]};
-            const R lu_u = lu[0] * u[0] + lu[1] * u[1] + lu[2] * u[2];
-            const R ir = R(1) / rho;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const R lc = R(cx(i)) * lu[0] + R(cy(i)) * lu[1] + R(cz(i)) * lu[2];
-                a.lamf_in[(size_t)i * N + n] += (lc - lu_u) * ir;
+            const R ir = R(1) / a.rho1[n];
+            const R lu_u = lu[0] * a.up[n] + lu[1] * a.up[N + n] + lu[2] * a.up[2 * N + n];
+            for (int k = 0; k < 3; ++k) {
+                a.amom[k * N + n] = lu[k] * ir;
+                a.lamF[k * N + n] = R(0.5) * lu[k] * ir;
             }
-            for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0.5) * lu[k] * ir;
+            a.amom[3 * N + n] = -lu_u * ir;
         }
     }
     block_add<1>(ds, a.grad + 4 * a.ntypes);
 }
 
-// transpose of streaming (pull) and of the collision at fluid node n
+// transpose of streaming (pull, with the moments term of the pulled
+// population) and of the collision at fluid node n
 template <typename R>
 __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,20 +90,11 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
         const uint8_t nt = v.ntype[n];
         const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
         const Nbr o = make_nbr(v, n);
-        // forward collision quantities
-        R d[Q];
-        R rho = R(1), m[3] = {R(0), R(0), R(0)};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            d[i] = a.fn[(size_t)i * N + n];
-            rho += d[i];
-            m[0] += R(cx(i)) * d[i];
-            m[1] += R(cy(i)) * d[i];
-            m[2] += R(cz(i)) * d[i];
-        }
+        // forward collision quantities, as the collision computed them
+        const R rho = a.rec[n];
+        const R u[3] = {a.rec[N + n], a.rec[2 * N + n], a.rec[3 * N + n]};
         const R F[3] = {v.F[n], v.F[N + n], v.F[2 * N + n]};
         const R ir = R(1) / rho;
-        const R u[3] = {(m[0] + R(0.5) * F[0]) * ir, (m[1] + R(0.5) * F[1]) * ir, (m[2] + R(0.5) * F[2]) * ir};
         const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const R om = v.omega, s0 = R(1) - R(0.5) * om;
         // pulled adjoint of the post-collision populations
@@ -112,14 +104,21 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const int code = link_code(lk, j);
-            if (code) {
-                const R lj = a.lamf_in[(size_t)opp(j) * N + n];
+            if (code) {  // bounced back into opp(j) at n
+                const R lj = a.lamf_in[(size_t)opp(j) * N + n] -
+                             (R(cx(j)) * a.amom[n] + R(cy(j)) * a.amom[N + n] + R(cz(j)) * a.amom[2 * N + n]) +
+                             a.amom[3 * N + n];
                 ls[j] = lj;
                 const R cw = R(cx(j)) * v.uw[code][0] + R(cy(j)) * v.uw[code][1] + R(cz(j)) * v.uw[code][2];
                 lrho -= R(6) * R(wgt(j)) * cw * lj;
                 dsw -= 6.0 * wgt(j) * (double)rho * (double)cw * (double)lj;
             } else {
-                ls[j] = a.lamf_in[(size_t)j * N + n + o.of(cx(j), cy(j), cz(j))];
+                const size_t m = n + o.of(cx(j), cy(j), cz(j));
+                R lj = a.lamf_in[(size_t)j * N + m] + a.amom[3 * N + m];
+                if (cx(j)) lj += cx(j) > 0 ? a.amom[m] : -a.amom[m];
+                if (cy(j)) lj += cy(j) > 0 ? a.amom[N + m] : -a.amom[N + m];
+                if (cz(j)) lj += cz(j) > 0 ? a.amom[2 * N + m] : -a.amom[2 * N + m];
+                ls[j] = lj;
             }
         }
         R grho = R(0), gu[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)};

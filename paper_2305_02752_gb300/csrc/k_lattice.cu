@@ -74,6 +74,12 @@ __global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
     const R ux = (mx + R(0.5) * Fx) * inv;
     const R uy = (my + R(0.5) * Fy) * inv;
     const R uz = (mz + R(0.5) * Fz) * inv;
+    if (v.rec) {
+        v.rec[n] = rho;
+        v.rec[N + n] = ux;
+        v.rec[2 * N + n] = uy;
+        v.rec[3 * N + n] = uz;
+    }
     const R uu = ux * ux + uy * uy + uz * uz;
     const R om = v.omega;
     const R src = R(1) - R(0.5) * om;
@@ -111,7 +117,15 @@ __global__ void __launch_bounds__(256) moments_kernel(View<R> v) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= v.N) return;
     const uint8_t nt = v.ntype[n];
-    if (nt & 0x7f) return;
+    if (nt & 0x7f) {
+        if (v.rec) {  // recording into a fresh velocity buffer
+            const int id = nt & 0x7f;
+            v.u[n] = v.uw[id][0];
+            v.u[(size_t)v.N + n] = v.uw[id][1];
+            v.u[2 * (size_t)v.N + n] = v.uw[id][2];
+        }
+        return;
+    }
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr o = make_nbr(v, n);
     R d[Q];

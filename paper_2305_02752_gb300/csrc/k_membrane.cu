@@ -117,7 +117,10 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
             const R r = R((double)o[k] - mean[k]);
             xs[3 * i + k] = r;
             fs[3 * i + k] = R(0);
-            if (mode == 0) o[k] = r;
+            if (mode == 0) {
+                o[k] = r;
+                if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r;
+            }
         }
     }
     if (mode == 0 && threadIdx.x == 0)
@@ -264,19 +267,8 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
     R *ft = xt + 3 * v.max_nv;                  // derivative of the forces along lamFv
     R *tn = ft + 3 * v.max_nv;                  // per triangle: n (3), dn (3), 1/|n|^2, its derivative
     __shared__ double scratch[6][32];
-    // the same re-basing as the forward step, so that the linearisation
-    // point carries the forward's rounding
-    double mean[3] = {0, 0, 0};
-    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-        const R *o = v.off + 3 * (size_t)(first + i);
-        mean[0] += (double)o[0];
-        mean[1] += (double)o[1];
-        mean[2] += (double)o[2];
-    }
-    block_sum<3>(mean, scratch);
-    for (int k = 0; k < 3; ++k) mean[k] /= m.nv;
-    for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) {
-        xs[i] = R((double)v.off[3 * (size_t)first + i] - mean[i % 3]);
+    for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) {  // re-based offsets of the forward step
+        xs[i] = v.off[3 * (size_t)first + i];
         xt[i] = a.lamFv[3 * (size_t)first + i];
         ft[i] = R(0);
     }
