@@ -75,7 +75,14 @@ typedef struct {
     hemo_alloc_fn alloc;         /* optional device memory provider                */
     hemo_free_fn release;
     void *alloc_ctx;
+    unsigned options;            /* bit mask of HEMO_OPT_*; 0 = defaults           */
 } hemo_lattice_desc;
+
+/* HEMO_OPT_NO_STAGING: collide every node with the per-node kernel instead of
+ * staging tiles of wall-free rows through shared memory by bulk copies on odd
+ * steps (whose reads and writes are shifted by one node in x).  The results
+ * are the same; the option exists for comparison and measurement. */
+enum { HEMO_OPT_NO_STAGING = 1u };
 
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
  * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
@@ -149,6 +156,13 @@ int hemo_get_sizes(const hemo_sim *sim, long long *n_nodes, long long *n_vertice
                    int *n_bins);
 
 /* ---- inspection of integer work and raw state (tests, tools) ----------- */
+
+/* How the collision is split (see HEMO_OPT_NO_STAGING): plan[0] tiles of
+ * wall-free rows staged through shared memory, plan[1] other rows with fluid
+ * (per-node kernel), plan[2] rows per tile at most, plan[3] ring stages.
+ * All zero when every node goes through the per-node kernel.  plan: host, 4
+ * ints, caller-owned. */
+int hemo_get_lattice_plan(const hemo_sim *sim, int *plan);
 
 /* The library's D3Q19 velocity order: c (host, 19*3 int), w (host, 19). */
 int hemo_velocity_set(int32_t *c, double *w);

@@ -123,6 +123,11 @@ struct hemo_sim {
     uint8_t *ntype = nullptr;
     uint64_t *links = nullptr;
     void *F = nullptr, *u = nullptr;
+    unsigned options = 0;
+    // staged collision (tiles of wall-free rows), see plan_rows
+    int2 *rtiles = nullptr;
+    int *erows = nullptr;
+    int ntiles = 0, nerows = 0, tile_rows = 0, tile_stages = 0, tile_grid = 0, tile_smem = 0;
     // cells (host until finalised)
     std::vector<HostMesh> meshes;
     std::vector<int> cell_type, cell_first, vcell;
@@ -202,6 +207,7 @@ size_t tsize(const hemo_sim *s) {
 int status_code(unsigned st) {
     if (st & ST_NUMERIC) return fail(HEMO_ERR_NUMERIC, "device status: non-finite or |u| > 0.3 velocity, or a link stretched past its maximum strain");
     if (st & ST_DOMAIN) return fail(HEMO_ERR_DOMAIN, "device status: a vertex left the lattice across a non-periodic axis");
+    if (st & ST_TIMEOUT) return fail(HEMO_ERR_CUDA, "device status: a copy pipeline wait timed out");
     return HEMO_OK;
 }
 
@@ -229,6 +235,14 @@ View<R> make_view(hemo_sim *s) {
     v.F = (R *)s->F;
     v.u = (R *)s->u;
     v.omega = R(1.0 / s->tau);
+    v.rtiles = s->rtiles;
+    v.ntiles = s->ntiles;
+    v.tile_rows = s->tile_rows;
+    v.tile_stages = s->tile_stages;
+    v.tile_grid = s->tile_grid;
+    v.tile_smem = s->tile_smem;
+    v.erows = s->erows;
+    v.nerows = s->nerows;
     for (int d = 0; d < 3; ++d) {
         v.g[d] = R(s->g[d]);
         v.uw[0][d] = R(0);
@@ -781,6 +795,92 @@ int hemo_velocity_set(int32_t *c, double *w) {
     return HEMO_OK;
 }
 
+// Rows (x-lines, index y + ny z) for the staged collision.  A row is
+// interior when it and the eight rows around it (the y-z offsets of D3Q19)
+// lie in the lattice, or wrap on periodic axes, and hold fluid only, with x
+// periodic: none of its populations meets a wall.  Runs of interior rows
+// within a z-plane are cut into tiles of at most tile_rows rows; the rows
+// that are not interior but hold fluid go to the per-node kernel.  Staging
+// needs 16-byte aligned rows (bulk copies) and at least two stages of the
+// ring in shared memory; FP64 keeps the per-node kernel (its collision is
+// arithmetic-bound on this GPU).
+constexpr size_t TILE_RING_BYTES = 54 * 1024;
+
+int plan_rows(hemo_sim *s, const uint8_t *mask) {
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    const size_t S = tsize(s), Rb = rsize(s);
+    if (is_f64(s) || (s->options & HEMO_OPT_NO_STAGING) || !s->per[0]) return HEMO_OK;
+    if (((size_t)nx * S) % 16 || ((size_t)nx * Rb) % 16) return HEMO_OK;
+    // whole rows of at most 256 nodes per tile (one per thread; the stage
+    // layout has room for 256), at most 54 KiB of ring per CTA so that four
+    // CTAs share an SM
+    if (nx > 256) return HEMO_OK;
+    const size_t per_node = Q * S + 3 * Rb;
+    const int k = std::min(256 / nx, ny);
+    const size_t stage = 256 * per_node;
+    const int stages = (int)std::min<size_t>(4, (TILE_RING_BYTES - 128) / stage);
+    if (stages < 2) return HEMO_OK;
+    std::vector<uint8_t> fluid((size_t)ny * nz, 1), any((size_t)ny * nz, mask ? 0 : 1);
+    if (mask)
+        for (int r = 0; r < ny * nz; ++r)
+            for (int x = 0; x < nx; ++x) {
+                const bool fl = mask[(size_t)r * nx + x] == 0;
+                fluid[r] &= fl;
+                any[r] |= fl;
+            }
+    auto row_fluid = [&](int y, int z) {
+        if (y < 0 || y >= ny) {
+            if (!s->per[1]) return false;
+            y = (y + ny) % ny;
+        }
+        if (z < 0 || z >= nz) {
+            if (!s->per[2]) return false;
+            z = (z + nz) % nz;
+        }
+        return fluid[(size_t)y + (size_t)ny * z] != 0;
+    };
+    auto interior = [&](int y, int z) {
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                if (!row_fluid(y + dy, z + dz)) return false;
+        return true;
+    };
+    std::vector<int2> tiles;
+    std::vector<int> erows;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny;) {
+            if (interior(y, z)) {
+                int len = 1;
+                while (len < k && y + len < ny && interior(y + len, z)) ++len;
+                tiles.push_back(make_int2(y + ny * z, len));
+                y += len;
+            } else {
+                if (any[(size_t)y + (size_t)ny * z]) erows.push_back(y + ny * z);
+                ++y;
+            }
+        }
+    if (tiles.empty()) return HEMO_OK;
+    int dev = 0, nsm = 0;
+    HEMO_CU(cudaGetDevice(&dev));
+    HEMO_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int smem = (int)(128 + stages * stage);
+    HEMO_CU(set_tile_smem_limit(s->precision, (int)TILE_RING_BYTES));  // the cap of every plan
+    s->rtiles = (int2 *)dalloc(s, sizeof(int2) * tiles.size());
+    s->erows = (int *)dalloc(s, sizeof(int) * std::max<size_t>(erows.size(), 1));
+    if (!s->rtiles || !s->erows) return fail(HEMO_ERR_OOM, "allocation of the row tables failed");
+    HEMO_CU(cudaMemcpyAsync(s->rtiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
+    if (!erows.empty())
+        HEMO_CU(cudaMemcpyAsync(s->erows, erows.data(), sizeof(int) * erows.size(), cudaMemcpyHostToDevice, s->stream));
+    HEMO_CU(cudaStreamSynchronize(s->stream));  // the host vectors go out of scope
+    s->ntiles = (int)tiles.size();
+    s->nerows = (int)erows.size();
+    s->tile_rows = k;
+    s->tile_stages = stages;
+    s->tile_grid = std::min(s->ntiles, 4 * std::max(nsm, 1));
+    s->tile_smem = smem;
+    return HEMO_OK;
+}
+
 int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
     if (!d || !out) return fail(HEMO_ERR_ARG, "hemo_create_lattice: null pointer");
     *out = nullptr;
@@ -809,6 +909,7 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
         s->uw[1][k] = d->wall_velocity[1][k];
     }
     s->tau = d->tau;
+    s->options = d->options;
     s->stream = (cudaStream_t)d->cuda_stream;
     s->alloc = d->alloc;
     s->release = d->release;
@@ -843,6 +944,7 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
                                  : cudaMemsetAsync(s->ntype, 0, (size_t)N, st);
     if (e != cudaSuccess) return bail(fail(HEMO_ERR_CUDA, std::string("wall mask upload: ") + cudaGetErrorString(e)));
     launch_build_links(s->nx, s->ny, s->nz, s->per, s->ntype, s->links, st);
+    if (int rc = plan_rows(s, d->wall_mask)) return bail(rc);
     if (is_f64(s)) launch_init_equilibrium<double>(make_view<double>(s), s->precision, nullptr, st);
     else launch_init_equilibrium<float>(make_view<float>(s), s->precision, nullptr, st);
     e = cudaStreamSynchronize(st);
@@ -985,6 +1087,15 @@ int hemo_get_sizes(const hemo_sim *s, long long *n_nodes, long long *n_vertices,
     if (n_vertices) *n_vertices = s->nv;
     if (n_cells) *n_cells = s->ncell;
     if (n_bins) *n_bins = s->nbins;
+    return HEMO_OK;
+}
+
+int hemo_get_lattice_plan(const hemo_sim *s, int *plan) {
+    if (!s || !plan) return fail(HEMO_ERR_ARG, "null pointer");
+    plan[0] = s->ntiles;
+    plan[1] = s->ntiles ? s->nerows : 0;
+    plan[2] = s->tile_rows;
+    plan[3] = s->tile_stages;
     return HEMO_OK;
 }
 

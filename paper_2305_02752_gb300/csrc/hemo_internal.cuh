@@ -17,6 +17,7 @@ constexpr int MAX_TYPES = 8;        // membrane mesh types per simulation
 // status bits raised on the device
 constexpr unsigned ST_NUMERIC = 1u;
 constexpr unsigned ST_DOMAIN = 2u;
+constexpr unsigned ST_TIMEOUT = 4u;  // a pipeline wait gave up
 constexpr float U_LIMIT2 = 0.09f;   // |u|^2 above which the step is unstable
 
 // ---------------------------------------------------------------------------
@@ -118,6 +119,12 @@ template <typename R> struct View {
     R *tiles;                  // nbins*3*11^3 per-bin spreading tiles
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
+    // staged collision: tiles {first row, rows} of wall-free rows (x-lines,
+    // row index y + ny z) and the other rows that hold fluid
+    const int2 *rtiles;
+    int ntiles, tile_rows, tile_stages, tile_grid, tile_smem;
+    const int *erows;
+    int nerows;
     // recording for the reverse sweep (null in plain steps)
     R *rec;                    // [4][N] collision density and velocity at fluid nodes; when set the
                                // moments kernel also writes the wall velocity into u at wall nodes
@@ -144,6 +151,8 @@ template <typename R> struct AdjView {
 
 // launchers (R = double for HEMO_F64, float otherwise)
 template <typename R> void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st);
+// allows the staged collision kernels of a precision `bytes` of dynamic shared memory
+cudaError_t set_tile_smem_limit(int precision, int bytes);
 template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);
 template <typename R> void launch_init_equilibrium(const View<R> &v, int precision, const double *u_dev, cudaStream_t st);
 template <typename R> void launch_populations_out(const View<R> &v, int precision, int parity, double *out, cudaStream_t st);

@@ -48,66 +48,369 @@ __device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, 
     }
 }
 
-template <typename T, typename R, int PARITY>
-__global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= v.N) return;
-    const uint8_t nt = v.ntype[n];
-    if (nt & 0x7f) return;  // wall node
-    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
-    const Nbr o = make_nbr(v, n);
-    R d[Q];
-    load_pops<T, R, PARITY>(v, n, lk, o, d);
+// BGK collision with the Guo source at one node: from the 19 deviations d
+// arriving at the node and the force F, the post-collision deviations p
+// (before any wall term), the density and the velocity with F/2.
+//
+// Per direction, with d^eq = f^eq - w and S the Guo source,
+//   p = (1 - om) d + om d^eq + S,
+//   d^eq = w (rho - 1) + w rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u),
+//   S = (1 - om/2) w (3 (c.F - u.F) + 9 (c.u)(c.F)).
+// Directions come in opposite pairs (c, -c): the terms even in c are shared
+// and the odd ones change sign, so each pair costs one c.u and one c.F.  In
+// exact arithmetic the collision keeps the mass and adds F to the momentum;
+// the rest population and the axis pairs' odd parts are computed so that
+// rounded arithmetic keeps both too.
+template <typename R>
+__device__ __forceinline__ R recip(R x) {
+    if constexpr (std::is_same<R, float>::value) return __frcp_rn(x);  // correctly rounded, as 1 / x
+    else return R(1) / x;
+}
 
-    // moments of the deviations: rho = 1 + sum d, rho u = sum d c + F/2
-    R rho = R(1), mx = R(0), my = R(0), mz = R(0);
+template <typename R>
+__device__ __forceinline__ void bgk_guo(const R (&d)[Q], R Fx, R Fy, R Fz, R om, R (&p)[Q], R &rho, R &ux, R &uy,
+                                        R &uz) {
+    // moments of the deviations: rho - 1 = sum d (summed without the 1, so
+    // that FP32 keeps the density deviation's own precision), rho u = sum d c
+    // + F/2
+    R drho = R(0), mx = R(0), my = R(0), mz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        rho += d[i];
+        drho += d[i];
         if (cx(i)) mx += cx(i) > 0 ? d[i] : -d[i];
         if (cy(i)) my += cy(i) > 0 ? d[i] : -d[i];
         if (cz(i)) mz += cz(i) > 0 ? d[i] : -d[i];
     }
+    rho = R(1) + drho;
+    const R inv = recip(rho);
+    ux = (mx + R(0.5) * Fx) * inv;
+    uy = (my + R(0.5) * Fy) * inv;
+    uz = (mz + R(0.5) * Fz) * inv;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R om1 = R(1) - om, src = R(1) - R(0.5) * om;
+    // even part A + (c.u) (B (c.u) + C (c.F)) of om d^eq + S and odd part
+    // G (c.u) + H (c.F), for the axis weight 1/18; the diagonal weight 1/36
+    // is exactly half of it
+    const R w1 = R(1.0 / 18.0), ow = om * w1, sw = src * w1;
+    const R A = ow * (drho - R(1.5) * rho * uu) - R(3) * sw * uF;
+    const R B = R(4.5) * ow * rho, C = R(9) * sw, G = R(3) * ow * rho, H = R(3) * sw;
+    // The weights' rounding (18 fl(1/18) = 1 + 7e-9 in FP32) would scale the
+    // momentum by the same factor in every collision, a drift that adds up
+    // over the steps.  The odd parts of the three axis pairs are therefore
+    // the remainders that make the post-collision momentum m + F (what the
+    // formulas give in exact arithmetic), and the rest population the
+    // remainder that conserves mass.
+    R sx = R(0), sy = R(0), sz = R(0), se = R(0), od[6];
+#pragma unroll
+    for (int a = 7; a < Q; a += 2) {  // diagonal pairs: even part now, odd part kept
+        const R cu = R(cx(a)) * ux + R(cy(a)) * uy + R(cz(a)) * uz;
+        const R cF = R(cx(a)) * Fx + R(cy(a)) * Fy + R(cz(a)) * Fz;
+        const R even = R(0.5) * (A + cu * (B * cu + C * cF));
+        const R odd = R(0.5) * (G * cu + H * cF);
+        p[a] = om1 * d[a] + even;
+        p[a + 1] = om1 * d[a + 1] + even;
+        od[(a - 7) / 2] = odd;
+        se += even;
+        if (cx(a)) sx += cx(a) > 0 ? odd : -odd;
+        if (cy(a)) sy += cy(a) > 0 ? odd : -odd;
+        if (cz(a)) sz += cz(a) > 0 ? odd : -odd;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // axis pairs (1, 2), (3, 4), (5, 6)
+        const int a = 1 + 2 * k;
+        const R cu = k == 0 ? ux : (k == 1 ? uy : uz);
+        const R cF = k == 0 ? Fx : (k == 1 ? Fy : Fz);
+        const R mk = k == 0 ? mx : (k == 1 ? my : mz);
+        const R sk = k == 0 ? sx : (k == 1 ? sy : sz);
+        const R even = A + cu * (B * cu + C * cF);
+        const R odd = R(0.5) * (om * mk + cF) - sk;  // sum over pairs of 2 c odd = om m + F
+        se += even;
+        p[a] = om1 * d[a] + even + odd;
+        p[a + 1] = om1 * d[a + 1] + even - odd;
+    }
+    p[0] = om1 * d[0] + (om * drho - R(2) * se);  // sum over directions of om d^eq + S = om (rho - 1)
+#pragma unroll
+    for (int a = 7; a < Q; a += 2) {
+        p[a] += od[(a - 7) / 2];
+        p[a + 1] -= od[(a - 7) / 2];
+    }
+}
+
+// collision and streaming of fluid node n, reading and writing the global
+// array directly (any node, walls included)
+template <typename T, typename R, int PARITY>
+__device__ __forceinline__ void collide_node(const View<R> &v, int n) {
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) return;  // wall node
+    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
+    const Nbr o = make_nbr(v, n);
+    R d[Q], p[Q];
+    load_pops<T, R, PARITY>(v, n, lk, o, d);
     const size_t N = (size_t)v.N;
-    const R Fx = v.F[n], Fy = v.F[N + n], Fz = v.F[2 * N + n];
-    const R inv = R(1) / rho;
-    const R ux = (mx + R(0.5) * Fx) * inv;
-    const R uy = (my + R(0.5) * Fy) * inv;
-    const R uz = (mz + R(0.5) * Fz) * inv;
+    R rho, ux, uy, uz;
+    bgk_guo<R>(d, v.F[n], v.F[N + n], v.F[2 * N + n], v.omega, p, rho, ux, uy, uz);
     if (v.rec) {
         v.rec[n] = rho;
         v.rec[N + n] = ux;
         v.rec[2 * N + n] = uy;
         v.rec[3 * N + n] = uz;
     }
-    const R uu = ux * ux + uy * uy + uz * uz;
-    const R om = v.omega;
-    const R src = R(1) - R(0.5) * om;
-    const R uF = ux * Fx + uy * Fy + uz * Fz;
-
     T *f = (T *)v.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const R w = R(wgt(i));
-        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
-        const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
-        const R deq = w * ((rho - R(1)) + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-        const R S = src * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-        R p = d[i] - om * (d[i] - deq) + S;
         const int code = link_code(lk, i);
+        R q = p[i];
         if (code) {
             const R cw = R(cx(i)) * v.uw[code][0] + R(cy(i)) * v.uw[code][1] + R(cz(i)) * v.uw[code][2];
-            p -= R(6) * w * rho * cw;
+            q -= R(6) * R(wgt(i)) * rho * cw;
         }
         if (PARITY == 0) {
-            f[(size_t)opp(i) * N + n] = Store<T>::st(p);
+            f[(size_t)opp(i) * N + n] = Store<T>::st(q);
         } else {
             if (code)
-                f[(size_t)opp(i) * N + n] = Store<T>::st(p);
+                f[(size_t)opp(i) * N + n] = Store<T>::st(q);
             else
-                f[(size_t)i * N + n + o.of(cx(i), cy(i), cz(i))] = Store<T>::st(p);
+                f[(size_t)i * N + n + o.of(cx(i), cy(i), cz(i))] = Store<T>::st(q);
         }
     }
+}
+
+template <typename T, typename R, int PARITY>
+__global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < v.N) collide_node<T, R, PARITY>(v, n);
+}
+
+// the same over the listed rows (x-lines) only: the rows next to walls when
+// the interior is handled by the staged kernel
+template <typename T, typename R, int PARITY>
+__global__ void __launch_bounds__(256) collide_rows_kernel(View<R> v) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)v.nerows * v.nx) return;
+    const int j = (int)(t / v.nx);
+    collide_node<T, R, PARITY>(v, v.erows[j] * v.nx + (int)(t - (long long)j * v.nx));
+}
+
+// ---------------------------------------------------------------------------
+// Staged collision for tiles of interior rows.
+//
+// An interior row is an x-line whose nodes, and the nodes of the eight rows
+// around it, are all fluid (x periodic): no population of its nodes meets a
+// wall.  For such a tile of consecutive rows, the 19 slot ranges that its
+// nodes read in one step are whole rows, and every element of those ranges is
+// read and written by exactly one node of the tile (even step: slot i of the
+// tile's own rows; odd step: slot opp(i) of the rows shifted by -c_i, the
+// x-shift applied in shared memory with the periodic wrap).  A persistent CTA
+// copies them, with the force rows, into a ring of shared-memory stages by
+// bulk copies (cp.async.bulk, completion on an mbarrier), collides in place
+// (each node writes its outgoing value where the opposite incoming value was)
+// and writes the same ranges back by bulk stores.  The ring keeps several
+// tiles of loads in flight per SM without holding them in registers, which
+// is what 2-byte populations need to reach the HBM bandwidth; four CTAs of
+// 256 threads share an SM, so that one computes while another waits.
+constexpr int TILE_THREADS = 256;
+constexpr int TILE_CTAS_PER_SM = 4;
+constexpr int TILE_NODES = 256;  // stride of a direction's range in a stage (nodes)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// waits for the phase with the given parity; gives up after about a second
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 256; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int K>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(K) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// The rows of a tile (k rows from global row r0 = y0 + ny z) shifted by
+// (dy, dz), as at most two contiguous pieces (a periodic wrap in y splits
+// them): fn(first element of the piece in the lattice, first element in the
+// tile buffer, element count).
+template <typename R, typename Fn>
+__device__ __forceinline__ void tile_pieces(const View<R> &v, int r0, int k, int dy, int dz, Fn fn) {
+    const int y0 = r0 % v.ny, z = r0 / v.ny;
+    const long long plane = (long long)v.ny * wrap(z + dz, v.nz);
+    const int ya = wrap(y0 + dy, v.ny);
+    const int c1 = min(k, v.ny - ya);
+    fn((plane + ya) * v.nx, 0, c1 * v.nx);
+    if (c1 < k) fn(plane * v.nx, c1 * v.nx, (k - c1) * v.nx);
+}
+
+// y and z components of the velocities packed two bits each (c + 1), so
+// that lanes holding different directions look them up without a table
+__host__ __device__ constexpr unsigned long long pack_c(int axis) {
+    unsigned long long b = 0;
+    for (int i = 0; i < Q; ++i) b |= (unsigned long long)((axis == 1 ? cy(i) : cz(i)) + 1) << (2 * i);
+    return b;
+}
+constexpr unsigned long long CY_PACK = pack_c(1), CZ_PACK = pack_c(2);
+__device__ __forceinline__ int cy_of(int i) { return (int)((CY_PACK >> (2 * i)) & 3ull) - 1; }
+__device__ __forceinline__ int cz_of(int i) { return (int)((CZ_PACK >> (2 * i)) & 3ull) - 1; }
+static_assert(((CY_PACK >> 6) & 3) == 2 && ((CZ_PACK >> 10) & 3) == 2, "packed velocity components");
+
+constexpr int TILE_COPIES = Q + 3;  // lanes of warp 0 that issue the copies of a stage
+
+template <typename T, typename R, int PARITY>
+__global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_kernel(View<R> v) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *ring = smem + 128;
+    constexpr int TNM = TILE_NODES;
+    constexpr size_t pop_bytes = (size_t)TNM * sizeof(T), stage_bytes = Q * pop_bytes + 3 * (size_t)TNM * sizeof(R);
+    const int nx = v.nx, S = v.tile_stages;
+    const size_t N = (size_t)v.N;
+    const int ntiles = v.ntiles;
+    const int lane = threadIdx.x;  // meaningful in warp 0
+    const bool issuer = threadIdx.x < TILE_COPIES, storer = threadIdx.x < Q;
+    auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
+    T *f = (T *)v.f;
+
+    // Lane i < 19 of warp 0 copies direction i's range (slot i of the tile's
+    // rows on even steps, slot opp(i) of the rows shifted by -c_i on odd
+    // steps); lanes 19..21 copy the three force components.  Each lane
+    // announces its own bytes on the stage's barrier (22 arrivals).
+    auto issue_load = [&](int it) {
+        const int2 tl = v.rtiles[tile_of(it)];
+        const int s = it % S;
+        unsigned char *st = ring + s * stage_bytes;
+        const unsigned tn = (unsigned)(tl.y * nx);
+        if (lane < Q) {
+            T *buf = (T *)(st + lane * pop_bytes);
+            const T *src = f + (size_t)(PARITY ? opp(lane) : lane) * N;
+            mbar_expect_tx(bar + s, tn * (unsigned)sizeof(T));
+            tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+                        [&](long long g, int b, int cnt) {
+                            bulk_load(buf + b, src + g, (unsigned)(cnt * sizeof(T)), bar + s);
+                        });
+        } else {
+            const int c = lane - Q;
+            R *fs = (R *)(st + Q * pop_bytes) + c * TNM;
+            mbar_expect_tx(bar + s, tn * (unsigned)sizeof(R));
+            bulk_load(fs, v.F + c * N + (size_t)tl.x * nx, tn * (unsigned)sizeof(R), bar + s);
+        }
+    };
+    auto issue_store = [&](int it) {  // lane < 19: the range it loaded
+        const int2 tl = v.rtiles[tile_of(it)];
+        unsigned char *st = ring + (it % S) * stage_bytes;
+        T *buf = (T *)(st + lane * pop_bytes);
+        T *dst = f + (size_t)(PARITY ? opp(lane) : lane) * N;
+        tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+                    [&](long long g, int b, int cnt) { bulk_store(dst + g, buf + b, (unsigned)(cnt * sizeof(T))); });
+        bulk_commit();
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(bar + s, TILE_COPIES);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (issuer)
+        for (int it = 0; it < S - 1 && tile_of(it) < ntiles; ++it) issue_load(it);
+
+    for (int it = 0; tile_of(it) < ntiles; ++it) {
+        const int s = it % S;
+        const bool ok = mbar_wait(bar + s, (unsigned)((it / S) & 1));
+        if (__syncthreads_or(!ok)) {  // let the copies in flight land, then report
+            if (threadIdx.x == 0)
+                for (int j = it; j < it + S - 1 && tile_of(j) < ntiles; ++j)
+                    mbar_wait(bar + j % S, (unsigned)((j / S) & 1));
+            if (storer) bulk_wait_read<0>();
+            if (threadIdx.x == 0) atomicOr(v.status, ST_TIMEOUT);
+            return;
+        }
+        const int2 tl = v.rtiles[tile_of(it)];
+        const int TN = tl.y * nx;
+        T *P = (T *)(ring + s * stage_bytes);
+        const R *Fs = (const R *)(ring + s * stage_bytes + Q * pop_bytes);
+        for (int L = threadIdx.x; L < TN; L += TILE_THREADS) {
+            const int j = L / nx, x = L - j * nx;
+            const int xm = (x == 0 ? nx : x) - 1, xp = (x == nx - 1 ? -1 : x) + 1;
+            // the value arriving from direction i sits in direction i's range
+            // at x - c_i on odd steps (x wrapped), at x on even steps; the
+            // range offsets i * TNM are constants
+            T *const b0 = P + L, *const bm = P + (j * nx + xm), *const bp = P + (j * nx + xp);
+            auto at = [&](int i) -> T & {
+                return (PARITY == 0 ? b0 : (cx(i) > 0 ? bm : (cx(i) < 0 ? bp : b0)))[i * TNM];
+            };
+            R d[Q], p[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) d[i] = Store<T>::ld(at(i));
+            R rho, ux, uy, uz;
+            bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], v.omega, p, rho, ux, uy, uz);
+            if (v.rec) {
+                const size_t n = (size_t)tl.x * nx + L;
+                v.rec[n] = rho;
+                v.rec[N + n] = ux;
+                v.rec[2 * N + n] = uy;
+                v.rec[3 * N + n] = uz;
+            }
+            // outgoing direction i takes the place of incoming opp(i)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) at(opp(i)) = Store<T>::st(p[i]);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (storer) issue_store(it);
+        if (issuer && tile_of(it + S - 1) < ntiles) {
+            if (storer) bulk_wait_read<1>();  // this lane's range of tile it - 1 has been written out
+            issue_load(it + S - 1);           // into the stage tile it - 1 used
+        }
+    }
+    if (storer) bulk_wait_read<0>();
 }
 
 // post-streaming velocity u = (sum f c + F/2) / rho with the force just
@@ -130,16 +433,16 @@ __global__ void __launch_bounds__(256) moments_kernel(View<R> v) {
     const Nbr o = make_nbr(v, n);
     R d[Q];
     load_pops<T, R, LAYOUT>(v, n, lk, o, d);
-    R rho = R(1), mx = R(0), my = R(0), mz = R(0);
+    R drho = R(0), mx = R(0), my = R(0), mz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        rho += d[i];
+        drho += d[i];
         if (cx(i)) mx += cx(i) > 0 ? d[i] : -d[i];
         if (cy(i)) my += cy(i) > 0 ? d[i] : -d[i];
         if (cz(i)) mz += cz(i) > 0 ? d[i] : -d[i];
     }
     const size_t N = (size_t)v.N;
-    const R inv = R(1) / rho;
+    const R inv = recip(R(1) + drho);
     const R ux = (mx + R(0.5) * v.F[n]) * inv;
     const R uy = (my + R(0.5) * v.F[N + n]) * inv;
     const R uz = (mz + R(0.5) * v.F[2 * N + n]) * inv;
@@ -212,9 +515,9 @@ __global__ void rho_out_kernel(View<R> v, R *out) {
     const Nbr nb = make_nbr(v, n);
     R d[Q];
     load_pops<T, R, LAYOUT>(v, n, lk, nb, d);
-    R rho = R(1);
-    for (int i = 0; i < Q; ++i) rho += d[i];
-    out[n] = rho;
+    R drho = R(0);
+    for (int i = 0; i < Q; ++i) drho += d[i];
+    out[n] = R(1) + drho;
 }
 
 template <typename R>
@@ -330,11 +633,32 @@ inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
 template <typename R>
 void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) {
+        // odd steps (reads and writes shifted by one node in x) go through
+        // the staged kernel; even steps touch each node's own slots, which
+        // the per-node kernel reads and writes at full width
+        if (v.ntiles && parity == 1) {
+            const int ge = nblocks((long long)v.nerows * v.nx, 256);
+            HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
+            if (v.nerows) HEMO_DISPATCH_T(precision, R, (collide_rows_kernel<T, R, 1><<<ge, 256, 0, st>>>(v)));
+            return;
+        }
+    }
     const int g = nblocks(v.N, 256);
     if (parity == 0)
         HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0><<<g, 256, 0, st>>>(v)));
     else
         HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1><<<g, 256, 0, st>>>(v)));
+}
+
+cudaError_t set_tile_smem_limit(int precision, int bytes) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    using R = float;
+    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1>)));
+    return e;
 }
 
 template <typename R>

@@ -30,7 +30,9 @@ class hemo_lattice_desc(C.Structure):
                 ('precision', C.c_int), ('periodic', C.c_int * 3), ('wall_mask', C.c_void_p),
                 ('wall_velocity', (C.c_double * 3) * 2), ('body_force', C.c_double * 3),
                 ('cuda_stream', C.c_void_p), ('alloc', ALLOC_FN), ('release', FREE_FN),
-                ('alloc_ctx', C.c_void_p)]
+                ('alloc_ctx', C.c_void_p), ('options', C.c_uint)]
+
+HEMO_OPT_NO_STAGING = 1
 
 
 class hemo_mesh_desc(C.Structure):
@@ -68,6 +70,7 @@ def lib():
         'hemo_sync': ([vp], i),
         'hemo_get_fields': ([vp, C.c_uint, vp, vp, vp, vp, vp], i),
         'hemo_get_sizes': ([vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(i), C.POINTER(i)], i),
+        'hemo_get_lattice_plan': ([vp, vp], i),
         'hemo_velocity_set': ([vp, vp], i),
         'hemo_get_populations': ([vp, vp], i),
         'hemo_get_links': ([vp, vp], i),
@@ -94,7 +97,7 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the load test)."""
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_sync',
-            'hemo_get_fields', 'hemo_get_sizes', 'hemo_velocity_set', 'hemo_get_populations',
+            'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
             'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
             'hemo_deformation_loss', 'hemo_backward', 'hemo_destroy', 'hemo_last_error']
@@ -140,7 +143,7 @@ class Simulation:
     """One coupled LBM-IBM simulation on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, tau=1.0, precision='f32', periodic=(1, 1, 1), wall_mask=None,
-                 wall_velocity=None, body_force=None, stream=None, torch_allocator=True):
+                 wall_velocity=None, body_force=None, stream=None, torch_allocator=True, options=0):
         import torch
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -166,6 +169,7 @@ class Simulation:
         for k in range(3):
             d.body_force[k] = g[k]
         d.cuda_stream = self._stream.cuda_stream
+        d.options = int(options)
         if torch_allocator:
             dev = torch.cuda.current_device()
             stream = self._stream
@@ -244,6 +248,13 @@ class Simulation:
         n, v, c, b = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_int()
         check(lib().hemo_get_sizes(self.handle, C.byref(n), C.byref(v), C.byref(c), C.byref(b)))
         return n.value, v.value, c.value, b.value
+
+    def lattice_plan(self):
+        """(tiles staged through shared memory, rows for the per-node
+        kernel, rows per tile, ring stages); zeros without staging."""
+        plan = (C.c_int * 4)()
+        check(lib().hemo_get_lattice_plan(self.handle, plan))
+        return tuple(plan)
 
     # -- read-out ----------------------------------------------------------
     def get_fields(self, what=HEMO_RHO | HEMO_U | HEMO_VERTS | HEMO_FORCES | HEMO_CELLSTATS, out=None):
