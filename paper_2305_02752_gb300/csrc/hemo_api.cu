@@ -132,7 +132,7 @@ struct hemo_sim {
     std::vector<HostMesh> meshes;
     std::vector<int> cell_type, cell_first, vcell;
     std::vector<double> X0;
-    int nv = 0, ncell = 0, max_nv = 0, max_nt = 0;
+    int nv = 0, ncell = 0, max_nv = 0, max_nt = 0, max_ne = 0;
     bool finalized = false;
     long long steps_done = 0;
     // device cells and bins
@@ -261,6 +261,7 @@ View<R> make_view(hemo_sim *s) {
     v.meshes = (const MeshDev<R> *)s->meshes_d;
     v.max_nv = s->max_nv;
     v.max_nt = s->max_nt;
+    v.max_ne = s->max_ne;
     for (int d = 0; d < 3; ++d) v.nb[d] = s->nb[d];
     v.nbins = s->nbins;
     v.key = s->key;
@@ -282,11 +283,12 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, cudaStream_t st) {
         if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
     };
     mark(HEMO_PHASE_MEMBRANE);
-    if (s->ncell) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n
-    mark(HEMO_PHASE_BINS);
     if (s->ncell) {
-        launch_bins<R>(v, st, false);  // anchors, counting sort by block
+        cudaMemsetAsync(v.counts, 0, sizeof(int) * v.nbins, st);
+        launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
     }
+    mark(HEMO_PHASE_BINS);
+    if (s->ncell) launch_bin_ranges<R>(v, st);  // counting sort by block
     mark(HEMO_PHASE_SPREAD);
     if (s->ncell) launch_spread<R>(v, st);  // F = g + sum F_v delta
     mark(HEMO_PHASE_COLLIDE);
@@ -340,7 +342,9 @@ int finalize_impl(hemo_sim *s) {
         int *detri = (int *)dalloc(s, sizeof(int) * 2 * (size_t)m.ne);
         R *dL0 = (R *)dalloc(s, rs * m.ne);
         R *dth0 = (R *)dalloc(s, rs * m.ne);
-        if (!dtri || !dedge || !detri || !dL0 || !dth0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        int4 *dtri4 = (int4 *)dalloc(s, sizeof(int4) * (size_t)m.nt);
+        if (!dtri || !dedge || !detri || !dL0 || !dth0 || !dtri4)
+            return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
         // processing order: item q is q * stride mod n (stride coprime with
         // n, about n/32), so a warp's lanes work on far-apart mesh parts
         const int se = coprime_stride(m.ne), st3 = coprime_stride(m.nt);
@@ -366,6 +370,42 @@ int finalize_impl(hemo_sim *s) {
             invL0[q] = R(1.0 / m.L0[e]);
             th0[q] = R(m.th0[e]);
         }
+        // incidence of each vertex: the edges it ends, the edges it is a
+        // wing of, its triangles (processing order), stored slot-major
+        std::vector<std::vector<int4>> ends(m.nv), tris(m.nv);
+        std::vector<std::vector<int2>> wings(m.nv);
+        for (int q = 0; q < m.ne; ++q) {
+            const int *E = &edge_p[4 * (size_t)q];
+            const int t1 = etri_p[2 * (size_t)q], t2 = etri_p[2 * (size_t)q + 1];
+            ends[E[0]].push_back(make_int4(q << 1, E[1], t1, t2));
+            ends[E[1]].push_back(make_int4((q << 1) | 1, E[0], t1, t2));
+            wings[E[2]].push_back(make_int2(q, t1));
+            wings[E[3]].push_back(make_int2(q, t2));
+        }
+        std::vector<int4> tri4(m.nt);
+        for (int q = 0; q < m.nt; ++q) {
+            const int *T = &tri_p[3 * (size_t)q];
+            tri4[q] = make_int4(T[0], T[1], T[2], 0);
+            for (int r = 0; r < 3; ++r) tris[T[r]].push_back(make_int4(q, T[(r + 1) % 3], T[(r + 2) % 3], 0));
+        }
+        int maxv = 0;
+        for (int i = 0; i < m.nv; ++i)
+            maxv = std::max(maxv, (int)std::max(ends[i].size(), std::max(wings[i].size(), tris[i].size())));
+        std::vector<int4> vend((size_t)maxv * m.nv, make_int4(-1, 0, 0, 0)), vtri((size_t)maxv * m.nv, make_int4(-1, 0, 0, 0));
+        std::vector<int2> vwing((size_t)maxv * m.nv, make_int2(-1, 0));
+        for (int i = 0; i < m.nv; ++i) {
+            for (size_t k = 0; k < ends[i].size(); ++k) vend[k * m.nv + i] = ends[i][k];
+            for (size_t k = 0; k < wings[i].size(); ++k) vwing[k * m.nv + i] = wings[i][k];
+            for (size_t k = 0; k < tris[i].size(); ++k) vtri[k * m.nv + i] = tris[i][k];
+        }
+        int4 *dvend = (int4 *)dalloc(s, sizeof(int4) * vend.size());
+        int2 *dvwing = (int2 *)dalloc(s, sizeof(int2) * vwing.size());
+        int4 *dvtri = (int4 *)dalloc(s, sizeof(int4) * vtri.size());
+        if (!dvend || !dvwing || !dvtri) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        HEMO_CU(cudaMemcpy(dvend, vend.data(), sizeof(int4) * vend.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dvwing, vwing.data(), sizeof(int2) * vwing.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dvtri, vtri.data(), sizeof(int4) * vtri.size(), cudaMemcpyHostToDevice));
+        HEMO_CU(cudaMemcpy(dtri4, tri4.data(), sizeof(int4) * tri4.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dtri, tri_p.data(), sizeof(int) * tri_p.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dedge, edge_p.data(), sizeof(int) * edge_p.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(detri, etri_p.data(), sizeof(int) * etri_p.size(), cudaMemcpyHostToDevice));
@@ -380,6 +420,11 @@ int finalize_impl(hemo_sim *s) {
         d.etri = detri;
         d.invL0 = dL0;
         d.th0 = dth0;
+        d.tri4 = dtri4;
+        d.maxv = maxv;
+        d.vend = dvend;
+        d.vwing = dvwing;
+        d.vtri = dvtri;
         d.A0 = m.A0;
         d.V0 = m.V0;
         d.K = R(m.k_link * m.kbt / m.persistence);
@@ -414,7 +459,7 @@ int finalize_impl(hemo_sim *s) {
         HEMO_CU(cudaMemcpy(s->cell_first_d, s->cell_first.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(s->cell_type_d, s->cell_type.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
     }
-    const size_t smem = cell_smem_bytes<R>(s->max_nv, s->max_nt);
+    const size_t smem = cell_smem_bytes<R>(s->max_nv, s->max_nt, s->max_ne);
     if (smem > 48 * 1024) HEMO_CU(set_cell_smem_limit<R>(smem));
     const size_t smem_adj = cell_adjoint_smem_bytes<R>(s->max_nv, s->max_nt);
     if (smem_adj > 48 * 1024) HEMO_CU(set_cell_adjoint_smem_limit<R>(smem_adj));
@@ -1028,6 +1073,7 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     s->meshes.push_back(hm);
     s->max_nv = std::max(s->max_nv, hm.nv);
     s->max_nt = std::max(s->max_nt, hm.nt);
+    s->max_ne = std::max(s->max_ne, hm.ne);
     if (first_cell_id) *first_cell_id = s->ncell;
     for (int k = 0; k < ncells; ++k) {
         const double *R = rot + 9 * (size_t)k;

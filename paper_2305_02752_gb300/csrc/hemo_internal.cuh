@@ -71,6 +71,18 @@ template <typename R> struct MeshDev {
     const int *etri;    // ne*2: the triangles (v0, v1, a) and (v1, v0, b), processing positions
     const R *invL0;     // ne: 1 / rest length
     const R *th0;       // ne: rest dihedral angle
+    const int4 *tri4;   // nt: the triangle's corners, padded to 16 bytes
+    // per vertex, the edges and triangles it belongs to, slot-major (entry
+    // [slot * nv + vertex]; slots 0 .. maxv - 1, id -1 = empty), one record
+    // each so that the gather needs no further table lookups; ids in
+    // processing order:
+    //   ends:  {edge << 1 | role (0 = v0, 1 = v1), other end, t1, t2}
+    //   wings: {edge, the triangle (v0, v1, this vertex) or (v1, v0, this)}
+    //   tris:  {triangle, next corner, the one after, -}
+    int maxv;
+    const int4 *vend;
+    const int2 *vwing;
+    const int4 *vtri;
     double A0, V0;
     R K;                // k_link * kbt / persistence
     R m2;               // max_strain^2
@@ -105,6 +117,7 @@ template <typename R> struct View {
     const MeshDev<R> *meshes;  // per type
     int max_nv;                // largest vertex count of a mesh type
     int max_nt;                // largest triangle count of a mesh type
+    int max_ne;                // largest edge count of a mesh type
     // bins
     int nb[3];
     int nbins;
@@ -160,10 +173,18 @@ template <typename R> void launch_rho_out(const View<R> &v, int precision, int p
 template <typename R> void launch_u_out(const View<R> &v, R *out, cudaStream_t st);
 void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, uint64_t *links, cudaStream_t st);
 
+// mode 0 (the step): re-base the offsets, membrane forces into Fv, and the
+// vertices' anchors, bin keys and bin counts (counts zeroed beforehand);
+// mode 1: per-cell statistics into stats (6 per cell), no writes to the state
 template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
 template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
-template <typename R> size_t cell_smem_bytes(int max_nv, int max_nt) { return (6 * (size_t)max_nv + 4 * (size_t)max_nt) * sizeof(R); }
+template <typename R> size_t cell_smem_bytes(int max_nv, int max_nt, int max_ne) {
+    return (3 * (size_t)max_nv + 4 * (size_t)max_nt + 6 * (size_t)max_ne) * sizeof(R);
+}
 template <typename R> void launch_bins(const View<R> &v, cudaStream_t st, bool stable);
+// the bin ranges and the (unstable) order once the step's membrane kernel
+// has written the anchors, keys and counts
+template <typename R> void launch_bin_ranges(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_spread(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_interpolate(const View<R> &v, cudaStream_t st);
 template <typename R> void launch_verts_out(const View<R> &v, double *X, double *F, cudaStream_t st);

@@ -616,6 +616,12 @@ void launch_bins(const View<R> &v, cudaStream_t st, bool stable) {
 }
 
 template <typename R>
+void launch_bin_ranges(const View<R> &v, cudaStream_t st) {
+    scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins);
+    scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv);
+}
+
+template <typename R>
 void launch_spread(const View<R> &v, cudaStream_t st) {
     spread_tile_kernel<R><<<v.nbins, 256, 0, st>>>(v);
     spread_gather_kernel<R><<<v.nbins, 256, 0, st>>>(v);
@@ -643,6 +649,7 @@ void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st) {
 
 #define HEMO_INST(R)                                                                      \
     template void launch_bins<R>(const View<R> &, cudaStream_t, bool);                    \
+    template void launch_bin_ranges<R>(const View<R> &, cudaStream_t);                     \
     template void launch_spread<R>(const View<R> &, cudaStream_t);                        \
     template void launch_interpolate<R>(const View<R> &, cudaStream_t);                   \
     template void launch_verts_out<R>(const View<R> &, double *, double *, cudaStream_t); \

@@ -88,78 +88,227 @@ __device__ void sym3_eig(double a00, double a11, double a22, double a01, double 
     lmin = q + 2.0 * p * cos(phi + 2.0943951023931954923);
 }
 
-// mode 0: re-base + forces (step); mode 1: statistics only (no writes to
-// the state): stats[6c..] = centroid, area, volume, deformation index.
+// Per-cell sums at FP64-level precision.  In the FP64 path a plain double;
+// in FP32 a two-word accumulator (hi + lo, each addition by Knuth's TwoSum),
+// so the loops over triangles and vertices do no FP64 arithmetic (slow on
+// this GPU) and only the per-warp totals are combined in FP64.
+template <typename R> struct Acc {
+    double s = 0;
+    __device__ void add(double x) { s += x; }
+    __device__ void add_shfl(int o) { s += __shfl_down_sync(0xffffffffu, s, o); }
+    __device__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float x) {
+        const float sum = hi + x, bp = sum - hi;
+        lo += (hi - (sum - bp)) + (x - bp);
+        hi = sum;
+    }
+    __device__ void add_shfl(int o) {
+        const float h = __shfl_down_sync(0xffffffffu, hi, o), l = __shfl_down_sync(0xffffffffu, lo, o);
+        add(h);
+        lo += l;
+    }
+    __device__ double value() const { return (double)hi + (double)lo; }
+};
+
+// block totals of K accumulators, returned to every thread
+template <typename R, int K>
+__device__ void block_total(Acc<R> (&acc)[K], double (&out)[K], double (*scratch)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k].add_shfl(o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) scratch[k][wid] = acc[k].value();
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0;
+        for (int w = 0; w < nw; ++w) t += scratch[threadIdx.x][w];
+        scratch[threadIdx.x][31] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = scratch[k][31];
+}
+
+// block-wide sum of K values of R, returned to every thread
+template <typename R, int K>
+__device__ void block_sum_r(R (&val)[K], R (*scratch)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_down_sync(0xffffffffu, val[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) scratch[k][wid] = val[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        R t = R(0);
+        for (int w = 0; w < nw; ++w) t += scratch[k][w];
+        val[k] = t;
+    }
+    __syncthreads();
+}
+
+// Anchor of a coordinate X = c + o (c the FP64 centroid, o the offset):
+// j = floor(X), t = X - j.  FP32 path: c arrives split into two floats
+// (c = ch + cl to 48 bits) and X is formed as a two-float sum, which keeps
+// t to FP32 precision without FP64 arithmetic.
+__device__ __forceinline__ void anchor_of(float ch, float cl, float o, int &j, float &t) {
+    const float sum = ch + o, bp = sum - ch;
+    const float err = ((ch - (sum - bp)) + (o - bp)) + cl;
+    const float fl = floorf(sum);
+    j = (int)fl;
+    t = (sum - fl) + err;  // sum - fl is exact
+    if (t >= 1.f) {
+        t -= 1.f;
+        ++j;
+    } else if (t < 0.f) {
+        t += 1.f;
+        --j;
+    }
+}
+__device__ __forceinline__ void anchor_of(double c, double, double o, int &j, double &t) {
+    const double X = c + o, fl = floor(X);
+    j = (int)fl;
+    t = X - fl;
+}
+
+// One CTA per cell.
+// mode 0 (the step): re-base the offsets (centroid += mean offset), area and
+//   volume, membrane forces F_v = -grad E into Fv, and each vertex's anchor
+//   (floor and fraction of X per axis), bin key and bin count;
+// mode 1: statistics only, no writes to the state: stats[6c..] = centroid,
+//   area, volume, deformation index.
+//
+// Forces are gathered, not scattered: an edge pass leaves six coefficients
+// per edge in shared memory (link: F on v0 = s (x1 - x0); bending: the
+// wing vertices get cb |e| n/|n|^2 of their triangle, the edge vertices the
+// lever-rule combinations of both), then each vertex sums the terms of the
+// edges it ends, the edges it is a wing of and its triangles, one loop per
+// kind over a per-mesh incidence table (so the lanes of a warp take the
+// same branch).  No atomics, and the summation order is fixed: the forces
+// are reproducible bit for bit.
 template <typename R>
 __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *stats) {
     const int c = blockIdx.x;
     const MeshDev<R> m = v.meshes[v.cell_type[c]];
     const int first = v.cell_first[c];
+    const int ME = v.max_ne;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *xs = reinterpret_cast<R *>(smem_raw);  // nv*3 positions relative to the centroid
-    R *fs = xs + 3 * v.max_nv;                  // nv*3 force accumulators
-    R *tn = fs + 3 * v.max_nv;                  // nt*4 triangle normal n and 1/|n|^2
+    R *xs = reinterpret_cast<R *>(smem_raw);  // nv*3 offsets from the (new) centroid
+    R *tn = xs + 3 * v.max_nv;                  // nt*4: n / |n|^2 and |n|
+    R *es = tn + 4 * v.max_nt;                  // 6*ne per-edge force coefficients
     __shared__ double scratch[6][32];
+    __shared__ R rscratch[3][32];
+    __shared__ double cnew[3];
+    __shared__ R csplit[2][3];  // the new centroid as R hi + lo
 
-    // mean offset (FP64)
-    double mean[3] = {0, 0, 0};
+    // mean offset: any shift works, the centroid takes what the offsets lose
+    R mean[3] = {R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
         const R *o = v.off + 3 * (size_t)(first + i);
-        mean[0] += (double)o[0];
-        mean[1] += (double)o[1];
-        mean[2] += (double)o[2];
+        mean[0] += o[0];
+        mean[1] += o[1];
+        mean[2] += o[2];
     }
-    block_sum<3>(mean, scratch);
-    for (int k = 0; k < 3; ++k) mean[k] /= m.nv;
+    block_sum_r<R, 3>(mean, rscratch);
+    for (int k = 0; k < 3; ++k) mean[k] /= R(m.nv);
     for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
         R *o = v.off + 3 * (size_t)(first + i);
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const R r = R((double)o[k] - mean[k]);
+            const R r = o[k] - mean[k];
             xs[3 * i + k] = r;
-            fs[3 * i + k] = R(0);
             if (mode == 0) {
                 o[k] = r;
                 if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r;
             }
         }
     }
-    if (mode == 0 && threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) v.ctr[3 * c + k] += mean[k];
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) {
+            cnew[k] = v.ctr[3 * c + k] + (double)mean[k];
+            if (mode == 0) v.ctr[3 * c + k] = cnew[k];
+            csplit[0][k] = R(cnew[k]);
+            csplit[1][k] = R(cnew[k] - (double)csplit[0][k]);
+        }
     __syncthreads();
 
-    // per triangle: normal n = (x1 - x0) x (x2 - x0) kept in shared memory;
-    // area and volume terms in R, their sums in FP64
-    double av[2] = {0, 0};
-    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
-        const V3<R> p0 = ld3(xs + 3 * m.tri[3 * t]), p1 = ld3(xs + 3 * m.tri[3 * t + 1]), p2 = ld3(xs + 3 * m.tri[3 * t + 2]);
-        const V3<R> n = cross(p1 - p0, p2 - p0);
-        const R q = dot(n, n);
-        tn[4 * t] = n.x;
-        tn[4 * t + 1] = n.y;
-        tn[4 * t + 2] = n.z;
-        tn[4 * t + 3] = R(1) / q;
-        av[0] += 0.5 * (double)sqrt_r(q);
-        av[1] += (double)dot(p0, cross(p1, p2)) / 6.0;
+    if (mode == 0) {  // anchors, keys and counts at the re-based positions
+        const R ch[3] = {csplit[0][0], csplit[0][1], csplit[0][2]}, cl[3] = {csplit[1][0], csplit[1][1], csplit[1][2]};
+        const int dims[3] = {v.nx, v.ny, v.nz};
+        for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+            const size_t g = (size_t)(first + i);
+            int b[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                int j;
+                R t;
+                anchor_of(ch[d], cl[d], xs[3 * i + d], j, t);
+                if (v.per[d]) {
+                    j = wrap(j, dims[d]);
+                } else if (j < 0 || j >= dims[d]) {
+                    atomicOr(v.status, ST_DOMAIN);
+                }
+                v.anc_i[3 * g + d] = j;
+                v.anc_t[3 * g + d] = t;
+                const int jc = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
+                b[d] = jc / BLK;
+            }
+            const int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
+            v.key[g] = key;
+            const unsigned act = __activemask();
+            const unsigned grp = __match_any_sync(act, key);
+            if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
+        }
     }
-    block_sum<2>(av, scratch);  // (synchronises: tn is complete below)
-    const double A = av[0], V = av[1];
+
+    // per triangle: a = n / |n|^2 and |n|, with n = (x1 - x0) x (x2 - x0);
+    // area |n|/2 and volume x0 . (x1 x x2) / 6 summed per cell
+    Acc<R> av[2];
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const int4 T = __ldg(m.tri4 + t);
+        const V3<R> p0 = ld3(xs + 3 * T.x), p1 = ld3(xs + 3 * T.y), p2 = ld3(xs + 3 * T.z);
+        const V3<R> n = cross(p1 - p0, p2 - p0);
+        const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
+        tn[4 * t] = iq * n.x;
+        tn[4 * t + 1] = iq * n.y;
+        tn[4 * t + 2] = iq * n.z;
+        tn[4 * t + 3] = ln;
+        av[0].add(R(0.5) * ln);
+        av[1].add(dot(p0, cross(p1, p2)) / R(6));
+    }
+    double AV[2];
+    block_total<R, 2>(av, AV, scratch);  // (synchronises: tn is complete below)
+    const double A = AV[0], V = AV[1];
 
     if (mode == 1) {
-        double G[6] = {0, 0, 0, 0, 0, 0};
+        Acc<R> G[6];
         for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-            const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
-            G[0] += x * x; G[1] += y * y; G[2] += z * z;
-            G[3] += x * y; G[4] += x * z; G[5] += y * z;
+            const R x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+            G[0].add(x * x);
+            G[1].add(y * y);
+            G[2].add(z * z);
+            G[3].add(x * y);
+            G[4].add(x * z);
+            G[5].add(y * z);
         }
-        block_sum<6>(G, scratch);
+        double Gt[6];
+        block_total<R, 6>(G, Gt, scratch);
         if (threadIdx.x == 0) {
             double lmax, lmin;
-            sym3_eig(G[0] / m.nv, G[1] / m.nv, G[2] / m.nv, G[3] / m.nv, G[4] / m.nv, G[5] / m.nv, lmax, lmin);
+            const double in = 1.0 / m.nv;
+            sym3_eig(Gt[0] * in, Gt[1] * in, Gt[2] * in, Gt[3] * in, Gt[4] * in, Gt[5] * in, lmax, lmin);
             const double a = sqrt(lmax), b = sqrt(lmin > 0 ? lmin : 0);
             double *o = stats + 6 * (size_t)c;
-            o[0] = v.ctr[3 * c] + mean[0];
-            o[1] = v.ctr[3 * c + 1] + mean[1];
-            o[2] = v.ctr[3 * c + 2] + mean[2];
+            o[0] = cnew[0];
+            o[1] = cnew[1];
+            o[2] = cnew[2];
             o[3] = A;
             o[4] = V;
             o[5] = (a - b) / (a + b);
@@ -167,50 +316,70 @@ __global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *
         return;
     }
 
-    // link and bending, one edge per thread; the normals of the edge's two
-    // triangles (v0, v1, a) and (v1, v0, b) come from the triangle pass
+    // per edge: link and bending coefficients; the edge's two triangles
+    // are (v0, v1, a) and (v1, v0, b)
+#pragma unroll 2
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
-        const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
-        const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
-        const V3<R> p0 = ld3(xs + 3 * i0), p1 = ld3(xs + 3 * i1), pa = ld3(xs + 3 * ia), pb = ld3(xs + 3 * ib);
+        const int4 E = __ldg(reinterpret_cast<const int4 *>(m.edge) + e);  // v0, v1, a, b
+        const int2 T = __ldg(reinterpret_cast<const int2 *>(m.etri) + e);
+        const R il0 = __ldg(m.invL0 + e), th0 = __ldg(m.th0 + e);
+        const int t1 = T.x, t2 = T.y;
+        const V3<R> p0 = ld3(xs + 3 * E.x), p1 = ld3(xs + 3 * E.y), pa = ld3(xs + 3 * E.z), pb = ld3(xs + 3 * E.w);
         const V3<R> ed = p1 - p0;
         const R L = sqrt_r(dot(ed, ed));
         const R iL = R(1) / L;
-        const R eps = L * m.invL0[e] - R(1);
+        const R eps = L * il0 - R(1);
         const R den = m.m2 - eps * eps;
         if (!(den > R(0))) atomicOr(v.status, ST_NUMERIC);
         const R dEdL = m.K * (eps + eps / den);
-        const V3<R> fl = (dEdL * iL) * ed;  // force on v0 (towards v1 when stretched)
-        sub_into(fs + 3 * i0, R(-1) * fl);
-        sub_into(fs + 3 * i1, fl);
-
-        const V3<R> n1 = ld3(tn + 4 * t1), n2 = ld3(tn + 4 * t2);
-        const V3<R> a1 = tn[4 * t1 + 3] * n1, a2 = tn[4 * t2 + 3] * n2;  // n / |n|^2
-        const R th = atan2_r(dot(cross(n1, n2), ed) * iL, dot(n1, n2));
-        const R cb = m.kb * (th - m.th0[e]);
-        const V3<R> da = pa - p0, db = pb - p0;
-        const R sa0 = dot(pa - p1, ed) * iL, sb0 = dot(pb - p1, ed) * iL;
-        const R sa1 = dot(da, ed) * iL, sb1 = dot(db, ed) * iL;
-        sub_into(fs + 3 * ia, (-cb * L) * a1);
-        sub_into(fs + 3 * ib, (-cb * L) * a2);
-        sub_into(fs + 3 * i0, cb * (R(-1) * (sa0 * a1 + sb0 * a2)));
-        sub_into(fs + 3 * i1, cb * (sa1 * a1 + sb1 * a2));
-    }
-
-    // area and volume gradients, one triangle per thread
-    const R ca = R(m.k_area * (A - m.A0) / (m.A0 * m.A0));
-    const R cv = R(m.k_volume * (V - m.V0) / (m.V0 * m.V0));
-    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
-        const int j0 = m.tri[3 * t], j1 = m.tri[3 * t + 1], j2 = m.tri[3 * t + 2];
-        const V3<R> p0 = ld3(xs + 3 * j0), p1 = ld3(xs + 3 * j1), p2 = ld3(xs + 3 * j2);
-        const V3<R> nh = sqrt_r(tn[4 * t + 3]) * ld3(tn + 4 * t);  // unit normal
-        const R ha = R(0.5) * ca, sv = cv / R(6);
-        sub_into(fs + 3 * j0, ha * cross(nh, p2 - p1) + sv * cross(p1, p2));
-        sub_into(fs + 3 * j1, ha * cross(nh, p0 - p2) + sv * cross(p2, p0));
-        sub_into(fs + 3 * j2, ha * cross(nh, p1 - p0) + sv * cross(p0, p1));
+        const V3<R> a1 = ld3(tn + 4 * t1), a2 = ld3(tn + 4 * t2);  // n / |n|^2
+        const R th = atan2_r(dot(cross(a1, a2), ed) * iL, dot(a1, a2));
+        const R cb = m.kb * (th - th0);
+        es[e] = dEdL * iL;
+        es[ME + e] = cb * L;
+        es[2 * ME + e] = cb * (dot(pa - p1, ed) * iL);
+        es[3 * ME + e] = cb * (dot(pb - p1, ed) * iL);
+        es[4 * ME + e] = cb * (dot(pa - p0, ed) * iL);
+        es[5 * ME + e] = cb * (dot(pb - p0, ed) * iL);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < 3 * m.nv; k += blockDim.x) v.Fv[3 * (size_t)first + k] = fs[k];
+
+    // per vertex: the sum over its edges and triangles
+    const R ca = R(m.k_area * (A - m.A0) / (m.A0 * m.A0));
+    const R cv = R(m.k_volume * (V - m.V0) / (m.V0 * m.V0));
+    const R ha = R(0.5) * ca, sv = cv / R(6);
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        const V3<R> pi = ld3(xs + 3 * i);
+        V3<R> f = {R(0), R(0), R(0)};
+#pragma unroll 2
+        for (int k = 0; k < m.maxv; ++k) {  // edges that end here: link and lever-rule bending terms
+            const int4 g = __ldg(m.vend + (size_t)k * m.nv + i);
+            if (g.x < 0) continue;
+            const int id = g.x >> 1, r = g.x & 1;
+            const V3<R> a1 = ld3(tn + 4 * g.z), a2 = ld3(tn + 4 * g.w);
+            const R s1 = es[(2 + 2 * r) * ME + id], s2 = es[(3 + 2 * r) * ME + id];
+            const V3<R> lever = s1 * a1 + s2 * a2;
+            f = f + es[id] * (ld3(xs + 3 * g.y) - pi) + (r ? R(-1) : R(1)) * lever;
+        }
+#pragma unroll 2
+        for (int k = 0; k < m.maxv; ++k) {  // edges this vertex is a wing of
+            const int2 g = __ldg(m.vwing + (size_t)k * m.nv + i);
+            if (g.x < 0) continue;
+            f = f + es[ME + g.x] * ld3(tn + 4 * g.y);
+        }
+#pragma unroll 2
+        for (int k = 0; k < m.maxv; ++k) {  // triangles: area and volume
+            const int4 g = __ldg(m.vtri + (size_t)k * m.nv + i);
+            if (g.x < 0) continue;
+            const V3<R> pa = ld3(xs + 3 * g.y), pb = ld3(xs + 3 * g.z);
+            const V3<R> nh = tn[4 * g.x + 3] * ld3(tn + 4 * g.x);  // unit normal
+            f = f - (ha * cross(nh, pb - pa) + sv * cross(pa, pb));
+        }
+        R *o = v.Fv + 3 * (size_t)(first + i);
+        o[0] = f.x;
+        o[1] = f.y;
+        o[2] = f.z;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -437,7 +606,7 @@ template <typename R>
 void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st) {
     if (v.ncell == 0) return;
     // positions and force accumulators of the largest mesh type
-    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv, v.max_nt), st>>>(v, mode, stats);
+    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv, v.max_nt, v.max_ne), st>>>(v, mode, stats);
 }
 
 template <typename R>
