@@ -138,7 +138,7 @@ class L2Flush:
         self.sink.copy_(self.r.sum().reshape(1))
 
 
-def timed_steps(sim, torch, steps, flush, phase_every=10):
+def timed_steps(sim, torch, steps, flush, phase_every=5):
     """Run `steps` steps, each bracketed by CUDA events on the simulation's
     stream with an L2 flush before it; returns (total ms, per-phase ms
     averaged over the sampled steps, kernels per step)."""

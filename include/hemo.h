@@ -80,8 +80,9 @@ typedef struct {
 
 /* HEMO_OPT_NO_STAGING: collide every node with the per-node kernel instead of
  * staging tiles of wall-free rows through shared memory by bulk copies on odd
- * steps (whose reads and writes are shifted by one node in x).  The results
- * are the same; the option exists for comparison and measurement. */
+ * steps (whose reads and writes are shifted by one node in x); staging is
+ * used with 16-bit storage only.  The results are the same; the option
+ * exists for comparison and measurement. */
 enum { HEMO_OPT_NO_STAGING = 1u };
 
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are

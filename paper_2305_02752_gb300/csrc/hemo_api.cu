@@ -132,7 +132,7 @@ struct hemo_sim {
     std::vector<HostMesh> meshes;
     std::vector<int> cell_type, cell_first, vcell;
     std::vector<double> X0;
-    int nv = 0, ncell = 0, max_nv = 0, max_nt = 0, max_ne = 0;
+    int nv = 0, ncell = 0, max_nv = 0, max_nt = 0, max_ne = 0, nsm = 1;
     bool finalized = false;
     long long steps_done = 0;
     // device cells and bins
@@ -262,6 +262,7 @@ View<R> make_view(hemo_sim *s) {
     v.max_nv = s->max_nv;
     v.max_nt = s->max_nt;
     v.max_ne = s->max_ne;
+    v.nsm = s->nsm;
     for (int d = 0; d < 3; ++d) v.nb[d] = s->nb[d];
     v.nbins = s->nbins;
     v.key = s->key;
@@ -847,14 +848,15 @@ int hemo_velocity_set(int32_t *c, double *w) {
 // within a z-plane are cut into tiles of at most tile_rows rows; the rows
 // that are not interior but hold fluid go to the per-node kernel.  Staging
 // needs 16-byte aligned rows (bulk copies) and at least two stages of the
-// ring in shared memory; FP64 keeps the per-node kernel (its collision is
-// arithmetic-bound on this GPU).
+// ring in shared memory.  It is used for 2-byte storage only: with 4-byte
+// populations the per-node kernel keeps enough bytes in flight by itself and
+// is as fast, and FP64's collision is arithmetic-bound on this GPU.
 constexpr size_t TILE_RING_BYTES = 54 * 1024;
 
 int plan_rows(hemo_sim *s, const uint8_t *mask) {
     const int nx = s->nx, ny = s->ny, nz = s->nz;
     const size_t S = tsize(s), Rb = rsize(s);
-    if (is_f64(s) || (s->options & HEMO_OPT_NO_STAGING) || !s->per[0]) return HEMO_OK;
+    if (S != 2 || (s->options & HEMO_OPT_NO_STAGING) || !s->per[0]) return HEMO_OK;
     if (((size_t)nx * S) % 16 || ((size_t)nx * Rb) % 16) return HEMO_OK;
     // whole rows of at most 256 nodes per tile (one per thread; the stage
     // layout has room for 256), at most 54 KiB of ring per CTA so that four
@@ -905,9 +907,7 @@ int plan_rows(hemo_sim *s, const uint8_t *mask) {
             }
         }
     if (tiles.empty()) return HEMO_OK;
-    int dev = 0, nsm = 0;
-    HEMO_CU(cudaGetDevice(&dev));
-    HEMO_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nsm = s->nsm;
     const int smem = (int)(128 + stages * stage);
     HEMO_CU(set_tile_smem_limit(s->precision, (int)TILE_RING_BYTES));  // the cap of every plan
     s->rtiles = (int2 *)dalloc(s, sizeof(int2) * tiles.size());
@@ -988,6 +988,9 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
     cudaError_t e = d->wall_mask ? cudaMemcpyAsync(s->ntype, d->wall_mask, (size_t)N, cudaMemcpyHostToDevice, st)
                                  : cudaMemsetAsync(s->ntype, 0, (size_t)N, st);
     if (e != cudaSuccess) return bail(fail(HEMO_ERR_CUDA, std::string("wall mask upload: ") + cudaGetErrorString(e)));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(HEMO_ERR_CUDA, "device query failed"));
     launch_build_links(s->nx, s->ny, s->nz, s->per, s->ntype, s->links, st);
     if (int rc = plan_rows(s, d->wall_mask)) return bail(rc);
     if (is_f64(s)) launch_init_equilibrium<double>(make_view<double>(s), s->precision, nullptr, st);

@@ -118,6 +118,7 @@ template <typename R> struct View {
     int max_nv;                // largest vertex count of a mesh type
     int max_nt;                // largest triangle count of a mesh type
     int max_ne;                // largest edge count of a mesh type
+    int nsm;                   // multiprocessors of the device
     // bins
     int nb[3];
     int nbins;
@@ -202,6 +203,31 @@ template <typename R>
 void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_grad, R *out_interp, cudaStream_t st);
 template <typename R>
 void launch_deformation_loss(const View<R> &v, const double *c0, double *cell_loss, R *dLdX, cudaStream_t st);
+
+// Sums at FP64-level precision.  In the FP64 path a plain double; in FP32 a
+// two-word accumulator (hi + lo, each addition by Knuth's TwoSum),
+// so the loops over triangles and vertices do no FP64 arithmetic (slow on
+// this GPU) and only the per-warp totals are combined in FP64.
+template <typename R> struct Acc {
+    double s = 0;
+    __device__ void add(double x) { s += x; }
+    __device__ void add_shfl(int o) { s += __shfl_down_sync(0xffffffffu, s, o); }
+    __device__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float x) {
+        const float sum = hi + x, bp = sum - hi;
+        lo += (hi - (sum - bp)) + (x - bp);
+        hi = sum;
+    }
+    __device__ void add_shfl(int o) {
+        const float h = __shfl_down_sync(0xffffffffu, hi, o), l = __shfl_down_sync(0xffffffffu, lo, o);
+        add(h);
+        lo += l;
+    }
+    __device__ double value() const { return (double)hi + (double)lo; }
+};
 
 // sets the message returned by hemo_last_error() on the calling thread
 void set_last_error(const char *msg);

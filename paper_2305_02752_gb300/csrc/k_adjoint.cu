@@ -19,7 +19,8 @@
 //   g_rho = w sum_i lambda*_i f^eq_i / rho,
 //   g_u = sum_i lambda*_i (w df^eq_i/du + dS_i/du),
 //   lambda_F += sum_i lambda*_i dS_i/dF + g_u / (2 rho).
-// Gradients accumulate in FP64: wall-velocity scale s (u_wall = s u_given):
+// Gradients accumulate in FP64 (per block in two-float precision first):
+// wall-velocity scale s (u_wall = s u_given):
 // sum over wall nodes of lambda_u . u_wall plus the bounce-back terms;
 // body force g: sum over fluid nodes of lambda_F.
 #include <type_traits>
@@ -32,21 +33,26 @@ namespace {
 
 inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// block-wide sum of K doubles into acc (one atomic per block and value)
-template <int K>
-__device__ void block_add(double (&val)[K], double *acc) {
+// block-wide sum of K per-thread values into the FP64 accumulators out (one
+// atomic per block and value); warps reduce in two-float precision (Acc),
+// only the per-warp totals are combined in FP64
+template <typename R, int K>
+__device__ void block_add(const R (&val)[K], double *out) {
     __shared__ double part[K][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    Acc<R> a[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_down_sync(0xffffffffu, val[k], o);
+    for (int k = 0; k < K; ++k) {
+        a[k].add(val[k]);
+        for (int o = 16; o > 0; o >>= 1) a[k].add_shfl(o);
+    }
     if (lane == 0)
-        for (int k = 0; k < K; ++k) part[k][wid] = val[k];
+        for (int k = 0; k < K; ++k) part[k][wid] = a[k].value();
     __syncthreads();
     if (threadIdx.x < K) {
-        double s = 0;
-        for (int w = 0; w < nw; ++w) s += part[threadIdx.x][w];
-        if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+        double t = 0;
+        for (int w = 0; w < nw; ++w) t += part[threadIdx.x][w];
+        if (t != 0.0) atomicAdd(out + threadIdx.x, t);
     }
 }
 
@@ -57,13 +63,13 @@ __device__ void block_add(double (&val)[K], double *acc) {
 template <typename R>
 __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double ds[1] = {0.0};
+    R ds[1] = {R(0)};
     if (n < v.N) {
         const size_t N = (size_t)v.N;
         const R lu[3] = {a.lamu[n], a.lamu[N + n], a.lamu[2 * N + n]};
         const int id = v.ntype[n] & 0x7f;
         if (id) {
-            if (id >= 2) ds[0] = (double)(lu[0] * v.uw[id][0] + lu[1] * v.uw[id][1] + lu[2] * v.uw[id][2]);
+            if (id >= 2) ds[0] = lu[0] * v.uw[id][0] + lu[1] * v.uw[id][1] + lu[2] * v.uw[id][2];
             for (int k = 0; k < 3; ++k) a.lamF[k * N + n] = R(0);
             for (int k = 0; k < 4; ++k) a.amom[k * N + n] = R(0);
         } else {
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> 
             a.amom[3 * N + n] = -lu_u * ir;
         }
     }
-    block_add<1>(ds, a.grad + 4 * a.ntypes);
+    block_add<R, 1>(ds, a.grad + 4 * a.ntypes);
 }
 
 // transpose of streaming (pull, with the moments term of the pulled
@@ -84,7 +90,7 @@ __global__ void __launch_bounds__(256) adj_moments_kernel(View<R> v, AdjView<R> 
 template <typename R>
 __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> a) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // wall-velocity scale, g_x, g_y, g_z
+    R acc[4] = {R(0), R(0), R(0), R(0)};  // wall-velocity scale, g_x, g_y, g_z
     if (n < v.N && !(v.ntype[n] & 0x7f)) {
         const size_t N = (size_t)v.N;
         const uint8_t nt = v.ntype[n];
@@ -100,7 +106,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
         // pulled adjoint of the post-collision populations
         R ls[Q];
         R lrho = R(0);
-        double dsw = 0.0;
+        R dsw = R(0);
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const int code = link_code(lk, j);
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
                 ls[j] = lj;
                 const R cw = R(cx(j)) * v.uw[code][0] + R(cy(j)) * v.uw[code][1] + R(cz(j)) * v.uw[code][2];
                 lrho -= R(6) * R(wgt(j)) * cw * lj;
-                dsw -= 6.0 * wgt(j) * (double)rho * (double)cw * (double)lj;
+                dsw -= R(6) * R(wgt(j)) * rho * cw * lj;
             } else {
                 const size_t m = n + o.of(cx(j), cy(j), cz(j));
                 R lj = a.lamf_in[(size_t)j * N + m] + a.amom[3 * N + m];
@@ -146,14 +152,14 @@ __global__ void __launch_bounds__(256) adj_collide_kernel(View<R> v, AdjView<R> 
         for (int k = 0; k < 3; ++k) {
             const R tot = a.lamF[k * N + n] + lF[k] + R(0.5) * gu[k] * ir;
             a.lamF[k * N + n] = tot;
-            acc[1 + k] = (double)tot;
+            acc[1 + k] = tot;
         }
         acc[0] = dsw;
     } else if (n < v.N) {
         const size_t N = (size_t)v.N;
         for (int j = 0; j < Q; ++j) a.lamf_out[(size_t)j * N + n] = R(0);
     }
-    block_add<4>(acc, a.grad + 4 * a.ntypes);
+    block_add<R, 4>(acc, a.grad + 4 * a.ntypes);
 }
 
 }  // namespace

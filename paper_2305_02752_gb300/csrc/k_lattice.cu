@@ -182,16 +182,6 @@ __global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
     if (n < v.N) collide_node<T, R, PARITY>(v, n);
 }
 
-// the same over the listed rows (x-lines) only: the rows next to walls when
-// the interior is handled by the staged kernel
-template <typename T, typename R, int PARITY>
-__global__ void __launch_bounds__(256) collide_rows_kernel(View<R> v) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)v.nerows * v.nx) return;
-    const int j = (int)(t / v.nx);
-    collide_node<T, R, PARITY>(v, v.erows[j] * v.nx + (int)(t - (long long)j * v.nx));
-}
-
 // ---------------------------------------------------------------------------
 // Staged collision for tiles of interior rows.
 //
@@ -205,7 +195,8 @@ __global__ void __launch_bounds__(256) collide_rows_kernel(View<R> v) {
 // copies them, with the force rows, into a ring of shared-memory stages by
 // bulk copies (cp.async.bulk, completion on an mbarrier), collides in place
 // (each node writes its outgoing value where the opposite incoming value was)
-// and writes the same ranges back by bulk stores.  The ring keeps several
+// and writes the same ranges back by bulk stores; the CTAs then collide the
+// rows next to walls node by node.  The ring keeps several
 // tiles of loads in flight per SM without holding them in registers, which
 // is what 2-byte populations need to reach the HBM bandwidth; four CTAs of
 // 256 threads share an SM, so that one computes while another waits.
@@ -411,6 +402,13 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
         }
     }
     if (storer) bulk_wait_read<0>();
+    // then the rows next to walls, node by node: their nodes own population
+    // slots disjoint from the tiles', so the order does not matter
+    const long long ne = (long long)v.nerows * nx;
+    for (long long t = (long long)blockIdx.x * TILE_THREADS + threadIdx.x; t < ne; t += (long long)gridDim.x * TILE_THREADS) {
+        const int jr = (int)(t / nx);
+        collide_node<T, R, PARITY>(v, v.erows[jr] * nx + (int)(t - (long long)jr * nx));
+    }
 }
 
 // post-streaming velocity u = (sum f c + F/2) / rho with the force just
@@ -634,13 +632,12 @@ inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
 template <typename R>
 void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value) {
-        // odd steps (reads and writes shifted by one node in x) go through
-        // the staged kernel; even steps touch each node's own slots, which
-        // the per-node kernel reads and writes at full width
+        // 16-bit storage, odd steps (reads and writes shifted by one node in
+        // x): the staged kernel, which also collides the rows next to walls
+        // node by node once its tiles are done.  Even steps touch each node's
+        // own slots, which the per-node kernel streams faster.
         if (v.ntiles && parity == 1) {
-            const int ge = nblocks((long long)v.nerows * v.nx, 256);
             HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
-            if (v.nerows) HEMO_DISPATCH_T(precision, R, (collide_rows_kernel<T, R, 1><<<ge, 256, 0, st>>>(v)));
             return;
         }
     }

@@ -88,31 +88,6 @@ __device__ void sym3_eig(double a00, double a11, double a22, double a01, double 
     lmin = q + 2.0 * p * cos(phi + 2.0943951023931954923);
 }
 
-// Per-cell sums at FP64-level precision.  In the FP64 path a plain double;
-// in FP32 a two-word accumulator (hi + lo, each addition by Knuth's TwoSum),
-// so the loops over triangles and vertices do no FP64 arithmetic (slow on
-// this GPU) and only the per-warp totals are combined in FP64.
-template <typename R> struct Acc {
-    double s = 0;
-    __device__ void add(double x) { s += x; }
-    __device__ void add_shfl(int o) { s += __shfl_down_sync(0xffffffffu, s, o); }
-    __device__ double value() const { return s; }
-};
-template <> struct Acc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ void add(float x) {
-        const float sum = hi + x, bp = sum - hi;
-        lo += (hi - (sum - bp)) + (x - bp);
-        hi = sum;
-    }
-    __device__ void add_shfl(int o) {
-        const float h = __shfl_down_sync(0xffffffffu, hi, o), l = __shfl_down_sync(0xffffffffu, lo, o);
-        add(h);
-        lo += l;
-    }
-    __device__ double value() const { return (double)hi + (double)lo; }
-};
-
 // block totals of K accumulators, returned to every thread
 template <typename R, int K>
 __device__ void block_total(Acc<R> (&acc)[K], double (&out)[K], double (*scratch)[32]) {
@@ -193,8 +168,15 @@ __device__ __forceinline__ void anchor_of(double c, double, double o, int &j, do
 // kind over a per-mesh incidence table (so the lanes of a warp take the
 // same branch).  No atomics, and the summation order is fixed: the forces
 // are reproducible bit for bit.
-template <typename R>
-__global__ void __launch_bounds__(256) cell_kernel(View<R> v, int mode, double *stats) {
+// CTA shapes of the cell kernels: NT = 256 threads sized so that three FP32
+// cells share an SM (registers and shared memory), or the largest CTA for
+// a cell that has an SM to itself (512 threads in FP32; FP64's larger
+// register footprint would spill at 512)
+template <typename R> struct CellMax { static constexpr int T = sizeof(R) == 4 ? 512 : 256; };
+template <typename R, int NT> struct CellMinBlocks { static constexpr int B = NT == 256 && sizeof(R) == 4 ? 3 : 1; };
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<R> v, int mode, double *stats) {
     const int c = blockIdx.x;
     const MeshDev<R> m = v.meshes[v.cell_type[c]];
     const int first = v.cell_first[c];
@@ -423,8 +405,8 @@ template <typename R> __device__ __forceinline__ void add_into(R *f, R s, V3<R> 
 //                            of F along lamFv, taken with dual numbers;
 //   grad[4 type + k] += lamFv . F_k / modulus_k for the four terms (each is
 //                            linear in its modulus).
-template <typename R>
-__global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R> a) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kernel(View<R> v, AdjView<R> a) {
     using D = Dual<R>;
     const int c = blockIdx.x;
     const int type = v.cell_type[c];
@@ -443,7 +425,7 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
     }
     __syncthreads();
 
-    double av[4] = {0, 0, 0, 0};  // A, dA, V, dV
+    Acc<R> av[4];  // A, dA, V, dV
     for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
         const int j0 = m.tri[3 * t], j1 = m.tri[3 * t + 1], j2 = m.tri[3 * t + 2];
         const V3<D> p0 = dld3(xs + 3 * j0, xt + 3 * j0), p1 = dld3(xs + 3 * j1, xt + 3 * j1),
@@ -457,16 +439,17 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
         o[6] = iq.v; o[7] = iq.t;
         const D ar = dconst(R(0.5)) * dsqrt(q);
         const D vo = dot(p0, cross(p1, p2));
-        av[0] += (double)ar.v;
-        av[1] += (double)ar.t;
-        av[2] += (double)vo.v / 6.0;
-        av[3] += (double)vo.t / 6.0;
+        av[0].add(ar.v);
+        av[1].add(ar.t);
+        av[2].add(vo.v / R(6));
+        av[3].add(vo.t / R(6));
     }
-    block_sum<4>(av, scratch);
-    const D ua = {R((av[0] - m.A0) / (m.A0 * m.A0)), R(av[1] / (m.A0 * m.A0))};
-    const D uv = {R((av[2] - m.V0) / (m.V0 * m.V0)), R(av[3] / (m.V0 * m.V0))};
+    double AV[4];
+    block_total<R, 4>(av, AV, scratch);  // (synchronises: tn is complete below)
+    const D ua = {R((AV[0] - m.A0) / (m.A0 * m.A0)), R(AV[1] / (m.A0 * m.A0))};
+    const D uv = {R((AV[2] - m.V0) / (m.V0 * m.V0)), R(AV[3] / (m.V0 * m.V0))};
 
-    double th[4] = {0, 0, 0, 0};  // lamFv . unit-modulus forces: link, bend, area, volume
+    Acc<R> th[4];  // lamFv . unit-modulus forces: link, bend, area, volume
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
         const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
         const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
@@ -482,7 +465,7 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
         const V3<D> u0 = (dEdL * iL) * ed;  // unit link force on v0; -u0 on v1
         add_into(ft + 3 * i0, m.k_link, tans(u0));
         add_into(ft + 3 * i1, -m.k_link, tans(u0));
-        th[0] += (double)(dot(l0, vals(u0)) - dot(l1, vals(u0)));
+        th[0].add(dot(l0, vals(u0)) - dot(l1, vals(u0)));
 
         const V3<D> n1 = dld3(tn + 8 * t1, tn + 8 * t1 + 3), n2 = dld3(tn + 8 * t2, tn + 8 * t2 + 3);
         const D iq1 = {tn[8 * t1 + 6], tn[8 * t1 + 7]}, iq2 = {tn[8 * t2 + 6], tn[8 * t2 + 7]};
@@ -498,7 +481,7 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
         add_into(ft + 3 * ib, m.k_bend, tans(fb));
         add_into(ft + 3 * i0, m.k_bend, tans(f0));
         add_into(ft + 3 * i1, m.k_bend, tans(f1));
-        th[1] += (double)(dot(la, vals(fa)) + dot(lb, vals(fb)) + dot(l0, vals(f0)) + dot(l1, vals(f1)));
+        th[1].add(dot(la, vals(fa)) + dot(lb, vals(fb)) + dot(l0, vals(f0)) + dot(l1, vals(f1)));
     }
     for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
         const int j[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
@@ -513,12 +496,13 @@ __global__ void __launch_bounds__(256) cell_adjoint_kernel(View<R> v, AdjView<R>
             add_into(ft + 3 * j[k], R(m.k_area), tans(fa));
             add_into(ft + 3 * j[k], R(m.k_volume), tans(fv));
             const V3<R> lk = ld3(xt + 3 * j[k]);
-            th[2] += (double)dot(lk, vals(fa));
-            th[3] += (double)dot(lk, vals(fv));
+            th[2].add(dot(lk, vals(fa)));
+            th[3].add(dot(lk, vals(fv)));
         }
     }
-    block_sum<4>(th, scratch);
-    if (threadIdx.x < 4) atomicAdd(a.grad + 4 * type + threadIdx.x, th[threadIdx.x]);
+    double TH[4];
+    block_total<R, 4>(th, TH, scratch);
+    if (threadIdx.x < 4) atomicAdd(a.grad + 4 * type + threadIdx.x, TH[threadIdx.x]);
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) a.lamX[3 * (size_t)first + i] += ft[i];
 }
@@ -602,27 +586,43 @@ __global__ void __launch_bounds__(256) deformation_loss_kernel(View<R> v, const 
 
 }  // namespace
 
+// with no more cells than multiprocessors each cell has an SM to itself and
+// the larger CTA shortens its latency; with more cells, 256 threads let
+// three cells share an SM
+template <typename R>
+bool cell_wide(const View<R> &v) { return CellMax<R>::T > 256 && v.ncell <= v.nsm; }
+
 template <typename R>
 void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st) {
     if (v.ncell == 0) return;
     // positions and force accumulators of the largest mesh type
-    cell_kernel<R><<<v.ncell, 256, cell_smem_bytes<R>(v.max_nv, v.max_nt, v.max_ne), st>>>(v, mode, stats);
+    const size_t smem = cell_smem_bytes<R>(v.max_nv, v.max_nt, v.max_ne);
+    if (cell_wide(v)) cell_kernel<R, CellMax<R>::T><<<v.ncell, CellMax<R>::T, smem, st>>>(v, mode, stats);
+    else cell_kernel<R, 256><<<v.ncell, 256, smem, st>>>(v, mode, stats);
 }
 
 template <typename R>
 cudaError_t set_cell_smem_limit(size_t bytes) {
-    return cudaFuncSetAttribute(cell_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(cell_kernel<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && CellMax<R>::T != 256)
+        e = cudaFuncSetAttribute(cell_kernel<R, CellMax<R>::T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
 }
 
 template <typename R>
 void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
     if (v.ncell == 0) return;
-    cell_adjoint_kernel<R><<<v.ncell, 256, cell_adjoint_smem_bytes<R>(v.max_nv, v.max_nt), st>>>(v, a);
+    const size_t smem = cell_adjoint_smem_bytes<R>(v.max_nv, v.max_nt);
+    if (cell_wide(v)) cell_adjoint_kernel<R, CellMax<R>::T><<<v.ncell, CellMax<R>::T, smem, st>>>(v, a);
+    else cell_adjoint_kernel<R, 256><<<v.ncell, 256, smem, st>>>(v, a);
 }
 
 template <typename R>
 cudaError_t set_cell_adjoint_smem_limit(size_t bytes) {
-    return cudaFuncSetAttribute(cell_adjoint_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(cell_adjoint_kernel<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && CellMax<R>::T != 256)
+        e = cudaFuncSetAttribute(cell_adjoint_kernel<R, CellMax<R>::T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
 }
 
 template <typename R>
