@@ -94,6 +94,8 @@ int coprime_stride(int n) {
 void hemo::set_last_error(const char *msg) { g_err = msg; }
 
 // device buffers of the reverse sweep (grown on demand, kept for reuse)
+constexpr size_t TILE_NODES3 = (size_t)(BLK + 3) * (BLK + 3) * (BLK + 3);  // nodes of a bin's spreading tile
+
 struct AdjBuffers {
     void *lamf_in = nullptr, *lamf_out = nullptr, *lamu = nullptr, *lamF = nullptr, *amom = nullptr;
     void *lamX = nullptr, *lamFv = nullptr, *grad = nullptr;
@@ -293,11 +295,21 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, cudaStream_t st) {
     mark(HEMO_PHASE_SPREAD);
     if (s->ncell) launch_spread<R>(v, st);  // F = g + sum F_v delta
     mark(HEMO_PHASE_COLLIDE);
-    launch_collide<R>(v, s->precision, parity, st);  // BGK + Guo force + AA streaming
+    View<R> vc = v;  // the spreading tiles are dead once F is gathered
+    if (s->ncell) {
+        vc.dead = s->tiles;
+        vc.dead_lines = (long long)(rsize(s) * 3 * (size_t)TILE_NODES3 * s->nbins / 128);
+    }
+    launch_collide<R>(vc, s->precision, parity, st);  // BGK + Guo force + AA streaming
     mark(HEMO_PHASE_MOMENTS);
     launch_moments<R>(v, s->precision, parity, st);  // post-streaming u (with F/2)
     mark(HEMO_PHASE_INTERP);
-    if (s->ncell) launch_interpolate<R>(v, st);  // X^{n+1} = X^n + I[u](X^n)
+    View<R> vi = v;  // F is dead once the moments have read it
+    if (!v.rec) {
+        vi.dead = v.F;
+        vi.dead_lines = (long long)(rsize(s) * 3 * (size_t)s->N / 128);
+    }
+    if (s->ncell) launch_interpolate<R>(vi, st);  // X^{n+1} = X^n + I[u](X^n)
     mark(HEMO_NUM_PHASES);
 }
 
@@ -325,7 +337,7 @@ int finalize_impl(hemo_sim *s) {
     s->counts = (int *)dalloc(s, sizeof(int) * s->nbins);
     s->cursor = (int *)dalloc(s, sizeof(int) * s->nbins);
     s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
-    s->tiles = dalloc(s, rs * 3 * (size_t)(BLK + 3) * (BLK + 3) * (BLK + 3) * s->nbins);
+    s->tiles = dalloc(s, rs * 3 * TILE_NODES3 * s->nbins);
     if (!s->tiles || !s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
         !s->key || !s->perm_raw || !s->perm || !s->anc_i || !s->anc_t ||
         !s->counts || !s->cursor || !s->start)

@@ -139,6 +139,10 @@ template <typename R> struct View {
     int ntiles, tile_rows, tile_stages, tile_grid, tile_smem;
     const int *erows;
     int nerows;
+    // a buffer whose contents are dead: the kernel drops its full 128-byte
+    // lines from L2 without writing them back (null / 0 = nothing to drop)
+    void *dead;
+    long long dead_lines;
     // recording for the reverse sweep (null in plain steps)
     R *rec;                    // [4][N] collision density and velocity at fluid nodes; when set the
                                // moments kernel also writes the wall velocity into u at wall nodes
@@ -228,6 +232,17 @@ template <> struct Acc<float> {
     }
     __device__ double value() const { return (double)hi + (double)lo; }
 };
+
+// Drops this thread's share of the dead buffer's L2 lines (discard.global.L2:
+// the lines are invalidated without write-back, so data that no kernel will
+// read again costs no DRAM writes when it would be evicted).
+template <typename R>
+__device__ __forceinline__ void drop_dead_lines(const View<R> &v) {
+    if (!v.dead_lines) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < v.dead_lines; l += stride)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"((char *)v.dead + 128 * l) : "memory");
+}
 
 // sets the message returned by hemo_last_error() on the calling thread
 void set_last_error(const char *msg);

@@ -390,6 +390,7 @@ __global__ void __launch_bounds__(256) spread_gather_kernel(View<R> v) {
 // partial sums are reduced with warp shuffles.
 template <typename R>
 __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
+    drop_dead_lines(v);
     constexpr int CAP = Stage<R>::CAP;
     const int k = blockIdx.x;
     const int s = v.start[k], e = v.start[k + 1];
@@ -459,6 +460,98 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
                 o[2] += U2;
             }
         }
+    }
+}
+
+// FP32 interpolation: one thread per vertex.  The bin's 11^3 neighbourhood
+// of u is staged once as (ux, uy, uz, 0) per node, so each stencil node is
+// one 16-byte shared load; the weights stay in registers and each thread
+// sums its vertex's 64 terms itself (no staging of weights, no shuffles).
+__global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
+    drop_dead_lines(v);
+    const int k = blockIdx.x;
+    const int s = v.start[k], e = v.start[k + 1];
+    if (s == e) return;
+    __shared__ float4 tile[TILE_SMEM];
+    __shared__ int jtab[3][TILE];  // wrapped lattice coordinate, -1 beyond a non-periodic edge
+    int org[3];
+    bin_origin(v, k, org);
+    // the first vertex's anchors, loaded before the tile so that the two
+    // latencies overlap
+    int i = -1, ai[3] = {0, 0, 0};
+    float at[3] = {0.f, 0.f, 0.f};
+    if (s + (int)threadIdx.x < e) {
+        i = v.perm[s + threadIdx.x];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ai[d] = v.anc_i[3 * (size_t)i + d];
+            at[d] = v.anc_t[3 * (size_t)i + d];
+        }
+    }
+    if (threadIdx.x < 3 * TILE) {
+        const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
+        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+        int j = org[d] - 1 + l;
+        if (v.per[d]) j = wrap(j, dims);
+        else if (j < 0 || j >= dims) j = -1;
+        jtab[d][l] = j;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+#pragma unroll 3
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+        const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
+        const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond a non-periodic edge: resting wall
+        if ((jx | jy | jz) >= 0) {
+            const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
+            t.x = __ldg(v.u + n);
+            t.y = __ldg(v.u + N + n);
+            t.z = __ldg(v.u + 2 * N + n);
+        }
+        tile[l0 + TS_Y * l1 + TS_Z * l2] = t;
+    }
+    __syncthreads();
+    for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+        if (j != s + (int)threadIdx.x) {
+            i = v.perm[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ai[d] = v.anc_i[3 * (size_t)i + d];
+                at[d] = v.anc_t[3 * (size_t)i + d];
+            }
+        }
+        float w[3][4];
+        int r0 = 0;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int b = ai[d] - org[d];
+            ok &= b >= 0 && b < BLK;
+            r0 += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
+            peskin4(at[d], w[d]);
+        }
+        if (!ok) continue;
+        float U0 = 0.f, U1 = 0.f, U2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float wyz = w[1][b] * w[2][c];
+                const float4 *row = tile + r0 + TS_Y * b + TS_Z * c;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float wa = wyz * w[0][a];
+                    const float4 t = row[a];
+                    U0 += wa * t.x;
+                    U1 += wa * t.y;
+                    U2 += wa * t.z;
+                }
+            }
+        float *o = v.off + 3 * (size_t)i;
+        o[0] += U0;
+        o[1] += U1;
+        o[2] += U2;
     }
 }
 
@@ -581,6 +674,87 @@ __global__ void __launch_bounds__(256) vertex_field_kernel(View<R> v, const R *A
     }
 }
 
+// FP32 form of vertex_field_kernel: one thread per vertex over a float4
+// tile, as in interpolate_v4_kernel
+__global__ void __launch_bounds__(256) vertex_field_v4_kernel(View<float> v, const float *A, const float *B,
+                                                              float *out_grad, float *out_interp) {
+    const int k = blockIdx.x;
+    const int s = v.start[k], e = v.start[k + 1];
+    if (s == e) return;
+    __shared__ float4 tile[TILE_SMEM];
+    __shared__ int jtab[3][TILE];
+    int org[3];
+    bin_origin(v, k, org);
+    if (threadIdx.x < 3 * TILE) {
+        const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
+        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+        int j = org[d] - 1 + l;
+        if (v.per[d]) j = wrap(j, dims);
+        else if (j < 0 || j >= dims) j = -1;
+        jtab[d][l] = j;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+        const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
+        const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((jx | jy | jz) >= 0) {
+            const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
+            t.x = A[n];
+            t.y = A[N + n];
+            t.z = A[2 * N + n];
+        }
+        tile[l0 + TS_Y * l1 + TS_Z * l2] = t;
+    }
+    __syncthreads();
+    for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+        const int i = v.perm[j];
+        float w[3][4], dw[3][4];
+        int r0 = 0;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int b = v.anc_i[3 * (size_t)i + d] - org[d];
+            ok &= b >= 0 && b < BLK;
+            r0 += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
+            peskin4_d(v.anc_t[3 * (size_t)i + d], w[d], dw[d]);
+        }
+        if (!ok) continue;
+        const float B0 = B ? B[3 * (size_t)i] : 0.f, B1 = B ? B[3 * (size_t)i + 1] : 0.f, B2 = B ? B[3 * (size_t)i + 2] : 0.f;
+        float U0 = 0.f, U1 = 0.f, U2 = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float wyz = w[1][b] * w[2][c], dyz = dw[1][b] * w[2][c], ydz = w[1][b] * dw[2][c];
+                const float4 *row = tile + r0 + TS_Y * b + TS_Z * c;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 t = row[a];
+                    const float wa = w[0][a] * wyz;
+                    U0 += wa * t.x;
+                    U1 += wa * t.y;
+                    U2 += wa * t.z;
+                    const float sAB = t.x * B0 + t.y * B1 + t.z * B2;
+                    G0 += sAB * dw[0][a] * wyz;
+                    G1 += sAB * w[0][a] * dyz;
+                    G2 += sAB * w[0][a] * ydz;
+                }
+            }
+        if (out_interp) {
+            out_interp[3 * (size_t)i] = U0;
+            out_interp[3 * (size_t)i + 1] = U1;
+            out_interp[3 * (size_t)i + 2] = U2;
+        }
+        if (out_grad) {
+            out_grad[3 * (size_t)i] += G0;
+            out_grad[3 * (size_t)i + 1] += G1;
+            out_grad[3 * (size_t)i + 2] += G2;
+        }
+    }
+}
+
 template <typename R>
 __global__ void verts_out_kernel(View<R> v, double *X, double *F) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -629,12 +803,16 @@ void launch_spread(const View<R> &v, cudaStream_t st) {
 
 template <typename R>
 void launch_interpolate(const View<R> &v, cudaStream_t st) {
-    interpolate_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    if constexpr (std::is_same<R, float>::value) interpolate_v4_kernel<<<v.nbins, 256, 0, st>>>(v);
+    else interpolate_kernel<R><<<v.nbins, 256, 0, st>>>(v);
 }
 
 template <typename R>
 void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_grad, R *out_interp, cudaStream_t st) {
-    vertex_field_kernel<R><<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
+    if constexpr (std::is_same<R, float>::value)
+        vertex_field_v4_kernel<<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
+    else
+        vertex_field_kernel<R><<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
 }
 
 template <typename R>

@@ -178,6 +178,7 @@ __device__ __forceinline__ void collide_node(const View<R> &v, int n) {
 
 template <typename T, typename R, int PARITY>
 __global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
+    drop_dead_lines(v);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n < v.N) collide_node<T, R, PARITY>(v, n);
 }
@@ -344,6 +345,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
         bulk_commit();
     };
 
+    drop_dead_lines(v);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(bar + s, TILE_COPIES);
         fence_mbar_init();
