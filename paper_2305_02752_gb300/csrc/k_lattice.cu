@@ -177,7 +177,7 @@ __device__ __forceinline__ void collide_node(const View<R> &v, int n) {
 }
 
 template <typename T, typename R, int PARITY>
-__global__ void __launch_bounds__(256) collide_stream_kernel(View<R> v) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) collide_stream_kernel(View<R> v) {
     drop_dead_lines(v);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n < v.N) collide_node<T, R, PARITY>(v, n);
