@@ -184,7 +184,7 @@ void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, 
 template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
 template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
 template <typename R> size_t cell_smem_bytes(int max_nv, int max_nt, int max_ne) {
-    return (3 * (size_t)max_nv + 4 * (size_t)max_nt + 6 * (size_t)max_ne) * sizeof(R);
+    return (4 * (size_t)max_nv + 4 * (size_t)max_nt + 4 * (size_t)max_ne) * sizeof(R);
 }
 template <typename R> void launch_bins(const View<R> &v, cudaStream_t st, bool stable);
 // the bin ranges and the (unstable) order once the step's membrane kernel

@@ -476,18 +476,6 @@ __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
     __shared__ int jtab[3][TILE];  // wrapped lattice coordinate, -1 beyond a non-periodic edge
     int org[3];
     bin_origin(v, k, org);
-    // the first vertex's anchors, loaded before the tile so that the two
-    // latencies overlap
-    int i = -1, ai[3] = {0, 0, 0};
-    float at[3] = {0.f, 0.f, 0.f};
-    if (s + (int)threadIdx.x < e) {
-        i = v.perm[s + threadIdx.x];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            ai[d] = v.anc_i[3 * (size_t)i + d];
-            at[d] = v.anc_t[3 * (size_t)i + d];
-        }
-    }
     if (threadIdx.x < 3 * TILE) {
         const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
         const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
@@ -498,38 +486,30 @@ __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
     }
     __syncthreads();
     const size_t N = (size_t)v.N;
-#pragma unroll 3
     for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
         const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
         const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond a non-periodic edge: resting wall
         if ((jx | jy | jz) >= 0) {
             const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
-            t.x = __ldg(v.u + n);
-            t.y = __ldg(v.u + N + n);
-            t.z = __ldg(v.u + 2 * N + n);
+            t.x = v.u[n];
+            t.y = v.u[N + n];
+            t.z = v.u[2 * N + n];
         }
         tile[l0 + TS_Y * l1 + TS_Z * l2] = t;
     }
     __syncthreads();
     for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
-        if (j != s + (int)threadIdx.x) {
-            i = v.perm[j];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                ai[d] = v.anc_i[3 * (size_t)i + d];
-                at[d] = v.anc_t[3 * (size_t)i + d];
-            }
-        }
+        const int i = v.perm[j];
         float w[3][4];
         int r0 = 0;
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int b = ai[d] - org[d];
+            const int b = v.anc_i[3 * (size_t)i + d] - org[d];
             ok &= b >= 0 && b < BLK;
             r0 += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
-            peskin4(at[d], w[d]);
+            peskin4(v.anc_t[3 * (size_t)i + d], w[d]);
         }
         if (!ok) continue;
         float U0 = 0.f, U1 = 0.f, U2 = 0.f;

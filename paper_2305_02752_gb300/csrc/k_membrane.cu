@@ -175,20 +175,35 @@ __device__ __forceinline__ void anchor_of(double c, double, double o, int &j, do
 template <typename R> struct CellMax { static constexpr int T = sizeof(R) == 4 ? 512 : 256; };
 template <typename R, int NT> struct CellMinBlocks { static constexpr int B = NT == 256 && sizeof(R) == 4 ? 3 : 1; };
 
+// 4-wide records in shared memory (16-byte aligned for FP32: one 128-bit load)
+template <typename R> struct Q4 {
+    R x, y, z, w;
+};
+template <typename R> __device__ __forceinline__ Q4<R> ld4(const R *p) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        return {q.x, q.y, q.z, q.w};
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        return {a.x, a.y, b.x, b.y};
+    }
+}
+template <typename R> __device__ __forceinline__ V3<R> xyz(Q4<R> q) { return {q.x, q.y, q.z}; }
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<R> v, int mode, double *stats) {
     const int c = blockIdx.x;
     const MeshDev<R> m = v.meshes[v.cell_type[c]];
     const int first = v.cell_first[c];
-    const int ME = v.max_ne;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *xs = reinterpret_cast<R *>(smem_raw);  // nv*3 offsets from the (new) centroid
-    R *tn = xs + 3 * v.max_nv;                  // nt*4: n / |n|^2 and |n|
-    R *es = tn + 4 * v.max_nt;                  // 6*ne per-edge force coefficients
+    R *xs = reinterpret_cast<R *>(smem_raw);  // nv*4: offsets from the (new) centroid, padded
+    R *tn = xs + 4 * v.max_nv;                  // nt*4: n / |n|^2 and |n|
+    R *es = tn + 4 * v.max_nt;                  // ne*4 per-edge force coefficients
     __shared__ double scratch[6][32];
     __shared__ R rscratch[3][32];
     __shared__ double cnew[3];
     __shared__ R csplit[2][3];  // the new centroid as R hi + lo
+    __shared__ R cav[2];        // area and volume coefficients
 
     // mean offset: any shift works, the centroid takes what the offsets lose
     R mean[3] = {R(0), R(0), R(0)};
@@ -205,12 +220,13 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const R r = o[k] - mean[k];
-            xs[3 * i + k] = r;
+            xs[4 * i + k] = r;
             if (mode == 0) {
                 o[k] = r;
                 if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r;
             }
         }
+        xs[4 * i + 3] = R(0);
     }
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; ++k) {
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
             for (int d = 0; d < 3; ++d) {
                 int j;
                 R t;
-                anchor_of(ch[d], cl[d], xs[3 * i + d], j, t);
+                anchor_of(ch[d], cl[d], xs[4 * i + d], j, t);
                 if (v.per[d]) {
                     j = wrap(j, dims[d]);
                 } else if (j < 0 || j >= dims[d]) {
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     Acc<R> av[2];
     for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
         const int4 T = __ldg(m.tri4 + t);
-        const V3<R> p0 = ld3(xs + 3 * T.x), p1 = ld3(xs + 3 * T.y), p2 = ld3(xs + 3 * T.z);
+        const V3<R> p0 = xyz(ld4(xs + 4 * T.x)), p1 = xyz(ld4(xs + 4 * T.y)), p2 = xyz(ld4(xs + 4 * T.z));
         const V3<R> n = cross(p1 - p0, p2 - p0);
         const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
         tn[4 * t] = iq * n.x;
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     if (mode == 1) {
         Acc<R> G[6];
         for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-            const R x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+            const R x = xs[4 * i], y = xs[4 * i + 1], z = xs[4 * i + 2];
             G[0].add(x * x);
             G[1].add(y * y);
             G[2].add(z * z);
@@ -297,16 +313,23 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         }
         return;
     }
+    if (threadIdx.x == 0) {  // once per cell: FP64 is slow on this GPU
+        cav[0] = R(0.5 * m.k_area * (A - m.A0) / (m.A0 * m.A0));
+        cav[1] = R(m.k_volume * (V - m.V0) / (m.V0 * m.V0) / 6.0);
+    }
 
-    // per edge: link and bending coefficients; the edge's two triangles
-    // are (v0, v1, a) and (v1, v0, b)
+    // per edge: link coefficient s (F on v0 = s (x1 - x0)), cb |e| for the
+    // wing vertices, and the lever-rule coefficients cb sa0, cb sb0 of v0
+    // (those of v1 are cb sa0 + cb |e| and cb sb0 + cb |e|, since
+    // sa1 - sa0 = sb1 - sb0 = |e|); the edge's triangles are (v0, v1, a)
+    // and (v1, v0, b)
 #pragma unroll 2
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
         const int4 E = __ldg(reinterpret_cast<const int4 *>(m.edge) + e);  // v0, v1, a, b
         const int2 T = __ldg(reinterpret_cast<const int2 *>(m.etri) + e);
         const R il0 = __ldg(m.invL0 + e), th0 = __ldg(m.th0 + e);
-        const int t1 = T.x, t2 = T.y;
-        const V3<R> p0 = ld3(xs + 3 * E.x), p1 = ld3(xs + 3 * E.y), pa = ld3(xs + 3 * E.z), pb = ld3(xs + 3 * E.w);
+        const V3<R> p0 = xyz(ld4(xs + 4 * E.x)), p1 = xyz(ld4(xs + 4 * E.y));
+        const V3<R> pa = xyz(ld4(xs + 4 * E.z)), pb = xyz(ld4(xs + 4 * E.w));
         const V3<R> ed = p1 - p0;
         const R L = sqrt_r(dot(ed, ed));
         const R iL = R(1) / L;
@@ -314,47 +337,45 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         const R den = m.m2 - eps * eps;
         if (!(den > R(0))) atomicOr(v.status, ST_NUMERIC);
         const R dEdL = m.K * (eps + eps / den);
-        const V3<R> a1 = ld3(tn + 4 * t1), a2 = ld3(tn + 4 * t2);  // n / |n|^2
+        const V3<R> a1 = xyz(ld4(tn + 4 * T.x)), a2 = xyz(ld4(tn + 4 * T.y));  // n / |n|^2
         const R th = atan2_r(dot(cross(a1, a2), ed) * iL, dot(a1, a2));
         const R cb = m.kb * (th - th0);
-        es[e] = dEdL * iL;
-        es[ME + e] = cb * L;
-        es[2 * ME + e] = cb * (dot(pa - p1, ed) * iL);
-        es[3 * ME + e] = cb * (dot(pb - p1, ed) * iL);
-        es[4 * ME + e] = cb * (dot(pa - p0, ed) * iL);
-        es[5 * ME + e] = cb * (dot(pb - p0, ed) * iL);
+        R *o = es + 4 * e;
+        o[0] = dEdL * iL;
+        o[1] = cb * L;
+        o[2] = cb * (dot(pa - p1, ed) * iL);
+        o[3] = cb * (dot(pb - p1, ed) * iL);
     }
     __syncthreads();
 
     // per vertex: the sum over its edges and triangles
-    const R ca = R(m.k_area * (A - m.A0) / (m.A0 * m.A0));
-    const R cv = R(m.k_volume * (V - m.V0) / (m.V0 * m.V0));
-    const R ha = R(0.5) * ca, sv = cv / R(6);
+    const R ha = cav[0], sv = cav[1];
     for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-        const V3<R> pi = ld3(xs + 3 * i);
+        const V3<R> pi = xyz(ld4(xs + 4 * i));
         V3<R> f = {R(0), R(0), R(0)};
 #pragma unroll 2
         for (int k = 0; k < m.maxv; ++k) {  // edges that end here: link and lever-rule bending terms
             const int4 g = __ldg(m.vend + (size_t)k * m.nv + i);
             if (g.x < 0) continue;
             const int id = g.x >> 1, r = g.x & 1;
-            const V3<R> a1 = ld3(tn + 4 * g.z), a2 = ld3(tn + 4 * g.w);
-            const R s1 = es[(2 + 2 * r) * ME + id], s2 = es[(3 + 2 * r) * ME + id];
-            const V3<R> lever = s1 * a1 + s2 * a2;
-            f = f + es[id] * (ld3(xs + 3 * g.y) - pi) + (r ? R(-1) : R(1)) * lever;
+            const V3<R> a1 = xyz(ld4(tn + 4 * g.z)), a2 = xyz(ld4(tn + 4 * g.w));
+            const Q4<R> cf = ld4(es + 4 * id);
+            const V3<R> lk = cf.x * (xyz(ld4(xs + 4 * g.y)) - pi);
+            f = r == 0 ? f + lk + (cf.z * a1 + cf.w * a2) : f + lk - ((cf.z + cf.y) * a1 + (cf.w + cf.y) * a2);
         }
 #pragma unroll 2
         for (int k = 0; k < m.maxv; ++k) {  // edges this vertex is a wing of
             const int2 g = __ldg(m.vwing + (size_t)k * m.nv + i);
             if (g.x < 0) continue;
-            f = f + es[ME + g.x] * ld3(tn + 4 * g.y);
+            f = f + es[4 * g.x + 1] * xyz(ld4(tn + 4 * g.y));
         }
 #pragma unroll 2
         for (int k = 0; k < m.maxv; ++k) {  // triangles: area and volume
             const int4 g = __ldg(m.vtri + (size_t)k * m.nv + i);
             if (g.x < 0) continue;
-            const V3<R> pa = ld3(xs + 3 * g.y), pb = ld3(xs + 3 * g.z);
-            const V3<R> nh = tn[4 * g.x + 3] * ld3(tn + 4 * g.x);  // unit normal
+            const V3<R> pa = xyz(ld4(xs + 4 * g.y)), pb = xyz(ld4(xs + 4 * g.z));
+            const Q4<R> tq = ld4(tn + 4 * g.x);
+            const V3<R> nh = tq.w * xyz(tq);  // unit normal
             f = f - (ha * cross(nh, pb - pa) + sv * cross(pa, pb));
         }
         R *o = v.Fv + 3 * (size_t)(first + i);
