@@ -383,6 +383,81 @@ __global__ void __launch_bounds__(256) spread_gather_kernel(View<R> v) {
     }
 }
 
+// Phase 2 with at least three blocks along every axis (neighbour blocks
+// distinct): along an axis the lower neighbour's tile covers this block's
+// local coordinates 0, 1 (tile positions 9, 10), the block's own tile all
+// eight (positions 1..8) and the upper neighbour's coordinate 7 (position
+// 0).  Each thread owns two nodes and adds, slot by slot in a fixed order,
+// the tile values that land on them.
+template <typename R>
+__global__ void __launch_bounds__(256) spread_gather3_kernel(View<R> v) {
+    __shared__ int nbin[27];  // bin of slot (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1), -1 if empty or absent
+    const int k = blockIdx.x;
+    const int bc[3] = {k % v.nb[0], (k / v.nb[0]) % v.nb[1], k / (v.nb[0] * v.nb[1])};
+    const int t = threadIdx.x;
+    if (t < 27) {
+        const int sz = t / 9 - 1, sy = (t / 3) % 3 - 1, sx = t % 3 - 1;
+        const int sl[3] = {sx, sy, sz};
+        int c[3];
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+            c[d] = bc[d] + sl[d];
+            if (v.per[d]) c[d] = wrap(c[d], v.nb[d]);
+            else ok &= c[d] >= 0 && c[d] < v.nb[d];
+        }
+        int kk = -1;
+        if (ok) {
+            kk = c[0] + v.nb[0] * (c[1] + v.nb[1] * c[2]);
+            if (v.start[kk + 1] == v.start[kk]) kk = -1;
+        }
+        nbin[t] = kk;
+    }
+    __syncthreads();
+    const size_t N = (size_t)v.N;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = t + 256 * h;
+        const int l[3] = {q % BLK, (q / BLK) % BLK, q / (BLK * BLK)};
+        const int x = bc[0] * BLK + l[0], y = bc[1] * BLK + l[1], z = bc[2] * BLK + l[2];
+        if (x >= v.nx || y >= v.ny || z >= v.nz) continue;
+        R f0 = R(0), f1 = R(0), f2 = R(0);
+        // per axis: the slots reaching this coordinate and the tile position there
+        int ns[3], sl[3][2] = {{0, 0}, {0, 0}, {0, 0}}, ps[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            // entry 0: lower neighbour (l < 2) or own block; entry 1: own block
+            // (l < 2) or upper neighbour (l = 7)
+            const bool lo = l[d] < 2, hi = l[d] == BLK - 1;
+            sl[d][0] = lo ? 0 : 1;
+            ps[d][0] = lo ? l[d] + 9 : l[d] + 1;
+            sl[d][1] = lo ? 1 : 2;
+            ps[d][1] = lo ? l[d] + 1 : 0;
+            ns[d] = (lo || hi) ? 2 : 1;
+        }
+        // at most two slots per axis: fixed trip counts keep the tables in registers
+#pragma unroll
+        for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+                for (int ix = 0; ix < 2; ++ix) {
+                    if (iz >= ns[2] || iy >= ns[1] || ix >= ns[0]) continue;
+                    const int kk = nbin[9 * sl[2][iz] + 3 * sl[1][iy] + sl[0][ix]];
+                    if (kk < 0) continue;
+                    const R *tt = v.tiles + (size_t)kk * 3 * TILE3;
+                    const int ti = ps[0][ix] + TILE * (ps[1][iy] + TILE * ps[2][iz]);
+                    f0 += tt[ti];
+                    f1 += tt[TILE3 + ti];
+                    f2 += tt[2 * TILE3 + ti];
+                }
+        const size_t n = (size_t)x + (size_t)v.nx * ((size_t)y + (size_t)v.ny * z);
+        const bool wall = !v.spread_all_nodes && (v.ntype[n] & 0x7f);
+        v.F[n] = wall ? R(0) : v.g[0] + f0;
+        v.F[N + n] = wall ? R(0) : v.g[1] + f1;
+        v.F[2 * N + n] = wall ? R(0) : v.g[2] + f2;
+    }
+}
+
 // Interpolation and Euler move: one CTA per non-empty bin stages u of the
 // 11^3 neighbourhood in shared memory (padded strides; lattice coordinates
 // of the tile's rows from per-axis tables built once); a warp takes two
@@ -778,7 +853,8 @@ void launch_bin_ranges(const View<R> &v, cudaStream_t st) {
 template <typename R>
 void launch_spread(const View<R> &v, cudaStream_t st) {
     spread_tile_kernel<R><<<v.nbins, 256, 0, st>>>(v);
-    spread_gather_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    if (v.nb[0] >= 3 && v.nb[1] >= 3 && v.nb[2] >= 3) spread_gather3_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    else spread_gather_kernel<R><<<v.nbins, 256, 0, st>>>(v);
 }
 
 template <typename R>
