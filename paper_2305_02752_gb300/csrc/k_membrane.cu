@@ -467,8 +467,16 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
     }
     double AV[4];
     block_total<R, 4>(av, AV, scratch);  // (synchronises: tn is complete below)
-    const D ua = {R((AV[0] - m.A0) / (m.A0 * m.A0)), R(AV[1] / (m.A0 * m.A0))};
-    const D uv = {R((AV[2] - m.V0) / (m.V0 * m.V0)), R(AV[3] / (m.V0 * m.V0))};
+    __shared__ R cuv[4];  // the area and volume strain factors and their derivatives, FP64 once per cell
+    if (threadIdx.x == 0) {
+        cuv[0] = R((AV[0] - m.A0) / (m.A0 * m.A0));
+        cuv[1] = R(AV[1] / (m.A0 * m.A0));
+        cuv[2] = R((AV[2] - m.V0) / (m.V0 * m.V0));
+        cuv[3] = R(AV[3] / (m.V0 * m.V0));
+    }
+    __syncthreads();
+    const D ua = {cuv[0], cuv[1]}, uv = {cuv[2], cuv[3]};
+    const R kA = R(m.k_area), kV = R(m.k_volume);
 
     Acc<R> th[4];  // lamFv . unit-modulus forces: link, bend, area, volume
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
@@ -514,8 +522,8 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
             const V3<D> &pk1 = p[(k + 1) % 3], &pk2 = p[(k + 2) % 3];
             const V3<D> fa = (dconst(R(-0.5)) * ua) * cross(nh, pk2 - pk1);
             const V3<D> fv = (dconst(R(-1) / R(6)) * uv) * cross(pk1, pk2);
-            add_into(ft + 3 * j[k], R(m.k_area), tans(fa));
-            add_into(ft + 3 * j[k], R(m.k_volume), tans(fv));
+            add_into(ft + 3 * j[k], kA, tans(fa));
+            add_into(ft + 3 * j[k], kV, tans(fv));
             const V3<R> lk = ld3(xt + 3 * j[k]);
             th[2].add(dot(lk, vals(fa)));
             th[3].add(dot(lk, vals(fv)));
