@@ -60,6 +60,8 @@ def lib():
         L.ora_set_velocity.argtypes = [C.c_void_p, C.c_void_p]
         L.ora_wall_links.argtypes = [C.c_void_p, _up]
         L.ora_step.argtypes = [C.c_void_p, C.c_int]
+        L.ora_set_time_scales.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.ora_set_time_scales.restype = C.c_int
         L.ora_get.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         L.ora_get_populations.argtypes = [C.c_void_p, _dp]
         L.ora_spread.argtypes = [C.c_void_p, C.c_long, _dp, _dp, _dp]
@@ -76,6 +78,9 @@ def lib():
         L.ora_num_cells.restype = C.c_int
         _lib = L
     return _lib
+
+
+INTEGRATORS = {'euler': 0, 'ab2': 1}
 
 
 def _c(a, dt=np.float64):
@@ -188,6 +193,13 @@ class OracleSim:
 
     def set_vertices(self, X):
         lib().ora_set_vertices(self.h, _c(X).ravel())
+
+    def set_time_scales(self, force_every=1, integrator='euler'):
+        """Membrane forces every `force_every` steps (held in between) and
+        the vertex integrator, 'euler' or 'ab2' (Sec. 2.6)."""
+        rc = lib().ora_set_time_scales(self.h, int(force_every), INTEGRATORS[integrator])
+        if rc != 0:
+            raise ValueError('force_every must be >= 1')
 
     def step(self, n=1):
         lib().ora_step(self.h, int(n))

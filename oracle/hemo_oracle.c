@@ -19,8 +19,9 @@
  *             F_total = F_link + F_bend + F_area + F_volume.
  *   Sec. 2.5  no-slip walls, periodic boundaries, walls moving in opposite
  *             directions (shear).
- *   Sec. 2.6  Euler integration of the vertex positions, cell update every
- *             fluid step.
+ *   Sec. 2.6  vertex positions integrated by Euler or by Adams-Bashforth;
+ *             the membrane (constitutive) model may be evaluated less often
+ *             than the fluid is updated (time-scale separation).
  * Readings where the paper is silent (each also applied by the CUDA path,
  * which implements them independently):
  *   - forcing: Guo-Zheng-Shi source term with the half-force velocity;
@@ -35,6 +36,15 @@
  *     K = k_link kBT / p, eps = (L - L0)/L0, m = maximum strain;
  *   - bending: 1/2 k_bend kBT (theta - theta0)^2 per edge, theta the signed
  *     angle between the outward normals of the two triangles of the edge;
+ *   - time-scale separation (Sec. 2.6, constant separation N): membrane
+ *     forces are evaluated on the steps n = n0, n0 + N, n0 + 2N, ... (n0 the
+ *     step at which the setting was made) and held unchanged on the steps in
+ *     between; spreading, the fluid update, interpolation and the vertex move
+ *     run every step.  The default is N = 1 with Euler;
+ *   - Adams-Bashforth (Sec. 2.6): the two-step explicit form
+ *     X^{n+1} = X^n + 3/2 U^n - 1/2 U^{n-1} with dt = 1, U^n the velocity
+ *     interpolated at X^n; the first step after the setting is made (no
+ *     U^{n-1} yet) is an Euler step;
  *   - area / volume: per cell, in strain form 1/2 k_area ((A - A0)/A0)^2 and
  *     1/2 k_volume ((V - V0)/V0)^2 with k in lattice energy units.  (The form
  *     1/2 k (V - V0)^2 / V0 with k_volume = 20 makes the explicit coupling
@@ -351,7 +361,16 @@ typedef struct {
     double *X, *Fv;        /* nvtot*3 */
     double *X0c;           /* initial centroids, ncell*3 */
     double discarded[3];
+    /* time-scale separation and vertex integrator (Sec. 2.6) */
+    int force_every;       /* N >= 1 */
+    int integrator;        /* ORA_EULER or ORA_AB2 */
+    long nstep, ts_origin; /* steps taken; step at which the setting was made */
+    int have_prev;         /* Up holds U^{n-1} */
+    double *Up;            /* nvtot*3 */
 } osim;
+
+#define ORA_EULER 0
+#define ORA_AB2 1
 
 void *ora_create(int nx, int ny, int nz, double tau, const int *periodic, const unsigned char *mask,
                  const double *wall_velocity, const double *g) {
@@ -372,6 +391,8 @@ void *ora_create(int nx, int ny, int nz, double tau, const int *periodic, const 
     s->f = (double *)malloc(sizeof(double) * Q * s->N);
     s->fn = (double *)malloc(sizeof(double) * Q * s->N);
     s->rho_c = (double *)malloc(sizeof(double) * s->N);
+    s->force_every = 1;
+    s->integrator = ORA_EULER;
     s->F = (double *)calloc(3 * s->N, sizeof(double));
     s->u = (double *)calloc(3 * s->N, sizeof(double));
     for (long n = 0; n < s->N; ++n) {
@@ -386,7 +407,7 @@ void ora_destroy(void *p) {
     if (!s) return;
     for (int t = 0; t < s->ntypes; ++t) mesh_free(&s->types[t]);
     free(s->mask); free(s->f); free(s->fn); free(s->rho_c); free(s->F); free(s->u);
-    free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c);
+    free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c); free(s->Up);
     free(s);
 }
 
@@ -414,6 +435,8 @@ int ora_add_cells(void *p, int type, int ncell, const double *centers, const dou
     s->X0c = (double *)realloc(s->X0c, sizeof(double) * 3 * (s->ncell + ncell));
     s->X = (double *)realloc(s->X, sizeof(double) * 3 * (old + (long)ncell * nv));
     s->Fv = (double *)realloc(s->Fv, sizeof(double) * 3 * (old + (long)ncell * nv));
+    s->Up = (double *)realloc(s->Up, sizeof(double) * 3 * (old + (long)ncell * nv));
+    s->have_prev = 0;
     for (int c = 0; c < ncell; ++c) {
         int id = s->ncell + c;
         s->cell_type[id] = type;
@@ -437,6 +460,20 @@ int ora_add_cells(void *p, int type, int ncell, const double *centers, const dou
 void ora_set_vertices(void *p, const double *X) {
     osim *s = (osim *)p;
     memcpy(s->X, X, sizeof(double) * 3 * s->nvtot);
+    s->have_prev = 0;
+    s->ts_origin = s->nstep;
+}
+
+/* time-scale separation N (membrane forces every N steps, held in between)
+ * and the vertex integrator; both count from the current step (Sec. 2.6) */
+int ora_set_time_scales(void *p, int force_every, int integrator) {
+    osim *s = (osim *)p;
+    if (force_every < 1 || (integrator != ORA_EULER && integrator != ORA_AB2)) return -1;
+    s->force_every = force_every;
+    s->integrator = integrator;
+    s->ts_origin = s->nstep;
+    s->have_prev = 0;
+    return 0;
 }
 
 /* populations at equilibrium with rho = 1 and the given velocity field
@@ -501,12 +538,15 @@ void ora_wall_links(void *p, uint32_t *links) {
  * velocity, interpolate and move */
 static void step_once(osim *s) {
     const long N = s->N;
-    /* 1-2: membrane forces at the current positions (per cell) */
-    for (long v = 0; v < 3 * s->nvtot; ++v) s->Fv[v] = 0;
-    for (int c = 0; c < s->ncell; ++c) {
-        const omesh *m = &s->types[s->cell_type[c]];
-        long o = s->cell_first[c];
-        membrane_forces(m, s->X + 3 * o, s->Fv + 3 * o, NULL, NULL, NULL);
+    /* 1-2: membrane forces at the current positions (per cell), on every
+     * N-th step only; the last ones are held in between */
+    if ((s->nstep - s->ts_origin) % s->force_every == 0) {
+        for (long v = 0; v < 3 * s->nvtot; ++v) s->Fv[v] = 0;
+        for (int c = 0; c < s->ncell; ++c) {
+            const omesh *m = &s->types[s->cell_type[c]];
+            long o = s->cell_first[c];
+            membrane_forces(m, s->X + 3 * o, s->Fv + 3 * o, NULL, NULL, NULL);
+        }
     }
     /* 3: F(x) = g + sum_v F_v delta_h(x - X_v); wall nodes discard */
     for (long n = 0; n < N; ++n)
@@ -583,7 +623,9 @@ static void step_once(osim *s) {
         }
         for (int d = 0; d < 3; ++d) s->u[3 * n + d] = (m[d] + 0.5 * s->F[3 * n + d]) / rho;
     }
-    /* 7: interpolate at X^n and move (Euler, dt = 1) */
+    /* 7: interpolate U^n at X^n and move (dt = 1): Euler X += U^n, or
+     * Adams-Bashforth X += 3/2 U^n - 1/2 U^{n-1} once U^{n-1} exists */
+    const int ab2 = s->integrator == ORA_AB2 && s->have_prev;
     for (long v = 0; v < s->nvtot; ++v) {
         double *X = s->X + 3 * v;
         long i0[3];
@@ -598,8 +640,14 @@ static void step_once(osim *s) {
                     if (n < 0) continue; /* resting wall outside the domain */
                     for (int d = 0; d < 3; ++d) U[d] += s->u[3 * n + d] * dl;
                 }
-        for (int d = 0; d < 3; ++d) X[d] += U[d];
+        double *Up = s->Up + 3 * v;
+        for (int d = 0; d < 3; ++d) {
+            X[d] += ab2 ? 1.5 * U[d] - 0.5 * Up[d] : U[d];
+            Up[d] = U[d];
+        }
     }
+    s->have_prev = s->integrator == ORA_AB2;
+    s->nstep += 1;
 }
 
 void ora_step(void *p, int nsteps) {
