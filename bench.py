@@ -185,6 +185,36 @@ def run_form(cfg, precision, warmup, steps, torch, flush, u_ref=None):
     return res, u
 
 
+TIME_SCALES = [(1, 'euler'), (2, 'euler'), (4, 'euler'), (4, 'ab2'), (10, 'ab2')]
+
+
+def time_scales(cfg, precision, warmup, steps, torch, flush):
+    """Time-scale separation (membrane forces every N steps, held in
+    between) and the vertex integrator: throughput of the same workload per
+    setting, and the velocity and vertex drift after warmup + steps steps
+    relative to forces every step with Euler."""
+    from paper_2305_02752_gb300 import hemo
+    out, ref = [], None
+    for n, integ in TIME_SCALES:
+        sim = hemo.Simulation.from_config(cfg, precision)
+        sim.set_time_scales(n, integ)
+        sim.step(warmup)
+        sim.sync()
+        total, _, _ = timed_steps(sim, torch, steps, flush, phase_every=0)
+        f = sim.get_fields(hemo.HEMO_U | hemo.HEMO_VERTS)
+        sim.close()
+        u, X = f['u'].astype(np.float64), f['X']
+        r = {'force_every': n, 'integrator': integ, 'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6,
+             'ms_per_step': total / steps}
+        if ref is None:
+            ref = (u, X)
+        else:
+            r['u_rel_l2_vs_every_step'] = float(np.linalg.norm(u - ref[0]) / np.linalg.norm(ref[0]))
+            r['X_max_abs_diff_vs_every_step'] = float(np.abs(X - ref[1]).max())
+        out.append(r)
+    return {'precision': precision, 'steps': warmup + steps, 'timed_steps': steps, 'results': out}
+
+
 def adjoint_cost(torch, steps=200, every=100):
     """Differentiation form on the 48^3 shear box with 4 red cells: device
     time per recorded forward step and per step of the reverse sweep
@@ -342,6 +372,7 @@ def main():
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-adjoint', action='store_true')
+    ap.add_argument('--no-time-scales', action='store_true')
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -428,6 +459,8 @@ def main():
         for p in ('f32', 'f16', 'bf16'):
             forms[p], _ = run_form(cfg, p, args.warmup, fsteps, torch, flush, u_ref=u64)
         line['forms'] = {'steps': args.warmup + fsteps, 'timed_steps': fsteps, 'results': forms}
+    if not args.no_time_scales and args.workload in ('channel', 'vessel'):
+        line['time_scales'] = time_scales(cfg, precision, args.warmup, min(args.steps, 200), torch, flush)
     if not args.no_e2e:
         line['e2e'] = e2e_job(cfg, precision, torch)
     if not args.no_adjoint:

@@ -127,11 +127,34 @@ int hemo_add_cells(hemo_sim *sim, const hemo_mesh_desc *mesh, int ncells, const 
 /* Advance `nsteps` coupled time steps, each in the order of Sec. 2.3:
  * membrane forces at X^n, spreading onto the lattice, BGK collision with the
  * force term and streaming, lattice velocity, interpolation to the vertices
- * and Euler move X^{n+1} = X^n + U (Sec. 2.6).  Asynchronous on the
+ * and the vertex move (Sec. 2.6; Euler X^{n+1} = X^n + U^n unless
+ * hemo_set_time_scales chose otherwise).  Asynchronous on the
  * simulation's stream.  Returns HEMO_OK or the sticky device status
  * (HEMO_ERR_NUMERIC / HEMO_ERR_DOMAIN) of earlier steps that has already
  * reached the host; hemo_sync() waits for it. */
 int hemo_step(hemo_sim *sim, int nsteps);
+
+/* Vertex integrators of Sec. 2.6. */
+enum hemo_integrator {
+    HEMO_EULER = 0,  /* X^{n+1} = X^n + U^n                                  */
+    HEMO_AB2 = 1     /* X^{n+1} = X^n + 3/2 U^n - 1/2 U^{n-1}, dt = 1; the
+                        first step after hemo_set_time_scales is an Euler
+                        step (no U^{n-1} yet)                                */
+};
+
+/* Time-scale separation of the cell and fluid updates (Sec. 2.6: the cell
+ * equations are integrated by Euler or Adams-Bashforth, and the constitutive
+ * model may be evaluated less often than the fluid is updated, with a
+ * constant separation).  From the current step on, the membrane forces are
+ * evaluated on every `force_every`-th step (the next step is one of them)
+ * and held unchanged on the steps in between; spreading, the lattice update,
+ * interpolation and the vertex move still run every step.  `integrator` is a
+ * hemo_integrator.  The default is force_every = 1 with HEMO_EULER.  May be
+ * called before or between steps.  Errors: HEMO_ERR_ARG for force_every < 1
+ * or an unknown integrator; HEMO_ERR_STATE while recording for hemo_backward
+ * (the differentiation form supports the default only, and hemo_record
+ * refuses other settings). */
+int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
 
 /* Wait for the stream and return the device status of all steps so far. */
 int hemo_sync(hemo_sim *sim);
@@ -203,7 +226,8 @@ int hemo_get_bins(hemo_sim *sim, int32_t *key, int32_t *perm, int32_t *start);
  * (even, >= 2), and take the current cell centroids as the reference of the
  * loss's drift term.  The current step count must be even.  Checkpoints are
  * device memory owned by the library: (steps / checkpoint_every + 1) copies
- * of the state. */
+ * of the state.  Needs the default time scales (forces every step, Euler):
+ * HEMO_ERR_STATE otherwise. */
 int hemo_record(hemo_sim *sim, int checkpoint_every);
 
 /* Deformation loss of the current vertices (its own definition; the paper

@@ -153,16 +153,25 @@ struct hemo_sim {
     cudaEvent_t ev = nullptr;
     bool ev_pending = false;
     unsigned sticky = 0;
-    // graphs
+    // time-scale separation and vertex integrator (Sec. 2.6)
+    int force_every = 1;          // membrane forces on every force_every-th step, held in between
+    int integrator = HEMO_EULER;
+    long long ts_origin = 0;      // step count at which the setting was made
+    bool have_prev = false;       // Uprev holds the previous step's vertex velocity
+    void *Uprev = nullptr;
+    void *csp = nullptr;          // per cell: centroid of the last re-base as R hi, lo
+    // graphs, one per step variant: parity + 2 force step + 4 integrator mode
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    static constexpr int NGRAPH = 12;
+    cudaGraphExec_t graph[NGRAPH] = {};
+    int graph_kernels[NGRAPH] = {};
+    int last_graph = -1;
     // staging for read-out
     void *staging = nullptr;
     size_t staging_bytes = 0;
     // phase timing
     bool timing = false;
     cudaEvent_t tev[HEMO_NUM_PHASES + 1] = {};
-    int kernels_per_step = 0;
     // differentiation form
     bool rec = false;
     int ck_every = 0;
@@ -277,18 +286,24 @@ View<R> make_view(hemo_sim *s) {
     v.anc_t = (R *)s->anc_t;
     v.tiles = (R *)s->tiles;
     v.status = s->status;
+    v.integ = 0;
+    v.Uprev = (R *)s->Uprev;
+    v.csp = (R *)s->csp;
     return v;
 }
 
+// One coupled step.  force: evaluate the membrane forces (else the last
+// ones are held, Sec. 2.6); v.integ selects the vertex integrator.
 template <typename R>
-void enqueue_step(hemo_sim *s, const View<R> &v, int parity, cudaStream_t st) {
+void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStream_t st) {
     auto mark = [&](int k) {
         if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
     };
     mark(HEMO_PHASE_MEMBRANE);
     if (s->ncell) {
         cudaMemsetAsync(v.counts, 0, sizeof(int) * v.nbins, st);
-        launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
+        if (force) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
+        else launch_hold_bins<R>(v, st);                        // F_v held: anchors and bin counts only
     }
     mark(HEMO_PHASE_BINS);
     if (s->ncell) launch_bin_ranges<R>(v, st);  // counting sort by block
@@ -309,13 +324,8 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, cudaStream_t st) {
         vi.dead = v.F;
         vi.dead_lines = (long long)(rsize(s) * 3 * (size_t)s->N / 128);
     }
-    if (s->ncell) launch_interpolate<R>(vi, st);  // X^{n+1} = X^n + I[u](X^n)
+    if (s->ncell) launch_interpolate<R>(vi, st);  // X^{n+1} = X^n + I[u](X^n) (Euler or Adams-Bashforth)
     mark(HEMO_NUM_PHASES);
-}
-
-template <typename R>
-void enqueue_step(hemo_sim *s, int parity, cudaStream_t st) {
-    enqueue_step<R>(s, make_view<R>(s), parity, st);
 }
 
 template <typename R>
@@ -338,7 +348,9 @@ int finalize_impl(hemo_sim *s) {
     s->cursor = (int *)dalloc(s, sizeof(int) * s->nbins);
     s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
     s->tiles = dalloc(s, rs * 3 * TILE_NODES3 * s->nbins);
-    if (!s->tiles || !s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
+    s->Uprev = dalloc(s, rs * 3 * std::max(nv, 1));
+    s->csp = dalloc(s, rs * 6 * std::max(nc, 1));
+    if (!s->tiles || !s->Uprev || !s->csp || !s->ctr || !s->off || !s->Fv || !s->vcell_d || !s->cell_first_d || !s->cell_type_d || !s->meshes_d ||
         !s->key || !s->perm_raw || !s->perm || !s->anc_i || !s->anc_t ||
         !s->counts || !s->cursor || !s->start)
         return fail(HEMO_ERR_OOM, "device allocation of cell and bin buffers failed");
@@ -490,28 +502,29 @@ int ensure_ready(hemo_sim *s) {
     return is_f64(s) ? finalize_impl<double>(s) : finalize_impl<float>(s);
 }
 
+// The step variant k = parity + 2 force + 4 integ, captured on first use.
 template <typename R>
-int capture_graphs(hemo_sim *s) {
-    for (int p = 0; p < 2; ++p) {
-        cudaGraph_t g = nullptr;
-        HEMO_CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-        enqueue_step<R>(s, p, s->cap);
-        cudaError_t e = cudaStreamEndCapture(s->cap, &g);
-        if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
-        size_t nn = 0;
-        cudaGraphGetNodes(g, nullptr, &nn);
-        std::vector<cudaGraphNode_t> nodes(nn);
-        cudaGraphGetNodes(g, nodes.data(), &nn);
-        int kernels = 0;
-        for (auto nd : nodes) {
-            cudaGraphNodeType ty;
-            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
-        }
-        s->kernels_per_step = kernels;
-        e = cudaGraphInstantiate(&s->graph[p], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+int capture_graph(hemo_sim *s, int k) {
+    cudaGraph_t g = nullptr;
+    View<R> v = make_view<R>(s);
+    v.integ = k >> 2;
+    HEMO_CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue_step<R>(s, v, k & 1, (k >> 1) & 1, s->cap);
+    cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
     }
+    s->graph_kernels[k] = kernels;
+    e = cudaGraphInstantiate(&s->graph[k], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return HEMO_OK;
 }
 
@@ -636,7 +649,7 @@ void enqueue_segment(hemo_sim *s, AdjView<R> a, int len, cudaStream_t st) {
         }
         return vj;
     };
-    for (int j = 0; j < len; ++j) enqueue_step<R>(s, slot(j), j & 1, st);
+    for (int j = 0; j < len; ++j) enqueue_step<R>(s, slot(j), j & 1, true, st);
     launch_rho_out<R>(v, s->precision, len & 1, rec + 4 * N * len, st);  // density after the segment
     for (int j = len - 1; j >= 0; --j) {
         View<R> vj = slot(j);
@@ -805,6 +818,8 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
     int rc = ensure_ready(s);
     if (rc) return rc;
     if (s->steps_done & 1) return fail(HEMO_ERR_STATE, "hemo_record: start at an even step count");
+    if (s->force_every != 1 || s->integrator != HEMO_EULER)
+        return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form needs forces every step and Euler");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     s->rec = true;
     s->ck_every = checkpoint_every;
@@ -1114,12 +1129,17 @@ int hemo_step(hemo_sim *s, int nsteps) {
     rc = poll_status(s);
     if (rc) return rc;
     if (nsteps == 0) return HEMO_OK;
-    if (!s->graph[0]) {
-        rc = is_f64(s) ? capture_graphs<double>(s) : capture_graphs<float>(s);
-        if (rc) return rc;
-    }
     for (int k = 0; k < nsteps; ++k) {
-        HEMO_CU(cudaGraphLaunch(s->graph[s->steps_done & 1], s->stream));
+        const bool force = (s->steps_done - s->ts_origin) % s->force_every == 0;
+        const int integ = s->integrator == HEMO_AB2 ? (s->have_prev ? 2 : 1) : 0;
+        const int gi = (int)(s->steps_done & 1) + 2 * (int)force + 4 * integ;
+        if (!s->graph[gi]) {
+            rc = is_f64(s) ? capture_graph<double>(s, gi) : capture_graph<float>(s, gi);
+            if (rc) return rc;
+        }
+        HEMO_CU(cudaGraphLaunch(s->graph[gi], s->stream));
+        s->last_graph = gi;
+        s->have_prev = s->integrator == HEMO_AB2;
         ++s->steps_done;
         if (s->rec && (s->steps_done - s->rec_start) % s->ck_every == 0) {
             rc = is_f64(s) ? save_checkpoint<double>(s) : save_checkpoint<float>(s);
@@ -1129,6 +1149,18 @@ int hemo_step(hemo_sim *s, int nsteps) {
     HEMO_CU(cudaMemcpyAsync(s->status_host, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
     HEMO_CU(cudaEventRecord(s->ev, s->stream));
     s->ev_pending = true;
+    return HEMO_OK;
+}
+
+int hemo_set_time_scales(hemo_sim *s, int force_every, int integrator) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (force_every < 1) return fail(HEMO_ERR_ARG, "force_every must be >= 1");
+    if (integrator != HEMO_EULER && integrator != HEMO_AB2) return fail(HEMO_ERR_ARG, "integrator must be HEMO_EULER or HEMO_AB2");
+    if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_time_scales: not while recording for the reverse sweep");
+    s->force_every = force_every;
+    s->integrator = integrator;
+    s->ts_origin = s->steps_done;
+    s->have_prev = false;
     return HEMO_OK;
 }
 
@@ -1274,21 +1306,22 @@ int hemo_set_phase_timing(hemo_sim *s, int on) {
     HEMO_CU(cudaStreamSynchronize(s->stream));
     if (on && !s->tev[0])
         for (int k = 0; k <= HEMO_NUM_PHASES; ++k) HEMO_CU(cudaEventCreate(&s->tev[k]));
-    for (int p = 0; p < 2; ++p)
-        if (s->graph[p]) {
-            cudaGraphExecDestroy(s->graph[p]);
-            s->graph[p] = nullptr;
+    for (int k = 0; k < hemo_sim::NGRAPH; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
         }
+    s->last_graph = -1;
     s->timing = on != 0;
     return HEMO_OK;
 }
 
 int hemo_get_phase_times(hemo_sim *s, float *ms, int *kernels_per_step) {
     if (!s || !ms) return fail(HEMO_ERR_ARG, "null pointer");
-    if (!s->timing || !s->steps_done || !s->graph[0]) return fail(HEMO_ERR_STATE, "phase timing is off or no timed step ran");
+    if (!s->timing || s->last_graph < 0) return fail(HEMO_ERR_STATE, "phase timing is off or no timed step ran");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     for (int k = 0; k < HEMO_NUM_PHASES; ++k) HEMO_CU(cudaEventElapsedTime(ms + k, s->tev[k], s->tev[k + 1]));
-    if (kernels_per_step) *kernels_per_step = s->kernels_per_step;
+    if (kernels_per_step) *kernels_per_step = s->graph_kernels[s->last_graph];
     return HEMO_OK;
 }
 
@@ -1298,8 +1331,8 @@ void hemo_destroy(hemo_sim *s) {
     clear_segment_graphs(s);
     for (int k = 0; k <= HEMO_NUM_PHASES; ++k)
         if (s->tev[k]) cudaEventDestroy(s->tev[k]);
-    for (int p = 0; p < 2; ++p)
-        if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
+    for (int k = 0; k < hemo_sim::NGRAPH; ++k)
+        if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->status_host) cudaFreeHost(s->status_host);

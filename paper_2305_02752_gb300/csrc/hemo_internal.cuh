@@ -131,6 +131,11 @@ template <typename R> struct View {
     int *anc_i;                // nv*3 stencil base floor(X) (wrapped on periodic axes)
     R *anc_t;                  // nv*3 fractions X - floor(X)
     R *tiles;                  // nbins*3*11^3 per-bin spreading tiles
+    // vertex integrator (Sec. 2.6): 0 Euler X += U; 1 Euler and U kept in
+    // Uprev; 2 Adams-Bashforth X += 3/2 U - 1/2 Uprev and U kept in Uprev
+    int integ;
+    R *Uprev;                  // nv*3 interpolated velocity of the previous step
+    R *csp;                    // ncell*6 centroid of the last re-base as R hi (3), lo (3)
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
     // staged collision: tiles {first row, rows} of wall-free rows (x-lines,
@@ -169,6 +174,7 @@ template <typename R> struct AdjView {
 
 // launchers (R = double for HEMO_F64, float otherwise)
 template <typename R> void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st);
+template <typename R> void launch_hold_bins(const View<R> &v, cudaStream_t st);
 // allows the staged collision kernels of a precision `bytes` of dynamic shared memory
 cudaError_t set_tile_smem_limit(int precision, int bytes);
 template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);
@@ -280,6 +286,60 @@ __device__ __forceinline__ int link_code(uint64_t lk, int i) { return (int)((lk 
 __host__ __device__ __forceinline__ int wrap(int j, int n) {
     int r = j % n;
     return r < 0 ? r + n : r;
+}
+
+// Anchor of a coordinate X = c + o (c the FP64 centroid, o the offset):
+// j = floor(X), t = X - j.  FP32 path: c arrives split into two floats
+// (c = ch + cl to 48 bits) and X is formed as a two-float sum, which keeps
+// t to FP32 precision without FP64 arithmetic.
+__device__ __forceinline__ void anchor_of(float ch, float cl, float o, int &j, float &t) {
+    const float sum = ch + o, bp = sum - ch;
+    const float err = ((ch - (sum - bp)) + (o - bp)) + cl;
+    const float fl = floorf(sum);
+    j = (int)fl;
+    t = (sum - fl) + err;  // sum - fl is exact
+    if (t >= 1.f) {
+        t -= 1.f;
+        ++j;
+    } else if (t < 0.f) {
+        t += 1.f;
+        --j;
+    }
+}
+__device__ __forceinline__ void anchor_of(double c, double, double o, int &j, double &t) {
+    const double X = c + o, fl = floor(X);
+    j = (int)fl;
+    t = X - fl;
+}
+
+// Stencil anchor (wrapped floor and fraction per axis), bin key and bin
+// count of vertex g at X = (ch + cl) + o; flags a vertex outside a
+// non-periodic axis.  Bin counts are added once per group of lanes with the
+// same key.
+template <typename R>
+__device__ __forceinline__ void bin_vertex(const View<R> &v, size_t g, const R *ch, const R *cl, const R *o) {
+    const int dims[3] = {v.nx, v.ny, v.nz};
+    int b[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int j;
+        R t;
+        anchor_of(ch[d], cl[d], o[d], j, t);
+        if (v.per[d]) {
+            j = wrap(j, dims[d]);
+        } else if (j < 0 || j >= dims[d]) {
+            atomicOr(v.status, ST_DOMAIN);
+        }
+        v.anc_i[3 * g + d] = j;
+        v.anc_t[3 * g + d] = t;
+        const int jc = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
+        b[d] = jc / BLK;
+    }
+    const int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
+    v.key[g] = key;
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, key);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
 }
 
 }  // namespace hemo

@@ -458,12 +458,55 @@ __global__ void __launch_bounds__(256) spread_gather3_kernel(View<R> v) {
     }
 }
 
-// Interpolation and Euler move: one CTA per non-empty bin stages u of the
+// The move of vertex i by its interpolated velocity U (dt = 1), Sec. 2.6:
+// INTEG 0 Euler; 1 Euler, keeping U; 2 the two-step Adams-Bashforth form
+// with the kept velocity of the previous step, keeping U.  All loads are
+// issued before the stores (off and Uprev are distinct buffers).
+template <int INTEG, typename R>
+__device__ __forceinline__ void move_vertex(const View<R> &v, int i, R U0, R U1, R U2) {
+    R *o = v.off + 3 * (size_t)i;
+    const R x0 = o[0], x1 = o[1], x2 = o[2];
+    if constexpr (INTEG == 0) {
+        o[0] = x0 + U0;
+        o[1] = x1 + U1;
+        o[2] = x2 + U2;
+    } else {
+        R *p = v.Uprev + 3 * (size_t)i;
+        if constexpr (INTEG == 2) {
+            const R p0 = p[0], p1 = p[1], p2 = p[2];
+            o[0] = x0 + (R(1.5) * U0 - R(0.5) * p0);
+            o[1] = x1 + (R(1.5) * U1 - R(0.5) * p1);
+            o[2] = x2 + (R(1.5) * U2 - R(0.5) * p2);
+        } else {
+            o[0] = x0 + U0;
+            o[1] = x1 + U1;
+            o[2] = x2 + U2;
+        }
+        p[0] = U0;
+        p[1] = U1;
+        p[2] = U2;
+    }
+}
+
+// Anchors, keys and bin counts on a step between two membrane-force
+// evaluations (Sec. 2.6), vertex-parallel: no re-base, so each vertex is at
+// X = (hi + lo of the centroid of the last re-base) + offset.
+template <typename R>
+__global__ void __launch_bounds__(256) hold_bins_kernel(View<R> v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.nv) return;
+    const R *cs = v.csp + 6 * (size_t)v.vcell[i];
+    const R *o = v.off + 3 * (size_t)i;
+    const R ch[3] = {cs[0], cs[1], cs[2]}, cl[3] = {cs[3], cs[4], cs[5]}, oi[3] = {o[0], o[1], o[2]};
+    bin_vertex(v, (size_t)i, ch, cl, oi);
+}
+
+// Interpolation and vertex move: one CTA per non-empty bin stages u of the
 // 11^3 neighbourhood in shared memory (padded strides; lattice coordinates
 // of the tile's rows from per-axis tables built once); a warp takes two
 // vertices, each half-warp's lanes own one (y, z) stencil row, and the 16
 // partial sums are reduced with warp shuffles.
-template <typename R>
+template <typename R, int INTEG>
 __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
     drop_dead_lines(v);
     constexpr int CAP = Stage<R>::CAP;
@@ -528,12 +571,7 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
                 U1 += __shfl_xor_sync(0xffffffffu, U1, o);
                 U2 += __shfl_xor_sync(0xffffffffu, U2, o);
             }
-            if (row0 >= 0 && (lane & 15) == 0) {
-                R *o = v.off + 3 * (size_t)sperm[q];
-                o[0] += U0;
-                o[1] += U1;
-                o[2] += U2;
-            }
+            if (row0 >= 0 && (lane & 15) == 0) move_vertex<INTEG>(v, sperm[q], U0, U1, U2);
         }
     }
 }
@@ -542,6 +580,7 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
 // of u is staged once as (ux, uy, uz, 0) per node, so each stencil node is
 // one 16-byte shared load; the weights stay in registers and each thread
 // sums its vertex's 64 terms itself (no staging of weights, no shuffles).
+template <int INTEG>
 __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
     drop_dead_lines(v);
     const int k = blockIdx.x;
@@ -603,10 +642,7 @@ __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
                     U2 += wa * t.z;
                 }
             }
-        float *o = v.off + 3 * (size_t)i;
-        o[0] += U0;
-        o[1] += U1;
-        o[2] += U2;
+        move_vertex<INTEG>(v, i, U0, U1, U2);
     }
 }
 
@@ -857,10 +893,22 @@ void launch_spread(const View<R> &v, cudaStream_t st) {
     else spread_gather_kernel<R><<<v.nbins, 256, 0, st>>>(v);
 }
 
+template <typename R, int INTEG>
+void launch_interpolate_as(const View<R> &v, cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) interpolate_v4_kernel<INTEG><<<v.nbins, 256, 0, st>>>(v);
+    else interpolate_kernel<R, INTEG><<<v.nbins, 256, 0, st>>>(v);
+}
+
 template <typename R>
 void launch_interpolate(const View<R> &v, cudaStream_t st) {
-    if constexpr (std::is_same<R, float>::value) interpolate_v4_kernel<<<v.nbins, 256, 0, st>>>(v);
-    else interpolate_kernel<R><<<v.nbins, 256, 0, st>>>(v);
+    if (v.integ == 2) launch_interpolate_as<R, 2>(v, st);
+    else if (v.integ == 1) launch_interpolate_as<R, 1>(v, st);
+    else launch_interpolate_as<R, 0>(v, st);
+}
+
+template <typename R>
+void launch_hold_bins(const View<R> &v, cudaStream_t st) {
+    if (v.nv) hold_bins_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v);
 }
 
 template <typename R>
@@ -886,6 +934,7 @@ void launch_set_vertices(const View<R> &v, const double *X, cudaStream_t st) {
     template void launch_bin_ranges<R>(const View<R> &, cudaStream_t);                     \
     template void launch_spread<R>(const View<R> &, cudaStream_t);                        \
     template void launch_interpolate<R>(const View<R> &, cudaStream_t);                   \
+    template void launch_hold_bins<R>(const View<R> &, cudaStream_t);                     \
     template void launch_verts_out<R>(const View<R> &, double *, double *, cudaStream_t); \
     template void launch_vertex_field<R>(const View<R> &, const R *, const R *, R *, R *, cudaStream_t); \
     template void launch_set_vertices<R>(const View<R> &, const double *, cudaStream_t);

@@ -129,30 +129,6 @@ __device__ void block_sum_r(R (&val)[K], R (*scratch)[32]) {
     __syncthreads();
 }
 
-// Anchor of a coordinate X = c + o (c the FP64 centroid, o the offset):
-// j = floor(X), t = X - j.  FP32 path: c arrives split into two floats
-// (c = ch + cl to 48 bits) and X is formed as a two-float sum, which keeps
-// t to FP32 precision without FP64 arithmetic.
-__device__ __forceinline__ void anchor_of(float ch, float cl, float o, int &j, float &t) {
-    const float sum = ch + o, bp = sum - ch;
-    const float err = ((ch - (sum - bp)) + (o - bp)) + cl;
-    const float fl = floorf(sum);
-    j = (int)fl;
-    t = (sum - fl) + err;  // sum - fl is exact
-    if (t >= 1.f) {
-        t -= 1.f;
-        ++j;
-    } else if (t < 0.f) {
-        t += 1.f;
-        --j;
-    }
-}
-__device__ __forceinline__ void anchor_of(double c, double, double o, int &j, double &t) {
-    const double X = c + o, fl = floor(X);
-    j = (int)fl;
-    t = X - fl;
-}
-
 // One CTA per cell.
 // mode 0 (the step): re-base the offsets (centroid += mean offset), area and
 //   volume, membrane forces F_v = -grad E into Fv, and each vertex's anchor
@@ -231,40 +207,19 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; ++k) {
             cnew[k] = v.ctr[3 * c + k] + (double)mean[k];
-            if (mode == 0) v.ctr[3 * c + k] = cnew[k];
             csplit[0][k] = R(cnew[k]);
             csplit[1][k] = R(cnew[k] - (double)csplit[0][k]);
+            if (mode == 0) {
+                v.ctr[3 * c + k] = cnew[k];
+                v.csp[6 * c + k] = csplit[0][k];
+                v.csp[6 * c + 3 + k] = csplit[1][k];
+            }
         }
     __syncthreads();
 
-    if (mode == 0) {  // anchors, keys and counts at the re-based positions
-        const R ch[3] = {csplit[0][0], csplit[0][1], csplit[0][2]}, cl[3] = {csplit[1][0], csplit[1][1], csplit[1][2]};
-        const int dims[3] = {v.nx, v.ny, v.nz};
-        for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-            const size_t g = (size_t)(first + i);
-            int b[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int j;
-                R t;
-                anchor_of(ch[d], cl[d], xs[4 * i + d], j, t);
-                if (v.per[d]) {
-                    j = wrap(j, dims[d]);
-                } else if (j < 0 || j >= dims[d]) {
-                    atomicOr(v.status, ST_DOMAIN);
-                }
-                v.anc_i[3 * g + d] = j;
-                v.anc_t[3 * g + d] = t;
-                const int jc = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
-                b[d] = jc / BLK;
-            }
-            const int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
-            v.key[g] = key;
-            const unsigned act = __activemask();
-            const unsigned grp = __match_any_sync(act, key);
-            if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
-        }
-    }
+    if (mode == 0)  // anchors, keys and counts at the re-based positions
+        for (int i = threadIdx.x; i < m.nv; i += blockDim.x)
+            bin_vertex(v, (size_t)(first + i), csplit[0], csplit[1], xs + 4 * i);
 
     // per triangle: a = n / |n|^2 and |n|, with n = (x1 - x0) x (x2 - x0);
     // area |n|/2 and volume x0 . (x1 x x2) / 6 summed per cell

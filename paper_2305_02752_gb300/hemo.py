@@ -33,6 +33,8 @@ class hemo_lattice_desc(C.Structure):
                 ('alloc_ctx', C.c_void_p), ('options', C.c_uint)]
 
 HEMO_OPT_NO_STAGING = 1
+HEMO_EULER, HEMO_AB2 = 0, 1
+INTEGRATORS = {'euler': HEMO_EULER, 'ab2': HEMO_AB2}
 
 
 class hemo_mesh_desc(C.Structure):
@@ -67,6 +69,7 @@ def lib():
         'hemo_set_velocity': ([vp, vp], i),
         'hemo_add_cells': ([vp, C.POINTER(hemo_mesh_desc), i, vp, vp, C.POINTER(i)], i),
         'hemo_step': ([vp, i], i),
+        'hemo_set_time_scales': ([vp, i, i], i),
         'hemo_sync': ([vp], i),
         'hemo_get_fields': ([vp, C.c_uint, vp, vp, vp, vp, vp], i),
         'hemo_get_sizes': ([vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(i), C.POINTER(i)], i),
@@ -96,7 +99,8 @@ def lib():
 
 def exported_symbols():
     """Names the header declares (used by the load test)."""
-    return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_sync',
+    return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_set_time_scales',
+            'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
             'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
@@ -240,6 +244,11 @@ class Simulation:
     # -- stepping ----------------------------------------------------------
     def step(self, n=1):
         check(lib().hemo_step(self.handle, int(n)))
+
+    def set_time_scales(self, force_every=1, integrator='euler'):
+        """Membrane forces every `force_every` steps, held in between, and
+        the vertex integrator 'euler' or 'ab2' (Sec. 2.6), from this step on."""
+        check(lib().hemo_set_time_scales(self.handle, int(force_every), INTEGRATORS[integrator]))
 
     def sync(self):
         return check(lib().hemo_sync(self.handle))

@@ -90,6 +90,7 @@ def test_null_handles():
     assert L.hemo_sync(None) == hemo.HEMO_ERR_ARG
     assert L.hemo_get_fields(None, 1, None, None, None, None, None) == hemo.HEMO_ERR_ARG
     assert L.hemo_velocity_set(None, None) == hemo.HEMO_ERR_ARG
+    assert L.hemo_set_time_scales(None, 2, hemo.HEMO_AB2) == hemo.HEMO_ERR_ARG
     L.hemo_destroy(None)
 
 
