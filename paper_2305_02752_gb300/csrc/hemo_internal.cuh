@@ -245,8 +245,11 @@ template <> struct Acc<float> {
 template <typename R>
 __device__ __forceinline__ void drop_dead_lines(const View<R> &v) {
     if (!v.dead_lines) return;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < v.dead_lines; l += stride)
+    const long long bs = (long long)blockDim.x * blockDim.y * blockDim.z;
+    const long long stride = (long long)gridDim.x * gridDim.y * gridDim.z * bs;
+    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    const long long t = threadIdx.x + (long long)blockDim.x * (threadIdx.y + (long long)blockDim.y * threadIdx.z);
+    for (long long l = b * bs + t; l < v.dead_lines; l += stride)
         asm volatile("discard.global.L2 [%0], 128;" ::"l"((char *)v.dead + 128 * l) : "memory");
 }
 
@@ -264,12 +267,8 @@ struct Nbr {
 };
 
 template <typename R>
-__device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
-    int x = n % v.nx;
-    int r = n / v.nx;
-    int y = r % v.ny;
-    int z = r / v.ny;
-    int sxy = v.nx * v.ny;
+__device__ __forceinline__ Nbr nbr_at(const View<R> &v, int x, int y, int z) {
+    const int sxy = v.nx * v.ny;
     Nbr o;
     o.xp = (x == v.nx - 1) ? -(v.nx - 1) : 1;
     o.xm = (x == 0) ? (v.nx - 1) : -1;
@@ -279,6 +278,18 @@ __device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
     o.zm = (z == 0) ? (v.nz - 1) * sxy : -sxy;
     return o;
 }
+
+template <typename R>
+__device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
+    const int r = n / v.nx;
+    return nbr_at(v, n % v.nx, r % v.ny, r / v.ny);
+}
+
+// Lattice kernels over all nodes use a grid of (x chunks of NODE_BX) x (y
+// groups of NODE_BY) x z with blocks of NODE_BX x NODE_BY threads: node
+// coordinates come without integer division and a warp covers 32
+// consecutive nodes of one x-row.
+constexpr int NODE_BX = 32, NODE_BY = 8;
 
 __device__ __forceinline__ int link_code(uint64_t lk, int i) { return (int)((lk >> (2 * i)) & 3u); }
 

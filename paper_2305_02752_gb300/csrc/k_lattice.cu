@@ -27,22 +27,24 @@ namespace {
 
 // Read the 19 populations arriving at node n.  LAYOUT 0: natural order (slot
 // i of n).  LAYOUT 1: after an even step (slot opp(i) of n - c_i, or slot i
-// of n when n - c_i is a wall).
-template <typename T, typename R, int LAYOUT>
+// of n when n - c_i is a wall).  LINKS false: no wall among the neighbours
+// (lk is not read).  I: the index type of the population array, 32-bit
+// unsigned when 19 N < 2^32 (fewer registers and address instructions).
+template <typename T, typename R, int LAYOUT, bool LINKS, typename I = size_t>
 __device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, const Nbr &o, R d[Q]) {
     const T *f = (const T *)v.f;
-    const size_t N = (size_t)v.N;
+    const I N = (I)v.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (LAYOUT == 0) {
-            d[i] = Store<T>::ld(f[(size_t)i * N + n]);
+            d[i] = Store<T>::ld(f[(I)i * N + (I)n]);
         } else {
             if (i == 0) {
                 d[i] = Store<T>::ld(f[n]);
-            } else if (link_code(lk, opp(i))) {
-                d[i] = Store<T>::ld(f[(size_t)i * N + n]);
+            } else if (LINKS && link_code(lk, opp(i))) {
+                d[i] = Store<T>::ld(f[(I)i * N + (I)n]);
             } else {
-                d[i] = Store<T>::ld(f[(size_t)opp(i) * N + n + o.of(-cx(i), -cy(i), -cz(i))]);
+                d[i] = Store<T>::ld(f[(I)opp(i) * N + (I)(n + o.of(-cx(i), -cy(i), -cz(i)))]);
             }
         }
     }
@@ -137,16 +139,13 @@ __device__ __forceinline__ void bgk_guo(const R (&d)[Q], R Fx, R Fy, R Fz, R om,
     }
 }
 
-// collision and streaming of fluid node n, reading and writing the global
-// array directly (any node, walls included)
-template <typename T, typename R, int PARITY>
-__device__ __forceinline__ void collide_node(const View<R> &v, int n) {
-    const uint8_t nt = v.ntype[n];
-    if (nt & 0x7f) return;  // wall node
-    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
-    const Nbr o = make_nbr(v, n);
+// collision and streaming of fluid node n with neighbour offsets o,
+// reading and writing the global array directly; LINKS false for a node
+// without wall neighbours (most of them: that path carries no wall terms)
+template <typename T, typename R, int PARITY, bool LINKS, typename I>
+__device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr &o, uint64_t lk) {
     R d[Q], p[Q];
-    load_pops<T, R, PARITY>(v, n, lk, o, d);
+    load_pops<T, R, PARITY, LINKS, I>(v, n, lk, o, d);
     const size_t N = (size_t)v.N;
     R rho, ux, uy, uz;
     bgk_guo<R>(d, v.F[n], v.F[N + n], v.F[2 * N + n], v.omega, p, rho, ux, uy, uz);
@@ -159,28 +158,50 @@ __device__ __forceinline__ void collide_node(const View<R> &v, int n) {
     T *f = (T *)v.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int code = link_code(lk, i);
+        const int code = LINKS ? link_code(lk, i) : 0;
         R q = p[i];
         if (code) {
             const R cw = R(cx(i)) * v.uw[code][0] + R(cy(i)) * v.uw[code][1] + R(cz(i)) * v.uw[code][2];
             q -= R(6) * R(wgt(i)) * rho * cw;
         }
+        const I NI = (I)N;
         if (PARITY == 0) {
-            f[(size_t)opp(i) * N + n] = Store<T>::st(q);
+            f[(I)opp(i) * NI + (I)n] = Store<T>::st(q);
         } else {
             if (code)
-                f[(size_t)opp(i) * N + n] = Store<T>::st(q);
+                f[(I)opp(i) * NI + (I)n] = Store<T>::st(q);
             else
-                f[(size_t)i * N + n + o.of(cx(i), cy(i), cz(i))] = Store<T>::st(q);
+                f[(I)i * NI + (I)(n + o.of(cx(i), cy(i), cz(i)))] = Store<T>::st(q);
         }
     }
 }
 
-template <typename T, typename R, int PARITY>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) collide_stream_kernel(View<R> v) {
+// node (x, y, z) = index n
+template <typename T, typename R, int PARITY, typename I>
+__device__ __forceinline__ void collide_at(const View<R> &v, int n, int x, int y, int z) {
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) return;  // wall node
+    if (nt & 0x80) collide_core<T, R, PARITY, true, I>(v, n, nbr_at(v, x, y, z), v.links[n]);
+    else collide_core<T, R, PARITY, false, I>(v, n, nbr_at(v, x, y, z), 0ull);
+}
+
+// any node given by its index (walls included), one code path for nodes
+// with and without wall links (the rows next to walls)
+template <typename T, typename R, int PARITY, typename I>
+__device__ __forceinline__ void collide_node(const View<R> &v, int n) {
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) return;  // wall node
+    const int r = n / v.nx;
+    collide_core<T, R, PARITY, true, I>(v, n, nbr_at(v, n % v.nx, r % v.ny, r / v.ny), (nt & 0x80) ? v.links[n] : 0ull);
+}
+
+// all nodes, grid of NODE_BX x NODE_BY blocks over (x, y, z)
+template <typename T, typename R, int PARITY, typename I>
+__global__ void __launch_bounds__(NODE_BX * NODE_BY, sizeof(R) == 4 ? 4 : 1) collide_stream_kernel(View<R> v) {
     drop_dead_lines(v);
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n < v.N) collide_node<T, R, PARITY>(v, n);
+    const int x = blockIdx.x * NODE_BX + threadIdx.x, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+    if (x >= v.nx || y >= v.ny) return;
+    collide_at<T, R, PARITY, I>(v, x + v.nx * (y + v.ny * z), x, y, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,7 +317,7 @@ static_assert(((CY_PACK >> 6) & 3) == 2 && ((CZ_PACK >> 10) & 3) == 2, "packed v
 
 constexpr int TILE_COPIES = Q + 3;  // lanes of warp 0 that issue the copies of a stage
 
-template <typename T, typename R, int PARITY>
+template <typename T, typename R, int PARITY, typename I>
 __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_kernel(View<R> v) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -409,30 +430,16 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
     const long long ne = (long long)v.nerows * nx;
     for (long long t = (long long)blockIdx.x * TILE_THREADS + threadIdx.x; t < ne; t += (long long)gridDim.x * TILE_THREADS) {
         const int jr = (int)(t / nx);
-        collide_node<T, R, PARITY>(v, v.erows[jr] * nx + (int)(t - (long long)jr * nx));
+        collide_node<T, R, PARITY, I>(v, v.erows[jr] * nx + (int)(t - (long long)jr * nx));
     }
 }
 
 // post-streaming velocity u = (sum f c + F/2) / rho with the force just
 // applied; LAYOUT as in load_pops.  Flags non-finite or |u| > 0.3.
-template <typename T, typename R, int LAYOUT>
-__global__ void __launch_bounds__(256) moments_kernel(View<R> v) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= v.N) return;
-    const uint8_t nt = v.ntype[n];
-    if (nt & 0x7f) {
-        if (v.rec) {  // recording into a fresh velocity buffer
-            const int id = nt & 0x7f;
-            v.u[n] = v.uw[id][0];
-            v.u[(size_t)v.N + n] = v.uw[id][1];
-            v.u[2 * (size_t)v.N + n] = v.uw[id][2];
-        }
-        return;
-    }
-    const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
-    const Nbr o = make_nbr(v, n);
+template <typename T, typename R, int LAYOUT, bool LINKS, typename I>
+__device__ __forceinline__ void moments_core(const View<R> &v, int n, const Nbr &o, uint64_t lk) {
     R d[Q];
-    load_pops<T, R, LAYOUT>(v, n, lk, o, d);
+    load_pops<T, R, LAYOUT, LINKS, I>(v, n, lk, o, d);
     R drho = R(0), mx = R(0), my = R(0), mz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -451,6 +458,25 @@ __global__ void __launch_bounds__(256) moments_kernel(View<R> v) {
     v.u[2 * N + n] = uz;
     const float q = (float)(ux * ux + uy * uy + uz * uz);
     if (!(q < U_LIMIT2)) atomicOr(v.status, ST_NUMERIC);
+}
+
+template <typename T, typename R, int LAYOUT, typename I>
+__global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_kernel(View<R> v) {
+    const int x = blockIdx.x * NODE_BX + threadIdx.x, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+    if (x >= v.nx || y >= v.ny) return;
+    const int n = x + v.nx * (y + v.ny * z);
+    const uint8_t nt = v.ntype[n];
+    if (nt & 0x7f) {
+        if (v.rec) {  // recording into a fresh velocity buffer
+            const int id = nt & 0x7f;
+            v.u[n] = v.uw[id][0];
+            v.u[(size_t)v.N + n] = v.uw[id][1];
+            v.u[2 * (size_t)v.N + n] = v.uw[id][2];
+        }
+        return;
+    }
+    if (nt & 0x80) moments_core<T, R, LAYOUT, true, I>(v, n, nbr_at(v, x, y, z), v.links[n]);
+    else moments_core<T, R, LAYOUT, false, I>(v, n, nbr_at(v, x, y, z), 0ull);
 }
 
 template <typename T, typename R>
@@ -498,7 +524,7 @@ __global__ void populations_out_kernel(View<R> v, double *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr nb = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT>(v, n, lk, nb, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, d);
     for (int i = 0; i < Q; ++i) o[i] = wgt(i) + (double)d[i];
 }
 
@@ -514,7 +540,7 @@ __global__ void rho_out_kernel(View<R> v, R *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr nb = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT>(v, n, lk, nb, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, d);
     R drho = R(0);
     for (int i = 0; i < Q; ++i) drho += d[i];
     out[n] = R(1) + drho;
@@ -579,7 +605,7 @@ __global__ void copy_natural_kernel(View<R> v, R *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr o = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT>(v, n, lk, o, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, o, d);
     for (int i = 0; i < Q; ++i) out[(size_t)i * N + n] = d[i];
 }
 
@@ -607,6 +633,15 @@ __global__ void restore_natural_kernel(View<R> v, const R *in) {
 }
 
 inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
+// 32-bit population indices when every index i N + n fits
+template <typename R>
+bool narrow_index(const View<R> &v) {
+    return (unsigned long long)Q * (unsigned long long)v.N <= 0xffffffffull;
+}
+template <typename R>
+dim3 node_grid(const View<R> &v) {
+    return dim3((unsigned)nblocks(v.nx, NODE_BX), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
+}
 
 }  // namespace
 
@@ -639,15 +674,25 @@ void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st
         // node by node once its tiles are done.  Even steps touch each node's
         // own slots, which the per-node kernel streams faster.
         if (v.ntiles && parity == 1) {
-            HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
+            if (narrow_index(v))
+                HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1, unsigned><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
+            else
+                HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1, size_t><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
             return;
         }
     }
-    const int g = nblocks(v.N, 256);
-    if (parity == 0)
-        HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0><<<g, 256, 0, st>>>(v)));
-    else
-        HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1><<<g, 256, 0, st>>>(v)));
+    const dim3 g = node_grid(v), b(NODE_BX, NODE_BY);
+    if (narrow_index(v)) {
+        if (parity == 0)
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned><<<g, b, 0, st>>>(v)));
+        else
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned><<<g, b, 0, st>>>(v)));
+    } else {
+        if (parity == 0)
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t><<<g, b, 0, st>>>(v)));
+        else
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t><<<g, b, 0, st>>>(v)));
+    }
 }
 
 cudaError_t set_tile_smem_limit(int precision, int bytes) {
@@ -656,7 +701,8 @@ cudaError_t set_tile_smem_limit(int precision, int bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     };
     using R = float;
-    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1>)));
+    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1, unsigned>)));
+    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1, size_t>)));
     return e;
 }
 
@@ -664,11 +710,18 @@ template <typename R>
 void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st) {
     // after an even step the array is in the swapped layout (1), after an odd
     // step in natural order (0)
-    const int g = nblocks(v.N, 256);
-    if (parity == 0)
-        HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 1><<<g, 256, 0, st>>>(v)));
-    else
-        HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 0><<<g, 256, 0, st>>>(v)));
+    const dim3 g = node_grid(v), b(NODE_BX, NODE_BY);
+    if (narrow_index(v)) {
+        if (parity == 0)
+            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 1, unsigned><<<g, b, 0, st>>>(v)));
+        else
+            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 0, unsigned><<<g, b, 0, st>>>(v)));
+    } else {
+        if (parity == 0)
+            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 1, size_t><<<g, b, 0, st>>>(v)));
+        else
+            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 0, size_t><<<g, b, 0, st>>>(v)));
+    }
 }
 
 template <typename R>
