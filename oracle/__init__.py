@@ -27,11 +27,15 @@ _bp = np.ctypeslib.ndpointer(dtype=np.uint8, flags='C_CONTIGUOUS')
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain -O2, strict IEEE: no fast-math and
-    no FMA contraction, so x86 and Arm hosts give the same results)."""
+    no FMA contraction, so x86 and Arm hosts give the same results), with
+    OpenMP where the compiler has it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f'.{os.getpid()}.tmp'
-        subprocess.check_call(['gcc', '-O2', '-std=c99', '-fPIC', '-shared', '-ffp-contract=off',
-                               '-o', tmp, _SRC, '-lm'])
+        base = ['gcc', '-O2', '-std=c99', '-fPIC', '-shared', '-ffp-contract=off', '-o', tmp, _SRC, '-lm']
+        try:
+            subprocess.check_call(base[:1] + ['-fopenmp'] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -76,11 +80,22 @@ def lib():
         L.ora_num_vertices.restype = C.c_long
         L.ora_num_cells.argtypes = [C.c_void_p]
         L.ora_num_cells.restype = C.c_int
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_get_threads.restype = C.c_int
+        L.ora_set_threads(1)
         _lib = L
     return _lib
 
 
 INTEGRATORS = {'euler': 0, 'ab2': 1}
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's loops over independent nodes, cells and
+    vertices (1 unless set; results do not depend on it).  Returns the
+    number in effect (1 when the oracle was built without OpenMP)."""
+    lib().ora_set_threads(int(n))
+    return lib().ora_get_threads()
 
 
 def _c(a, dt=np.float64):

@@ -8,7 +8,11 @@
  * (the CUDA library) never calls it and shares no code with it.
  *
  * Plain FP64 loops, two population arrays and pull streaming, in the order
- * the method states.  Paper passages followed:
+ * the method states.  The loops over independent nodes, cells and vertices
+ * carry OpenMP annotations (threads set by ora_set_threads, 1 by default);
+ * each iteration writes only its own node, cell or vertex, so the results
+ * do not depend on the thread count.  The spreading loop, which sums into
+ * shared nodes, stays serial.  Paper passages followed:
  *   Sec. 2.2  BGK lattice-Boltzmann update (eq. for f_i(x+e_i, t+1)), the
  *             moments rho = sum_i f_i and u = sum_i f_i e_i / rho, the
  *             second-order equilibrium w_i rho [1 + 3 e.u + 9/2 (e.u)^2 -
@@ -55,6 +59,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 
@@ -542,6 +549,7 @@ static void step_once(osim *s) {
      * N-th step only; the last ones are held in between */
     if ((s->nstep - s->ts_origin) % s->force_every == 0) {
         for (long v = 0; v < 3 * s->nvtot; ++v) s->Fv[v] = 0;
+        #pragma omp parallel for schedule(static)
         for (int c = 0; c < s->ncell; ++c) {
             const omesh *m = &s->types[s->cell_type[c]];
             long o = s->cell_first[c];
@@ -549,6 +557,7 @@ static void step_once(osim *s) {
         }
     }
     /* 3: F(x) = g + sum_v F_v delta_h(x - X_v); wall nodes discard */
+    #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n)
         for (int d = 0; d < 3; ++d) s->F[3 * n + d] = s->mask[n] ? 0.0 : s->g[d];
     s->discarded[0] = s->discarded[1] = s->discarded[2] = 0;
@@ -571,6 +580,7 @@ static void step_once(osim *s) {
     }
     /* 4: BGK collision with the Guo forcing term (in place in f) */
     double om = 1.0 / s->tau;
+    #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
         double *f = s->f + n * Q;
@@ -594,6 +604,7 @@ static void step_once(osim *s) {
         s->rho_c[n] = rho;
     }
     /* 5: pull streaming with halfway bounce-back */
+    #pragma omp parallel for schedule(static)
     for (int z = 0; z < s->nz; ++z)
         for (int y = 0; y < s->ny; ++y)
             for (int x = 0; x < s->nx; ++x) {
@@ -613,6 +624,7 @@ static void step_once(osim *s) {
             }
     double *tmp = s->f; s->f = s->fn; s->fn = tmp;
     /* 6: velocity of the streamed populations with the applied force F/2 */
+    #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
         const double *f = s->f + n * Q;
@@ -626,6 +638,7 @@ static void step_once(osim *s) {
     /* 7: interpolate U^n at X^n and move (dt = 1): Euler X += U^n, or
      * Adams-Bashforth X += 3/2 U^n - 1/2 U^{n-1} once U^{n-1} exists */
     const int ab2 = s->integrator == ORA_AB2 && s->have_prev;
+    #pragma omp parallel for schedule(static)
     for (long v = 0; v < s->nvtot; ++v) {
         double *X = s->X + 3 * v;
         long i0[3];
@@ -648,6 +661,23 @@ static void step_once(osim *s) {
     }
     s->have_prev = s->integrator == ORA_AB2;
     s->nstep += 1;
+}
+
+/* worker threads of the annotated loops (no effect without OpenMP) */
+void ora_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int ora_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void ora_step(void *p, int nsteps) {

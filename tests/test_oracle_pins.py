@@ -395,3 +395,24 @@ def test_wall_links_brute_force():
                         if yy < 0 or yy >= ny or mask[zz, yy, xx]:
                             b |= 1 << i
                 assert links[z, y, x] == b
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's loops over independent nodes, cells and vertices may run
+    on several threads: the coupled state is the same bits with 1 and 4."""
+    from tests.helpers import small_cell_shear
+    cfg = small_cell_shear(n=16, steps=6)
+    out = []
+    for nt in (1, 4):
+        O.set_threads(nt)
+        try:
+            s = O.from_config(cfg)
+            s.step(6)
+            out.append((s.get(), s.populations()))
+            s.close()
+        finally:
+            O.set_threads(1)
+    (a, fa), (b, fb) = out
+    assert np.array_equal(fa, fb)
+    for k in ('u', 'X', 'Fv', 'rho'):
+        assert np.array_equal(a[k], b[k]), k
