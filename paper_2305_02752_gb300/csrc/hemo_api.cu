@@ -423,6 +423,43 @@ int finalize_impl(hemo_sim *s) {
             for (size_t k = 0; k < wings[i].size(); ++k) vwing[k * m.nv + i] = wings[i][k];
             for (size_t k = 0; k < tris[i].size(); ++k) vtri[k * m.nv + i] = tris[i][k];
         }
+        // the fan of each vertex i in cyclic order: triangles T_k = (i, j_k,
+        // j_k+1) as oriented, so that consecutive T_k share the edge (i, j_k).
+        // Slot 0 repeats the last entry (the loop's carried values start
+        // from it), slots 1..deg hold k = 0..deg-1; per entry {T_k, j_k,
+        // edge (i, j_k) << 1 | role of i in it, edge (j_k, j_k+1)}.
+        std::unordered_map<long long, int> pair_edge;
+        pair_edge.reserve(2 * (size_t)m.ne);
+        for (int q = 0; q < m.ne; ++q) {
+            const int a = edge_p[4 * (size_t)q], b = edge_p[4 * (size_t)q + 1];
+            pair_edge[(long long)std::min(a, b) * m.nv + std::max(a, b)] = q;
+        }
+        auto edge_of = [&](int a, int b) { return pair_edge.at((long long)std::min(a, b) * m.nv + std::max(a, b)); };
+        std::vector<int4> vfan((size_t)(maxv + 1) * m.nv, make_int4(-1, 0, 0, 0));
+        for (int i = 0; i < m.nv; ++i) {
+            std::unordered_map<int, int4> from;  // j_k -> {T_k, j_k, j_k+1}
+            for (const int4 &g : tris[i]) from[g.y] = make_int4(g.x, g.y, g.z, 0);
+            const int deg = (int)tris[i].size();
+            std::vector<int4> fan;
+            int j = tris[i][0].y;
+            for (int k = 0; k < deg; ++k) {
+                const auto it = from.find(j);
+                if (it == from.end()) return fail(HEMO_ERR_ARG, "mesh: a vertex's triangles do not form one fan");
+                const int4 T = it->second;
+                const int e = edge_of(i, j), role = edge_p[4 * (size_t)e] == i ? 0 : 1;
+                // the edge's triangle lists: (v0, v1, a) first, (v1, v0, b) second
+                const int t_in = etri_p[2 * (size_t)e + role];  // contains i -> j
+                if (t_in != T.x) return fail(HEMO_ERR_ARG, "mesh: inconsistent orientation in a vertex fan");
+                fan.push_back(make_int4(T.x, j, (e << 1) | role, edge_of(T.y, T.z)));
+                j = T.z;
+            }
+            if (j != tris[i][0].y) return fail(HEMO_ERR_ARG, "mesh: a vertex's fan does not close");
+            vfan[i] = fan[deg - 1];
+            for (int k = 0; k < deg; ++k) vfan[(size_t)(k + 1) * m.nv + i] = fan[k];
+        }
+        int4 *dvfan = (int4 *)dalloc(s, sizeof(int4) * vfan.size());
+        if (!dvfan) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        HEMO_CU(cudaMemcpy(dvfan, vfan.data(), sizeof(int4) * vfan.size(), cudaMemcpyHostToDevice));
         int4 *dvend = (int4 *)dalloc(s, sizeof(int4) * vend.size());
         int2 *dvwing = (int2 *)dalloc(s, sizeof(int2) * vwing.size());
         int4 *dvtri = (int4 *)dalloc(s, sizeof(int4) * vtri.size());
@@ -450,6 +487,7 @@ int finalize_impl(hemo_sim *s) {
         d.vend = dvend;
         d.vwing = dvwing;
         d.vtri = dvtri;
+        d.vfan = dvfan;
         d.A0 = m.A0;
         d.V0 = m.V0;
         d.K = R(m.k_link * m.kbt / m.persistence);

@@ -83,6 +83,11 @@ template <typename R> struct MeshDev {
     const int4 *vend;
     const int2 *vwing;
     const int4 *vtri;
+    // per vertex its fan in cyclic order, slot-major over maxv + 1 slots:
+    // slot 0 = the last entry again, slots 1..deg the entries k = 0..deg-1,
+    // then -1; entry {T_k, j_k, edge (i, j_k) << 1 | role, edge (j_k, j_k+1)}
+    // with T_k = (i, j_k, j_k+1) as oriented
+    const int4 *vfan;
     double A0, V0;
     R K;                // k_link * kbt / persistence
     R m2;               // max_strain^2

@@ -303,35 +303,37 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     }
     __syncthreads();
 
-    // per vertex: the sum over its edges and triangles
+    // per vertex: the sum over its edges and triangles, walking the fan
+    // T_k = (i, j_k, j_k+1) in cyclic order so that each triangle record and
+    // each neighbour position is loaded once: at step k the edge (i, j_k)
+    // (link and lever-rule bending; its triangles are T_k and T_k-1) and the
+    // triangle T_k-1 (wing term of its edge opposite i, area and volume)
     const R ha = cav[0], sv = cav[1];
     for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
         const V3<R> pi = xyz(ld4(xs + 4 * i));
         V3<R> f = {R(0), R(0), R(0)};
-#pragma unroll 2
-        for (int k = 0; k < m.maxv; ++k) {  // edges that end here: link and lever-rule bending terms
-            const int4 g = __ldg(m.vend + (size_t)k * m.nv + i);
-            if (g.x < 0) continue;
-            const int id = g.x >> 1, r = g.x & 1;
-            const V3<R> a1 = xyz(ld4(tn + 4 * g.z)), a2 = xyz(ld4(tn + 4 * g.w));
-            const Q4<R> cf = ld4(es + 4 * id);
-            const V3<R> lk = cf.x * (xyz(ld4(xs + 4 * g.y)) - pi);
-            f = r == 0 ? f + lk + (cf.z * a1 + cf.w * a2) : f + lk - ((cf.z + cf.y) * a1 + (cf.w + cf.y) * a2);
-        }
-#pragma unroll 2
-        for (int k = 0; k < m.maxv; ++k) {  // edges this vertex is a wing of
-            const int2 g = __ldg(m.vwing + (size_t)k * m.nv + i);
-            if (g.x < 0) continue;
-            f = f + es[4 * g.x + 1] * xyz(ld4(tn + 4 * g.y));
-        }
-#pragma unroll 2
-        for (int k = 0; k < m.maxv; ++k) {  // triangles: area and volume
-            const int4 g = __ldg(m.vtri + (size_t)k * m.nv + i);
-            if (g.x < 0) continue;
-            const V3<R> pa = xyz(ld4(xs + 4 * g.y)), pb = xyz(ld4(xs + 4 * g.z));
-            const Q4<R> tq = ld4(tn + 4 * g.x);
-            const V3<R> nh = tq.w * xyz(tq);  // unit normal
-            f = f - (ha * cross(nh, pb - pa) + sv * cross(pa, pb));
+        int4 g = __ldg(m.vfan + i);  // slot 0: the last entry
+        Q4<R> ap = ld4(tn + 4 * g.x);  // T_k-1: n / |n|^2 and |n|
+        V3<R> xp = xyz(ld4(xs + 4 * g.y));  // position of j_k-1
+        int op = g.w;  // edge of T_k-1 opposite i
+        for (int k = 1; k <= m.maxv; ++k) {
+            g = __ldg(m.vfan + (size_t)k * m.nv + i);
+            if (g.x < 0) break;
+            const Q4<R> ak = ld4(tn + 4 * g.x);
+            const V3<R> xk = xyz(ld4(xs + 4 * g.y));
+            const Q4<R> cf = ld4(es + 4 * (g.z >> 1));
+            // the edge's triangles (v0, v1, a), (v1, v0, b) are T_k, T_k-1
+            // when i is its v0 (role 0) and T_k-1, T_k otherwise
+            const bool r1 = g.z & 1;
+            const V3<R> a1 = r1 ? xyz(ap) : xyz(ak), a2 = r1 ? xyz(ak) : xyz(ap);
+            const V3<R> lk = cf.x * (xk - pi);
+            f = r1 ? f + lk - ((cf.z + cf.y) * a1 + (cf.w + cf.y) * a2) : f + lk + (cf.z * a1 + cf.w * a2);
+            f = f + es[4 * op + 1] * xyz(ap);
+            const V3<R> nh = ap.w * xyz(ap);  // unit normal of T_k-1
+            f = f - (ha * cross(nh, xk - xp) + sv * cross(xp, xk));
+            ap = ak;
+            xp = xk;
+            op = g.w;
         }
         R *o = v.Fv + 3 * (size_t)(first + i);
         o[0] = f.x;
