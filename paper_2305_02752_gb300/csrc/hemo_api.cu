@@ -3,6 +3,7 @@
 // per-step kernel sequence captured once per parity as a CUDA graph, status
 // handling and read-out.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -526,6 +527,10 @@ int finalize_impl(hemo_sim *s) {
     if (smem > 48 * 1024) HEMO_CU(set_cell_smem_limit<R>(smem));
     const size_t smem_adj = cell_adjoint_smem_bytes<R>(s->max_nv, s->max_nt);
     if (smem_adj > 48 * 1024) HEMO_CU(set_cell_adjoint_smem_limit<R>(smem_adj));
+    if (std::is_same<R, float>::value) {
+        const size_t gs = cell_adjoint_gather_bytes(s->max_nv, s->max_nt, s->max_ne);
+        if (gs > 48 * 1024 && gs <= CELL_ADJ_GATHER_MAX_SMEM) HEMO_CU(set_cell_adjoint_gather_smem_limit(gs));
+    }
     if (!nc) {  // no cells: the force field is the body force, written once
         View<R> v = make_view<R>(s);
         launch_spread<R>(v, st);

@@ -214,6 +214,14 @@ template <typename R> void launch_adj_collide(const View<R> &v, const AdjView<R>
 template <typename R> void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st);
 template <typename R> cudaError_t set_cell_adjoint_smem_limit(size_t bytes);
 template <typename R> size_t cell_adjoint_smem_bytes(int max_nv, int max_nt) { return (9 * (size_t)max_nv + 8 * (size_t)max_nt) * sizeof(R); }
+// FP32 gather form of the membrane adjoint: positions, direction, triangle
+// and edge records with their derivatives, 16 bytes each; used while it fits
+// the largest shared-memory allocation of a CTA
+inline size_t cell_adjoint_gather_bytes(int max_nv, int max_nt, int max_ne) {
+    return 8 * ((size_t)max_nv + (size_t)max_nt + (size_t)max_ne) * sizeof(float);
+}
+constexpr size_t CELL_ADJ_GATHER_MAX_SMEM = 227 * 1024;
+cudaError_t set_cell_adjoint_gather_smem_limit(size_t bytes);
 template <typename R>
 void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_grad, R *out_interp, cudaStream_t st);
 template <typename R>

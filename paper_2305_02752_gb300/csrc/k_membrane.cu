@@ -19,6 +19,8 @@
 // standard one (Bridson et al. 2003): the wing vertices move along their
 // triangle normals with weight |e| / |n|^2, the edge vertices carry the
 // lever-rule remainder.
+#include <type_traits>
+
 #include "hemo_internal.cuh"
 
 namespace hemo {
@@ -493,6 +495,137 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
     for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) a.lamX[3 * (size_t)first + i] += ft[i];
 }
 
+// FP32 form of the membrane adjoint as a gather, in the forward kernel's
+// order: the triangle pass and the edge pass leave their records (as in
+// cell_kernel) with their derivatives along lamFv, then each vertex walks
+// its fan and sums its link, bending, area and volume terms as dual numbers.
+// The derivative parts give the Hessian product (times the moduli) added to
+// lamX; the value parts, dotted with lamFv, give the unit-modulus terms
+// summed into the gradients of the four moduli.  No shared atomics.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) cell_adjoint_gather_kernel(View<float> v, AdjView<float> a) {
+    using R = float;
+    using D = Dual<R>;
+    const int c = blockIdx.x;
+    const int type = v.cell_type[c];
+    const MeshDev<R> m = v.meshes[type];
+    const int first = v.cell_first[c];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *xv = reinterpret_cast<R *>(smem_raw);  // nv*4 positions (relative to the centroid)
+    R *xd = xv + 4 * v.max_nv;                 // nv*4 the direction lamFv
+    R *tv = xd + 4 * v.max_nv;                 // nt*4 n / |n|^2 and |n|
+    R *td = tv + 4 * v.max_nt;                 // nt*4 their derivatives
+    R *ev = td + 4 * v.max_nt;                 // ne*4 edge coefficients (unit moduli)
+    R *et = ev + 4 * v.max_ne;                 // ne*4 their derivatives
+    __shared__ double scratch[6][32];
+    __shared__ R cuv[4];  // unit-modulus area and volume factors and their derivatives
+    auto dq = [](const R *pv, const R *pt) -> V3<D> {
+        const float4 p = *reinterpret_cast<const float4 *>(pv), q = *reinterpret_cast<const float4 *>(pt);
+        return {{p.x, q.x}, {p.y, q.y}, {p.z, q.z}};
+    };
+    auto st4 = [](R *o, R x, R y, R z, R w) { *reinterpret_cast<float4 *>(o) = make_float4(x, y, z, w); };
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {  // re-based offsets of the forward step
+        const R *o = v.off + 3 * (size_t)(first + i), *l = a.lamFv + 3 * (size_t)(first + i);
+        st4(xv + 4 * i, o[0], o[1], o[2], R(0));
+        st4(xd + 4 * i, l[0], l[1], l[2], R(0));
+    }
+    __syncthreads();
+
+    Acc<R> av[4];  // A, dA, V, dV
+    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+        const int4 T = __ldg(m.tri4 + t);
+        const V3<D> p0 = dq(xv + 4 * T.x, xd + 4 * T.x), p1 = dq(xv + 4 * T.y, xd + 4 * T.y),
+                    p2 = dq(xv + 4 * T.z, xd + 4 * T.z);
+        const V3<D> n = cross(p1 - p0, p2 - p0);
+        const D q = dot(n, n), ln = dsqrt(q), iq = dconst(R(1)) / q;
+        const V3<D> an = iq * n;
+        st4(tv + 4 * t, an.x.v, an.y.v, an.z.v, ln.v);
+        st4(td + 4 * t, an.x.t, an.y.t, an.z.t, ln.t);
+        const D vo = dot(p0, cross(p1, p2));
+        av[0].add(R(0.5) * ln.v);
+        av[1].add(R(0.5) * ln.t);
+        av[2].add(vo.v / R(6));
+        av[3].add(vo.t / R(6));
+    }
+    double AV[4];
+    block_total<R, 4>(av, AV, scratch);  // (synchronises: the triangle records are complete below)
+    if (threadIdx.x == 0) {  // once per cell in FP64
+        cuv[0] = R(0.5 * (AV[0] - m.A0) / (m.A0 * m.A0));
+        cuv[1] = R(0.5 * AV[1] / (m.A0 * m.A0));
+        cuv[2] = R((AV[2] - m.V0) / (m.V0 * m.V0) / 6.0);
+        cuv[3] = R(AV[3] / (m.V0 * m.V0) / 6.0);
+    }
+
+    // per edge, unit moduli: link s (F on v0 = s (x1 - x0)), cb |e|, cb sa0, cb sb0
+    for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
+        const int4 E = __ldg(reinterpret_cast<const int4 *>(m.edge) + e);  // v0, v1, a, b
+        const int2 T = __ldg(reinterpret_cast<const int2 *>(m.etri) + e);
+        const V3<D> p0 = dq(xv + 4 * E.x, xd + 4 * E.x), p1 = dq(xv + 4 * E.y, xd + 4 * E.y);
+        const V3<D> pa = dq(xv + 4 * E.z, xd + 4 * E.z), pb = dq(xv + 4 * E.w, xd + 4 * E.w);
+        const V3<D> ed = p1 - p0;
+        const D L = dsqrt(dot(ed, ed)), iL = dconst(R(1)) / L;
+        const D eps = L * dconst(__ldg(m.invL0 + e)) - dconst(R(1));
+        const D den = dconst(m.m2) - eps * eps;
+        const D sl = dconst(m.Ku) * (eps + eps / den) * iL;
+        const V3<D> a1 = dq(tv + 4 * T.x, td + 4 * T.x), a2 = dq(tv + 4 * T.y, td + 4 * T.y);
+        const D th = datan2(dot(cross(a1, a2), ed) * iL, dot(a1, a2));
+        const D cb = dconst(m.kbu) * (th - dconst(__ldg(m.th0 + e)));
+        const D c1 = cb * L, c2 = cb * (dot(pa - p1, ed) * iL), c3 = cb * (dot(pb - p1, ed) * iL);
+        st4(ev + 4 * e, sl.v, c1.v, c2.v, c3.v);
+        st4(et + 4 * e, sl.t, c1.t, c2.t, c3.t);
+    }
+    __syncthreads();
+
+    const D ha = {cuv[0], cuv[1]}, sv = {cuv[2], cuv[3]};
+    const R kl = m.k_link, kb = m.k_bend, kA = R(m.k_area), kV = R(m.k_volume);
+    Acc<R> th[4];  // lamFv . unit-modulus forces: link, bend, area, volume
+    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+        const V3<D> pi = dq(xv + 4 * i, xd + 4 * i);
+        const V3<D> z = {dconst(R(0)), dconst(R(0)), dconst(R(0))};
+        V3<D> fl = z, fb = z, fa = z, fv = z;
+        int4 g = __ldg(m.vfan + i);  // slot 0: the last fan entry
+        V3<D> ap = dq(tv + 4 * g.x, td + 4 * g.x);
+        D aw = {tv[4 * g.x + 3], td[4 * g.x + 3]};
+        V3<D> xp = dq(xv + 4 * g.y, xd + 4 * g.y);
+        int op = g.w;
+        for (int k = 1; k <= m.maxv; ++k) {
+            g = __ldg(m.vfan + (size_t)k * m.nv + i);
+            if (g.x < 0) break;
+            const V3<D> ak = dq(tv + 4 * g.x, td + 4 * g.x);
+            const D kw = {tv[4 * g.x + 3], td[4 * g.x + 3]};
+            const V3<D> xk = dq(xv + 4 * g.y, xd + 4 * g.y);
+            const int id = g.z >> 1;
+            const float4 cv = *reinterpret_cast<const float4 *>(ev + 4 * id), ct = *reinterpret_cast<const float4 *>(et + 4 * id);
+            const D cs = {cv.x, ct.x}, cl = {cv.y, ct.y}, ca = {cv.z, ct.z}, cbb = {cv.w, ct.w};
+            const bool r1 = g.z & 1;
+            const V3<D> a1 = r1 ? ap : ak, a2 = r1 ? ak : ap;
+            fl = fl + cs * (xk - pi);
+            fb = r1 ? fb - ((ca + cl) * a1 + (cbb + cl) * a2) : fb + (ca * a1 + cbb * a2);
+            fb = fb + D{ev[4 * op + 1], et[4 * op + 1]} * ap;  // wing term of T_k-1's edge opposite i
+            const V3<D> nh = aw * ap;                          // unit normal of T_k-1
+            fa = fa - ha * cross(nh, xk - xp);
+            fv = fv - sv * cross(xp, xk);
+            ap = ak;
+            aw = kw;
+            xp = xk;
+            op = g.w;
+        }
+        const V3<R> tl = tans(fl), tb = tans(fb), ta = tans(fa), tw = tans(fv);
+        R *o = a.lamX + 3 * (size_t)(first + i);
+        o[0] += kl * tl.x + kb * tb.x + kA * ta.x + kV * tw.x;
+        o[1] += kl * tl.y + kb * tb.y + kA * ta.y + kV * tw.y;
+        o[2] += kl * tl.z + kb * tb.z + kA * ta.z + kV * tw.z;
+        const V3<R> lam = tans(pi);  // lamFv at this vertex
+        th[0].add(dot(lam, vals(fl)));
+        th[1].add(dot(lam, vals(fb)));
+        th[2].add(dot(lam, vals(fa)));
+        th[3].add(dot(lam, vals(fv)));
+    }
+    double TH[4];
+    block_total<R, 4>(th, TH, scratch);
+    if (threadIdx.x < 4) atomicAdd(a.grad + 4 * type + threadIdx.x, TH[threadIdx.x]);
+}
+
 // eigenvector of the symmetric 3x3 matrix g (xx, yy, zz, xy, xz, yz) for
 // the eigenvalue lam: the longest cross product of two rows of g - lam I
 __device__ void sym3_vec(const double *g, double lam, double *e) {
@@ -598,6 +731,14 @@ cudaError_t set_cell_smem_limit(size_t bytes) {
 template <typename R>
 void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st) {
     if (v.ncell == 0) return;
+    if constexpr (std::is_same<R, float>::value) {
+        const size_t gs = cell_adjoint_gather_bytes(v.max_nv, v.max_nt, v.max_ne);
+        if (gs <= CELL_ADJ_GATHER_MAX_SMEM) {
+            if (cell_wide(v)) cell_adjoint_gather_kernel<CellMax<R>::T><<<v.ncell, CellMax<R>::T, gs, st>>>(v, a);
+            else cell_adjoint_gather_kernel<256><<<v.ncell, 256, gs, st>>>(v, a);
+            return;
+        }
+    }
     const size_t smem = cell_adjoint_smem_bytes<R>(v.max_nv, v.max_nt);
     if (cell_wide(v)) cell_adjoint_kernel<R, CellMax<R>::T><<<v.ncell, CellMax<R>::T, smem, st>>>(v, a);
     else cell_adjoint_kernel<R, 256><<<v.ncell, 256, smem, st>>>(v, a);
@@ -608,6 +749,13 @@ cudaError_t set_cell_adjoint_smem_limit(size_t bytes) {
     cudaError_t e = cudaFuncSetAttribute(cell_adjoint_kernel<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess && CellMax<R>::T != 256)
         e = cudaFuncSetAttribute(cell_adjoint_kernel<R, CellMax<R>::T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e;
+}
+
+cudaError_t set_cell_adjoint_gather_smem_limit(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(cell_adjoint_gather_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cell_adjoint_gather_kernel<CellMax<float>::T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return e;
 }
 
