@@ -167,6 +167,14 @@ template <typename R> __device__ __forceinline__ Q4<R> ld4(const R *p) {
     }
 }
 template <typename R> __device__ __forceinline__ V3<R> xyz(Q4<R> q) { return {q.x, q.y, q.z}; }
+template <typename R> __device__ __forceinline__ void st4(R *p, R x, R y, R z, R w) {
+    if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, w);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(x, y);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(z, w);
+    }
+}
 
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<R> v, int mode, double *stats) {
@@ -183,9 +191,24 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     __shared__ R csplit[2][3];  // the new centroid as R hi + lo
     __shared__ R cav[2];        // area and volume coefficients
 
-    // mean offset: any shift works, the centroid takes what the offsets lose
+    // mean offset: any shift works, the centroid takes what the offsets lose.
+    // A thread's first KC vertices stay in registers between the two loops.
+    constexpr int KC = 4;
+    R oc[KC][3];
     R mean[3] = {R(0), R(0), R(0)};
-    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+        const int i = threadIdx.x + kk * (int)blockDim.x;
+        if (i < m.nv) {
+            const R *o = v.off + 3 * (size_t)(first + i);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                oc[kk][k] = o[k];
+                mean[k] += oc[kk][k];
+            }
+        }
+    }
+    for (int i = threadIdx.x + KC * (int)blockDim.x; i < m.nv; i += blockDim.x) {
         const R *o = v.off + 3 * (size_t)(first + i);
         mean[0] += o[0];
         mean[1] += o[1];
@@ -193,18 +216,29 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     }
     block_sum_r<R, 3>(mean, rscratch);
     for (int k = 0; k < 3; ++k) mean[k] /= R(m.nv);
-    for (int i = threadIdx.x; i < m.nv; i += blockDim.x) {
-        R *o = v.off + 3 * (size_t)(first + i);
+    auto rebase = [&](int i, const R *o0) {
+        R r[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const R r = o[k] - mean[k];
-            xs[4 * i + k] = r;
-            if (mode == 0) {
-                o[k] = r;
-                if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r;
+        for (int k = 0; k < 3; ++k) r[k] = o0[k] - mean[k];
+        st4(xs + 4 * i, r[0], r[1], r[2], R(0));
+        if (mode == 0) {
+            R *o = v.off + 3 * (size_t)(first + i);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                o[k] = r[k];
+                if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r[k];
             }
         }
-        xs[4 * i + 3] = R(0);
+    };
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+        const int i = threadIdx.x + kk * (int)blockDim.x;
+        if (i < m.nv) rebase(i, oc[kk]);
+    }
+    for (int i = threadIdx.x + KC * (int)blockDim.x; i < m.nv; i += blockDim.x) {
+        const R *o = v.off + 3 * (size_t)(first + i);
+        const R ol[3] = {o[0], o[1], o[2]};
+        rebase(i, ol);
     }
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; ++k) {
@@ -225,18 +259,22 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
 
     // per triangle: a = n / |n|^2 and |n|, with n = (x1 - x0) x (x2 - x0);
     // area |n|/2 and volume x0 . (x1 x x2) / 6 summed per cell
+    // (the next item's mesh records are loaded before this item is
+    // processed, here and in the edge pass: their L2 latency overlaps the
+    // arithmetic)
     Acc<R> av[2];
-    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
-        const int4 T = __ldg(m.tri4 + t);
-        const V3<R> p0 = xyz(ld4(xs + 4 * T.x)), p1 = xyz(ld4(xs + 4 * T.y)), p2 = xyz(ld4(xs + 4 * T.z));
-        const V3<R> n = cross(p1 - p0, p2 - p0);
-        const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
-        tn[4 * t] = iq * n.x;
-        tn[4 * t + 1] = iq * n.y;
-        tn[4 * t + 2] = iq * n.z;
-        tn[4 * t + 3] = ln;
-        av[0].add(R(0.5) * ln);
-        av[1].add(dot(p0, cross(p1, p2)) / R(6));
+    {
+        int4 Tn = threadIdx.x < m.nt ? __ldg(m.tri4 + threadIdx.x) : make_int4(0, 0, 0, 0);
+        for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+            const int4 T = Tn;
+            if (t + (int)blockDim.x < m.nt) Tn = __ldg(m.tri4 + t + blockDim.x);
+            const V3<R> p0 = xyz(ld4(xs + 4 * T.x)), p1 = xyz(ld4(xs + 4 * T.y)), p2 = xyz(ld4(xs + 4 * T.z));
+            const V3<R> n = cross(p1 - p0, p2 - p0);
+            const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
+            st4(tn + 4 * t, iq * n.x, iq * n.y, iq * n.z, ln);
+            av[0].add(R(0.5) * ln);
+            av[1].add(dot(p0, cross(p1, p2)) / R(6));
+        }
     }
     double AV[2];
     block_total<R, 2>(av, AV, scratch);  // (synchronises: tn is complete below)
@@ -280,11 +318,27 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     // (those of v1 are cb sa0 + cb |e| and cb sb0 + cb |e|, since
     // sa1 - sa0 = sb1 - sb0 = |e|); the edge's triangles are (v0, v1, a)
     // and (v1, v0, b)
-#pragma unroll 2
+    const int4 *edge4 = reinterpret_cast<const int4 *>(m.edge);  // v0, v1, a, b
+    const int2 *etri2 = reinterpret_cast<const int2 *>(m.etri);
+    int4 En = make_int4(0, 0, 0, 0);
+    int2 Tn = make_int2(0, 0);
+    R il0n = R(0), th0n = R(0);
+    if (threadIdx.x < m.ne) {
+        En = __ldg(edge4 + threadIdx.x);
+        Tn = __ldg(etri2 + threadIdx.x);
+        il0n = __ldg(m.invL0 + threadIdx.x);
+        th0n = __ldg(m.th0 + threadIdx.x);
+    }
     for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
-        const int4 E = __ldg(reinterpret_cast<const int4 *>(m.edge) + e);  // v0, v1, a, b
-        const int2 T = __ldg(reinterpret_cast<const int2 *>(m.etri) + e);
-        const R il0 = __ldg(m.invL0 + e), th0 = __ldg(m.th0 + e);
+        const int4 E = En;
+        const int2 T = Tn;
+        const R il0 = il0n, th0 = th0n;
+        if (e + (int)blockDim.x < m.ne) {
+            En = __ldg(edge4 + e + blockDim.x);
+            Tn = __ldg(etri2 + e + blockDim.x);
+            il0n = __ldg(m.invL0 + e + blockDim.x);
+            th0n = __ldg(m.th0 + e + blockDim.x);
+        }
         const V3<R> p0 = xyz(ld4(xs + 4 * E.x)), p1 = xyz(ld4(xs + 4 * E.y));
         const V3<R> pa = xyz(ld4(xs + 4 * E.z)), pb = xyz(ld4(xs + 4 * E.w));
         const V3<R> ed = p1 - p0;
@@ -297,11 +351,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         const V3<R> a1 = xyz(ld4(tn + 4 * T.x)), a2 = xyz(ld4(tn + 4 * T.y));  // n / |n|^2
         const R th = atan2_r(dot(cross(a1, a2), ed) * iL, dot(a1, a2));
         const R cb = m.kb * (th - th0);
-        R *o = es + 4 * e;
-        o[0] = dEdL * iL;
-        o[1] = cb * L;
-        o[2] = cb * (dot(pa - p1, ed) * iL);
-        o[3] = cb * (dot(pb - p1, ed) * iL);
+        st4(es + 4 * e, dEdL * iL, cb * L, cb * (dot(pa - p1, ed) * iL), cb * (dot(pb - p1, ed) * iL));
     }
     __syncthreads();
 
