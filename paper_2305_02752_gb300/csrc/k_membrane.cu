@@ -19,6 +19,7 @@
 // standard one (Bridson et al. 2003): the wing vertices move along their
 // triangle normals with weight |e| / |n|^2, the edge vertices carry the
 // lever-rule remainder.
+#include <algorithm>
 #include <type_traits>
 
 #include "hemo_internal.cuh"
@@ -428,7 +429,10 @@ template <typename R> __device__ __forceinline__ void add_into(R *f, R s, V3<R> 
     atomicAdd(f + 2, s * a.z);
 }
 
-// Adjoint of the membrane forces of one cell (one CTA per cell), at the
+// Adjoint of the membrane forces of one cell (`slices` CTAs per cell: each
+// computes the cell's triangle records, area and volume, then its share of
+// the edge and triangle terms, and adds its part of the product to lamX,
+// atomically when a cell has several CTAs), at the
 // positions X_n left by the forward recomputation (cell_kernel mode 0):
 //   lamX += (dF/dX) lamFv  -- F = -grad E, so dF/dX = -Hessian is symmetric
 //                            and its product with lamFv is the derivative
@@ -436,9 +440,9 @@ template <typename R> __device__ __forceinline__ void add_into(R *f, R s, V3<R> 
 //   grad[4 type + k] += lamFv . F_k / modulus_k for the four terms (each is
 //                            linear in its modulus).
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kernel(View<R> v, AdjView<R> a) {
+__global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kernel(View<R> v, AdjView<R> a, int slices) {
     using D = Dual<R>;
-    const int c = blockIdx.x;
+    const int c = blockIdx.x / slices, slice = blockIdx.x % slices;
     const int type = v.cell_type[c];
     const MeshDev<R> m = v.meshes[type];
     const int first = v.cell_first[c];
@@ -488,7 +492,8 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
     const R kA = R(m.k_area), kV = R(m.k_volume);
 
     Acc<R> th[4];  // lamFv . unit-modulus forces: link, bend, area, volume
-    for (int e = threadIdx.x; e < m.ne; e += blockDim.x) {
+    const int step = slices * (int)blockDim.x;  // this CTA's share of the edge and triangle terms
+    for (int e = slice * (int)blockDim.x + threadIdx.x; e < m.ne; e += step) {
         const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
         const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
         const V3<D> p0 = dld3(xs + 3 * i0, xt + 3 * i0), p1 = dld3(xs + 3 * i1, xt + 3 * i1);
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
         add_into(ft + 3 * i1, m.k_bend, tans(f1));
         th[1].add(dot(la, vals(fa)) + dot(lb, vals(fb)) + dot(l0, vals(f0)) + dot(l1, vals(f1)));
     }
-    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+    for (int t = slice * (int)blockDim.x + threadIdx.x; t < m.nt; t += step) {
         const int j[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
         const V3<D> p[3] = {dld3(xs + 3 * j[0], xt + 3 * j[0]), dld3(xs + 3 * j[1], xt + 3 * j[1]),
                             dld3(xs + 3 * j[2], xt + 3 * j[2])};
@@ -542,7 +547,10 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
     block_total<R, 4>(th, TH, scratch);
     if (threadIdx.x < 4) atomicAdd(a.grad + 4 * type + threadIdx.x, TH[threadIdx.x]);
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) a.lamX[3 * (size_t)first + i] += ft[i];
+    if (slices == 1)
+        for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) a.lamX[3 * (size_t)first + i] += ft[i];
+    else
+        for (int i = threadIdx.x; i < 3 * m.nv; i += blockDim.x) atomicAdd(a.lamX + 3 * (size_t)first + i, ft[i]);
 }
 
 // FP32 form of the membrane adjoint as a gather, in the forward kernel's
@@ -790,8 +798,11 @@ void launch_cell_adjoint(const View<R> &v, const AdjView<R> &a, cudaStream_t st)
         }
     }
     const size_t smem = cell_adjoint_smem_bytes<R>(v.max_nv, v.max_nt);
-    if (cell_wide(v)) cell_adjoint_kernel<R, CellMax<R>::T><<<v.ncell, CellMax<R>::T, smem, st>>>(v, a);
-    else cell_adjoint_kernel<R, 256><<<v.ncell, 256, smem, st>>>(v, a);
+    // few cells: spread each over several CTAs (FP64 arithmetic is slow per
+    // SM, so the work goes to as many SMs as there are)
+    const int slices = std::max(1, std::min(32, v.nsm / v.ncell));
+    if (slices == 1 && cell_wide(v)) cell_adjoint_kernel<R, CellMax<R>::T><<<v.ncell, CellMax<R>::T, smem, st>>>(v, a, 1);
+    else cell_adjoint_kernel<R, 256><<<v.ncell * slices, 256, smem, st>>>(v, a, slices);
 }
 
 template <typename R>
