@@ -174,6 +174,12 @@ __device__ __forceinline__ void peskin4(R t, R *w) {
     w[3] = (R(1) + R(2) * t - q) * R(0.125);
 }
 
+// FP64 vertex kernels: CTAs per bin, each taking every FP64_BIN_PARTS-th
+// chunk of the bin's vertices (FP64 arithmetic is slow per SM, and a bin
+// crowded with vertices would otherwise keep one SM busy long after the
+// others are done)
+constexpr int FP64_BIN_PARTS = 8;
+
 // distinct neighbour block coordinates along one axis
 __device__ __forceinline__ int neighbour_blocks(int b, int nb, int periodic, int out[3]) {
     int cnt = 0;
@@ -507,12 +513,12 @@ __global__ void __launch_bounds__(256) hold_bins_kernel(View<R> v) {
 // vertices, each half-warp's lanes own one (y, z) stencil row, and the 16
 // partial sums are reduced with warp shuffles.
 template <typename R, int INTEG>
-__global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
+__global__ void __launch_bounds__(256) interpolate_kernel(View<R> v, int parts) {
     drop_dead_lines(v);
     constexpr int CAP = Stage<R>::CAP;
-    const int k = blockIdx.x;
+    const int k = blockIdx.x / parts, part = blockIdx.x % parts;  // CTA part takes chunks part, part + parts, ...
     const int s = v.start[k], e = v.start[k + 1];
-    if (s == e) return;
+    if (s + part * CAP >= e) return;
     __shared__ R tile[3][TILE_SMEM];
     __shared__ int srow[CAP], sperm[CAP];
     __shared__ R sw[12 * CAP];
@@ -544,9 +550,9 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v) {
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
-    for (int c0 = s; c0 < e; c0 += CAP) {
+    for (int c0 = s + part * CAP; c0 < e; c0 += parts * CAP) {
         const int n = min(CAP, e - c0);
-        if (c0 != s) __syncthreads();
+        __syncthreads();  // the tile (first chunk) or the previous chunk's records
         stage_chunk(v, c0, n, org, srow, sw, (R *)nullptr, sperm);
         __syncthreads();
         for (int q0 = 2 * warp; q0 < n; q0 += 2 * nw) {  // uniform per warp: shuffles below
@@ -672,11 +678,11 @@ __device__ __forceinline__ void peskin4_d(R t, R *w, R *dw) {
 template <typename R> struct VfStage { static constexpr int CAP = sizeof(R) == 8 ? 16 : 128; };
 template <typename R>
 __global__ void __launch_bounds__(256) vertex_field_kernel(View<R> v, const R *A, const R *B, R *out_grad,
-                                                           R *out_interp) {
+                                                           R *out_interp, int parts) {
     constexpr int CAP = VfStage<R>::CAP;
-    const int k = blockIdx.x;
+    const int k = blockIdx.x / parts, part = blockIdx.x % parts;  // CTA part takes chunks part, part + parts, ...
     const int s = v.start[k], e = v.start[k + 1];
-    if (s == e) return;
+    if (s + part * CAP >= e) return;
     __shared__ R tile[3][TILE_SMEM];
     __shared__ int srow[CAP], sperm[CAP];
     __shared__ R sw[24 * CAP], sB[3 * CAP];
@@ -708,9 +714,9 @@ __global__ void __launch_bounds__(256) vertex_field_kernel(View<R> v, const R *A
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
-    for (int c0 = s; c0 < e; c0 += CAP) {
+    for (int c0 = s + part * CAP; c0 < e; c0 += parts * CAP) {
         const int n = min(CAP, e - c0);
-        if (c0 != s) __syncthreads();
+        __syncthreads();  // the tile (first chunk) or the previous chunk's records
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const int i = v.perm[c0 + j];
             int row = 0;
@@ -896,7 +902,7 @@ void launch_spread(const View<R> &v, cudaStream_t st) {
 template <typename R, int INTEG>
 void launch_interpolate_as(const View<R> &v, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value) interpolate_v4_kernel<INTEG><<<v.nbins, 256, 0, st>>>(v);
-    else interpolate_kernel<R, INTEG><<<v.nbins, 256, 0, st>>>(v);
+    else interpolate_kernel<R, INTEG><<<v.nbins * FP64_BIN_PARTS, 256, 0, st>>>(v, FP64_BIN_PARTS);
 }
 
 template <typename R>
@@ -916,7 +922,7 @@ void launch_vertex_field(const View<R> &v, const R *field, const R *vec, R *out_
     if constexpr (std::is_same<R, float>::value)
         vertex_field_v4_kernel<<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
     else
-        vertex_field_kernel<R><<<v.nbins, 256, 0, st>>>(v, field, vec, out_grad, out_interp);
+        vertex_field_kernel<R><<<v.nbins * FP64_BIN_PARTS, 256, 0, st>>>(v, field, vec, out_grad, out_interp, FP64_BIN_PARTS);
 }
 
 template <typename R>
