@@ -40,6 +40,29 @@ constexpr int TILE3 = TILE * TILE * TILE;
 constexpr int TS_Y = 12, TS_Z = 161;
 constexpr int TILE_SMEM = TS_Z * TILE;
 
+// A thread's walk over the positions q = l0 + TILE (l1 + TILE l2) of an
+// 11^3 tile with a stride of blockDim.x: the coordinates advance by the
+// stride's digits with carries, without integer division per position.
+struct TileWalk {
+    int l0, l1, l2, s0, s1, s2;
+    __device__ __forceinline__ TileWalk(int q, int stride)
+        : l0(q % TILE), l1((q / TILE) % TILE), l2(q / (TILE * TILE)), s0(stride % TILE), s1((stride / TILE) % TILE),
+          s2(stride / (TILE * TILE)) {}
+    __device__ __forceinline__ void next() {
+        l0 += s0;
+        if (l0 >= TILE) {
+            l0 -= TILE;
+            ++l1;
+        }
+        l1 += s1;
+        if (l1 >= TILE) {
+            l1 -= TILE;
+            ++l2;
+        }
+        l2 += s2;
+    }
+};
+
 // origin of bin k
 template <typename R>
 __device__ __forceinline__ void bin_origin(const View<R> &v, int k, int org[3]) {
@@ -163,6 +186,22 @@ __global__ void __launch_bounds__(128) sort_bins_kernel(const int *start, const 
     }
 }
 
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void ld4v(const float *p, float *o) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    o[0] = q.x;
+    o[1] = q.y;
+    o[2] = q.z;
+    o[3] = q.w;
+}
+__device__ __forceinline__ void ld4v(const double *p, double *o) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
 // Peskin 4-point weights of nodes floor(X) - 1 .. floor(X) + 2 for the
 // fraction t = X - floor(X) in [0, 1); one square root serves all four.
 template <typename R>
@@ -198,13 +237,14 @@ __device__ __forceinline__ int neighbour_blocks(int b, int nb, int periodic, int
 // per vertex reads its anchor through the permutation, computes its row in
 // the bin's padded tile (-1 if the anchor is outside the bin, i.e. the
 // vertex left the lattice) and its twelve Peskin weights (x0..3, y0..3,
-// z0..3), and optionally its force.  The per-vertex loops below then touch
+// z0..3), and optionally its force (four entries per vertex, times fscale
+// per component if given).  The per-vertex loops below then touch
 // shared memory only.  Chunk size by precision keeps the FP64 kernels within
 // 48 KB of static shared memory.
-template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 256; };
+template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 192; };
 template <typename R>
 __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, const int org[3], int *srow, R *sw,
-                                            R *sF, int *sperm) {
+                                            R *sF, int *sperm, const float *fscale = nullptr) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int i = v.perm[p0 + j];
         int row = 0;
@@ -214,7 +254,7 @@ __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, con
             ok &= b >= 0 && b < BLK;
             row += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
             peskin4(v.anc_t[3 * (size_t)i + d], sw + 12 * j + 4 * d);
-            if (sF) sF[3 * j + d] = v.Fv[3 * (size_t)i + d];
+            if (sF) sF[4 * j + d] = fscale ? v.Fv[3 * (size_t)i + d] * (R)fscale[d] : v.Fv[3 * (size_t)i + d];
         }
         srow[j] = ok ? row : -1;
         if (sperm) sperm[j] = i;
@@ -242,7 +282,7 @@ template <> struct TileAcc<float> {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(256) spread_tile_kernel(View<R> v) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kernel(View<R> v) {
     using A = typename TileAcc<R>::T;
     constexpr bool FIXED = std::is_same<A, int>::value;
     constexpr int CAP = Stage<R>::CAP;
@@ -251,7 +291,8 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(View<R> v) {
     if (s == e) return;
     __shared__ A acc[3][TILE_SMEM];
     __shared__ int srow[CAP];
-    __shared__ R sw[12 * CAP], sF[3 * CAP];
+    __shared__ __align__(16) R sw[12 * CAP];
+    __shared__ __align__(16) R sF[4 * CAP];
     __shared__ float smax[3][8];
     __shared__ float scale[3];
     for (int q = threadIdx.x; q < TILE_SMEM; q += blockDim.x) acc[0][q] = acc[1][q] = acc[2][q] = A(0);
@@ -281,24 +322,26 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(View<R> v) {
                 scale[threadIdx.x] = bound > 0.f ? ldexpf(1.f, min(29 - ilogbf(bound), 120)) : 0.f;
             }
         }
+        __syncthreads();  // the staging below applies the scale
     }
     for (int p0 = s; p0 < e; p0 += CAP) {
         const int n = min(CAP, e - p0);
         if (p0 != s) __syncthreads();
-        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr);
+        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr, FIXED ? scale : nullptr);
         __syncthreads();
         for (int q = 2 * warp + h; q < n; q += 2 * nw) {
             const int row0 = srow[q];
             if (row0 < 0) continue;  // vertex outside the lattice (domain status already raised)
             const R *w = sw + 12 * q;
             const R wyz = w[4 + b] * w[8 + c];
-            R f[3] = {sF[3 * q] * wyz, sF[3 * q + 1] * wyz, sF[3 * q + 2] * wyz};
-            if (FIXED)
-                for (int d = 0; d < 3; ++d) f[d] *= (R)scale[d];
+            R wx[4], fq[4];
+            ld4v(w, wx);
+            ld4v(sF + 4 * q, fq);  // (times the fixed-point scale)
+            const R f[3] = {fq[0] * wyz, fq[1] * wyz, fq[2] * wyz};
             const int row = row0 + TS_Y * b + TS_Z * c;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const R wa = w[a];
+                const R wa = wx[a];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     if (FIXED) atomicAdd((int *)&acc[d][row + a], __float2int_rn((float)(f[d] * wa)));
@@ -312,8 +355,9 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(View<R> v) {
     float inv[3] = {1.f, 1.f, 1.f};
     if (FIXED)
         for (int d = 0; d < 3; ++d) inv[d] = scale[d] > 0.f ? 1.f / scale[d] : 0.f;
-    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
-        const int sidx = q % TILE + TS_Y * ((q / TILE) % TILE) + TS_Z * (q / (TILE * TILE));
+    TileWalk tw(threadIdx.x, blockDim.x);
+    for (int q = threadIdx.x; q < TILE3; q += blockDim.x, tw.next()) {
+        const int sidx = tw.l0 + TS_Y * tw.l1 + TS_Z * tw.l2;
         for (int d = 0; d < 3; ++d) out[d * TILE3 + q] = FIXED ? (R)((float)acc[d][sidx] * inv[d]) : (R)acc[d][sidx];
     }
 }
