@@ -78,12 +78,12 @@ typedef struct {
     unsigned options;            /* bit mask of HEMO_OPT_*; 0 = defaults           */
 } hemo_lattice_desc;
 
-/* HEMO_OPT_NO_STAGING: collide every node with the per-node kernel instead of
- * staging tiles of wall-free rows through shared memory by bulk copies on odd
- * steps (whose reads and writes are shifted by one node in x); staging is
- * used with 16-bit storage only.  The results are the same; the option
- * exists for comparison and measurement. */
-enum { HEMO_OPT_NO_STAGING = 1u };
+/* HEMO_OPT_STAGED_COLLISION: on odd steps (whose reads and writes are
+ * shifted by one node in x), stage tiles of wall-free rows through shared
+ * memory by bulk copies instead of colliding every node with the per-node
+ * kernel; 16-bit storage only (ignored otherwise).  The results are the
+ * same.  Off by default: the per-node kernel is the faster of the two. */
+enum { HEMO_OPT_STAGED_COLLISION = 1u };
 
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
  * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
@@ -181,7 +181,7 @@ int hemo_get_sizes(const hemo_sim *sim, long long *n_nodes, long long *n_vertice
 
 /* ---- inspection of integer work and raw state (tests, tools) ----------- */
 
-/* How the collision is split (see HEMO_OPT_NO_STAGING): plan[0] tiles of
+/* How the collision is split (see HEMO_OPT_STAGED_COLLISION): plan[0] tiles of
  * wall-free rows staged through shared memory, plan[1] other rows with fluid
  * (per-node kernel), plan[2] rows per tile at most, plan[3] ring stages.
  * All zero when every node goes through the per-node kernel.  plan: host, 4

@@ -918,15 +918,15 @@ int hemo_velocity_set(int32_t *c, double *w) {
 // within a z-plane are cut into tiles of at most tile_rows rows; the rows
 // that are not interior but hold fluid go to the per-node kernel.  Staging
 // needs 16-byte aligned rows (bulk copies) and at least two stages of the
-// ring in shared memory.  It is used for 2-byte storage only: with 4-byte
-// populations the per-node kernel keeps enough bytes in flight by itself and
-// is as fast, and FP64's collision is arithmetic-bound on this GPU.
+// ring in shared memory.  It is used on request (HEMO_OPT_STAGED_COLLISION)
+// for 2-byte storage only: the per-node kernel on its (x, y, z) grid with
+// 32-bit indices is faster for every storage type.
 constexpr size_t TILE_RING_BYTES = 54 * 1024;
 
 int plan_rows(hemo_sim *s, const uint8_t *mask) {
     const int nx = s->nx, ny = s->ny, nz = s->nz;
     const size_t S = tsize(s), Rb = rsize(s);
-    if (S != 2 || (s->options & HEMO_OPT_NO_STAGING) || !s->per[0]) return HEMO_OK;
+    if (S != 2 || !(s->options & HEMO_OPT_STAGED_COLLISION) || !s->per[0]) return HEMO_OK;
     if (((size_t)nx * S) % 16 || ((size_t)nx * Rb) % 16) return HEMO_OK;
     // whole rows of at most 256 nodes per tile (one per thread; the stage
     // layout has room for 256), at most 54 KiB of ring per CTA so that four

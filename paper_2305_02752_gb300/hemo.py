@@ -32,7 +32,7 @@ class hemo_lattice_desc(C.Structure):
                 ('cuda_stream', C.c_void_p), ('alloc', ALLOC_FN), ('release', FREE_FN),
                 ('alloc_ctx', C.c_void_p), ('options', C.c_uint)]
 
-HEMO_OPT_NO_STAGING = 1
+HEMO_OPT_STAGED_COLLISION = 1
 HEMO_EULER, HEMO_AB2 = 0, 1
 INTEGRATORS = {'euler': HEMO_EULER, 'ab2': HEMO_AB2}
 

@@ -1,5 +1,6 @@
 """The staged collision (tiles of wall-free rows copied through shared
-memory by bulk copies) against the per-node kernel on the same inputs:
+memory by bulk copies; HEMO_OPT_STAGED_COLLISION) against the per-node
+kernel (the default) on the same inputs:
 identical populations, density and velocity after an odd number of steps
 (both step parities), for the storage types that use it (16-bit), on
 lattices with walls on one axis, with periodic wrap of the shifted rows in
@@ -66,8 +67,8 @@ def run(cfg, prec, steps, options):
 @pytest.mark.parametrize('case', sorted(CASES))
 def test_staged_matches_per_node(case, prec):
     cfg = CASES[case]()
-    plan, a = run(cfg, prec, 7, 0)
-    plan0, b = run(cfg, prec, 7, hemo.HEMO_OPT_NO_STAGING)
+    plan, a = run(cfg, prec, 7, hemo.HEMO_OPT_STAGED_COLLISION)
+    plan0, b = run(cfg, prec, 7, 0)
     assert plan[0] > 0 and plan0 == (0, 0, 0, 0)
     if case == 'box':
         assert plan[1] == 0
@@ -80,8 +81,8 @@ def test_staged_with_cells_matches_per_node():
     spreading is fixed-point, so the coupled step is reproducible and the
     two collision paths agree bit for bit."""
     cfg = small_cell_shear(n=24, steps=9, seed=5)
-    _, a = run(cfg, 'f16', 9, 0)
-    _, b = run(cfg, 'f16', 9, hemo.HEMO_OPT_NO_STAGING)
+    _, a = run(cfg, 'f16', 9, hemo.HEMO_OPT_STAGED_COLLISION)
+    _, b = run(cfg, 'f16', 9, 0)
     for k in ('f', 'u', 'X'):
         assert np.array_equal(a[k], b[k]), k
 
@@ -94,19 +95,22 @@ def test_channel_plan():
     three FP32 force components)."""
     cfg = _no_cells(I.channel(ncell=0, pack_iter=1))
     for prec in ('f16', 'bf16'):
-        sim = hemo.Simulation.from_config(cfg, prec)
+        sim = hemo.Simulation.from_config(cfg, prec, options=hemo.HEMO_OPT_STAGED_COLLISION)
         plan = sim.lattice_plan()
         sim.close()
         assert plan == (15 * 256, 2 * 256, 4, 4)
+        sim = hemo.Simulation.from_config(cfg, prec)  # default: per-node kernel only
+        assert sim.lattice_plan() == (0, 0, 0, 0)
+        sim.close()
 
 
 def test_no_staging_for_4_and_8_byte_storage_or_unaligned_rows():
     cfg = _no_cells(I.channel(nx=64, ny=20, nz=8, ncell=0, pack_iter=1))
     for prec in ('f64', 'f32'):
-        sim = hemo.Simulation.from_config(cfg, prec)
+        sim = hemo.Simulation.from_config(cfg, prec, options=hemo.HEMO_OPT_STAGED_COLLISION)
         assert sim.lattice_plan() == (0, 0, 0, 0)
         sim.close()
     cfg = _no_cells(I.channel(nx=60, ny=20, nz=8, ncell=0, pack_iter=1))  # 60 * 2 B is not a multiple of 16
-    sim = hemo.Simulation.from_config(cfg, 'f16')
+    sim = hemo.Simulation.from_config(cfg, 'f16', options=hemo.HEMO_OPT_STAGED_COLLISION)
     assert sim.lattice_plan() == (0, 0, 0, 0)
     sim.close()
