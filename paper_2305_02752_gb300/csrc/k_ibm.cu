@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v, int parts) 
 // one 16-byte shared load; the weights stay in registers and each thread
 // sums its vertex's 64 terms itself (no staging of weights, no shuffles).
 template <int INTEG>
-__global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
+__global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
     drop_dead_lines(v);
     const int k = blockIdx.x;
     const int s = v.start[k], e = v.start[k + 1];
@@ -640,6 +640,19 @@ __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
     __shared__ int jtab[3][TILE];  // wrapped lattice coordinate, -1 beyond a non-periodic edge
     int org[3];
     bin_origin(v, k, org);
+    // this thread's first vertex: its records are requested before the tile
+    // is staged, so their latency overlaps the staging
+    const int jf = s + threadIdx.x;
+    int ifst = -1, aif[3] = {0, 0, 0};
+    float atf[3] = {0.f, 0.f, 0.f};
+    if (jf < e) {
+        ifst = v.perm[jf];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            aif[d] = v.anc_i[3 * (size_t)ifst + d];
+            atf[d] = v.anc_t[3 * (size_t)ifst + d];
+        }
+    }
     if (threadIdx.x < 3 * TILE) {
         const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
         const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
@@ -663,17 +676,34 @@ __global__ void __launch_bounds__(256) interpolate_v4_kernel(View<float> v) {
         tile[l0 + TS_Y * l1 + TS_Z * l2] = t;
     }
     __syncthreads();
-    for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
-        const int i = v.perm[j];
+    for (int j = jf; j < e; j += blockDim.x) {
+        int i;
+        int ai[3];
+        float at[3];
+        if (j == jf) {
+            i = ifst;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ai[d] = aif[d];
+                at[d] = atf[d];
+            }
+        } else {
+            i = v.perm[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ai[d] = v.anc_i[3 * (size_t)i + d];
+                at[d] = v.anc_t[3 * (size_t)i + d];
+            }
+        }
         float w[3][4];
         int r0 = 0;
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int b = v.anc_i[3 * (size_t)i + d] - org[d];
+            const int b = ai[d] - org[d];
             ok &= b >= 0 && b < BLK;
             r0 += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
-            peskin4(v.anc_t[3 * (size_t)i + d], w[d]);
+            peskin4(at[d], w[d]);
         }
         if (!ok) continue;
         float U0 = 0.f, U1 = 0.f, U2 = 0.f;
