@@ -133,8 +133,16 @@ def build_edges(nv, tri):
 
 
 def membrane_params(mt):
+    """[k_link, k_bend, k_area, k_volume, kbt, persistence, max_strain,
+    k_local, theta_m] of a mesh type (the last two 0 unless set)."""
     return np.array([mt.k_link, mt.k_bend, mt.k_area, mt.k_volume, mt.kbt, mt.persistence,
-                     mt.max_strain], float)
+                     mt.max_strain, getattr(mt, 'k_local', 0.0), getattr(mt, 'theta_m', 0.0)], float)
+
+
+def _params9(params):
+    p = np.zeros(9)
+    p[:len(params)] = params
+    return p
 
 
 def membrane(rest, tri, params, X):
@@ -144,7 +152,7 @@ def membrane(rest, tri, params, X):
     F = np.zeros(rest.size)
     E = np.zeros(4)
     AV = np.zeros(4)
-    rc = lib().ora_membrane(len(rest), len(tri), tri.ravel(), rest.ravel(), _c(params),
+    rc = lib().ora_membrane(len(rest), len(tri), tri.ravel(), rest.ravel(), _params9(params),
                             _c(X).ravel(), F, E, AV)
     if rc != 0:
         raise ValueError('bad mesh')
@@ -185,7 +193,7 @@ class OracleSim:
 
     def add_mesh(self, rest, tri, params):
         t = lib().ora_add_mesh(self.h, len(rest), len(tri), _c(tri, np.int32).ravel(),
-                               _c(rest).ravel(), _c(params))
+                               _c(rest).ravel(), _params9(params))
         if t < 0:
             raise ValueError('bad mesh')
         self._rest.append(_c(rest))

@@ -49,6 +49,15 @@
  *     X^{n+1} = X^n + 3/2 U^n - 1/2 U^{n-1} with dt = 1, U^n the velocity
  *     interpolated at X^n; the first step after the setting is made (no
  *     U^{n-1} yet) is an Euler step;
+ *   - nonlinear bending and local area (Sec. 2.3: large deformations give a
+ *     highly non-linear response of membrane and cytoskeleton; both terms are
+ *     off unless their parameter is set): with a maximum bending deviation
+ *     theta_m > 0 the bending energy per edge is k_bend kBT theta_m^2 *
+ *     (-1/2) ln(1 - (theta - theta0)^2 / theta_m^2), which is the harmonic
+ *     1/2 k_bend kBT (theta - theta0)^2 for small deviations and stiffens
+ *     without bound as |theta - theta0| approaches theta_m; with k_local > 0
+ *     each triangle adds 1/2 k_local (A_t - A_t0)^2 / A_t0 (A_t0 its rest
+ *     area; lattice energy per lattice area);
  *   - area / volume: per cell, in strain form 1/2 k_area ((A - A0)/A0)^2 and
  *     1/2 k_volume ((V - V0)/V0)^2 with k in lattice energy units.  (The form
  *     1/2 k (V - V0)^2 / V0 with k_volume = 20 makes the explicit coupling
@@ -139,8 +148,10 @@ typedef struct {
     int *edge;      /* ne*4: v0, v1, a, b; triangle (v0,v1,a) and (v1,v0,b) */
     double *L0;     /* rest length per edge */
     double *th0;    /* rest dihedral angle per edge */
+    double *At0;    /* rest area per triangle */
     double A0, V0;
     double k_link, k_bend, k_area, k_volume, kbt, persistence, max_strain;
+    double k_local, theta_m; /* local area modulus; maximum bending deviation (0: harmonic) */
 } omesh;
 
 /* Edge table: triangles in order, their directed edges (t0,t1), (t1,t2),
@@ -234,18 +245,28 @@ static int mesh_init(omesh *m, int nv, int nt, const int *tri, const double *res
         m->th0[e] = dihedral(rest + 3 * E[0], rest + 3 * E[1], rest + 3 * E[2], rest + 3 * E[3]);
     }
     cell_area_volume(m, rest, &m->A0, &m->V0);
+    m->At0 = (double *)malloc(sizeof(double) * nt);
+    for (int t = 0; t < nt; ++t) {
+        double e1[3], e2[3], n[3];
+        sub3(rest + 3 * tri[3 * t + 1], rest + 3 * tri[3 * t], e1);
+        sub3(rest + 3 * tri[3 * t + 2], rest + 3 * tri[3 * t], e2);
+        cross3(e1, e2, n);
+        m->At0[t] = 0.5 * sqrt(dot3(n, n));
+    }
     m->k_link = params[0]; m->k_bend = params[1]; m->k_area = params[2]; m->k_volume = params[3];
     m->kbt = params[4]; m->persistence = params[5]; m->max_strain = params[6];
+    m->k_local = params[7]; m->theta_m = params[8];
     return 0;
 }
 
 static void mesh_free(omesh *m) {
-    free(m->tri); free(m->edge); free(m->L0); free(m->th0);
+    free(m->tri); free(m->edge); free(m->L0); free(m->th0); free(m->At0);
 }
 
 /* Sec. 2.3: F_v = -dE/dX_v with E = E_link + E_bend + E_area + E_volume.
- * Adds forces into F (nv*3); returns the four energies in E4 (may be NULL);
- * writes the cell's area and volume. */
+ * Adds forces into F (nv*3); returns the four energies in E4 (may be NULL;
+ * the local area energy is counted with the area term); writes the cell's
+ * area and volume. */
 static void membrane_forces(const omesh *m, const double *X, double *F, double *E4, double *Aout, double *Vout) {
     double El = 0, Eb = 0, Ea = 0, Ev = 0;
     /* link: per edge */
@@ -271,7 +292,15 @@ static void membrane_forces(const omesh *m, const double *X, double *F, double *
         const double *p0 = X + 3 * E[0], *p1 = X + 3 * E[1], *pa = X + 3 * E[2], *pb = X + 3 * E[3];
         double th = dihedral(p0, p1, pa, pb);
         double dth = th - m->th0[e];
-        Eb += 0.5 * kb * dth * dth;
+        double c;  /* dE/dtheta */
+        if (m->theta_m > 0) {
+            double r2 = dth * dth / (m->theta_m * m->theta_m);
+            Eb += -0.5 * kb * m->theta_m * m->theta_m * log(1.0 - r2);
+            c = kb * dth / (1.0 - r2);
+        } else {
+            Eb += 0.5 * kb * dth * dth;
+            c = kb * dth;
+        }
         double ed[3], da[3], db[3], n1[3], n2[3], t1[3], t0[3], ta[3], tb[3];
         sub3(p1, p0, ed); sub3(pa, p0, da); sub3(pb, p0, db);
         cross3(ed, da, n1);
@@ -288,7 +317,6 @@ static void membrane_forces(const omesh *m, const double *X, double *F, double *
             t0[k] = -sa0 * n1[k] / q1 - sb0 * n2[k] / q2;
             t1[k] = sa1 * n1[k] / q1 + sb1 * n2[k] / q2;
         }
-        double c = kb * dth;
         for (int k = 0; k < 3; ++k) {
             F[3 * E[0] + k] -= c * t0[k];
             F[3 * E[1] + k] -= c * t1[k];
@@ -313,6 +341,13 @@ static void membrane_forces(const omesh *m, const double *X, double *F, double *
         sub3(x1, x0, e1); sub3(x2, x0, e2); cross3(e1, e2, n);
         double nn = sqrt(dot3(n, n));
         double nh[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+        /* dE/dA_t of the global (per cell) and the local (per triangle) area terms */
+        double ct = ca;
+        if (m->k_local > 0) {
+            double At = 0.5 * nn;
+            Ea += 0.5 * m->k_local * (At - m->At0[t]) * (At - m->At0[t]) / m->At0[t];
+            ct += m->k_local * (At - m->At0[t]) / m->At0[t];
+        }
         double d21[3], d02[3], d10[3], g0[3], g1[3], g2[3];
         sub3(x2, x1, d21); sub3(x0, x2, d02); sub3(x1, x0, d10);
         cross3(nh, d21, g0); cross3(nh, d02, g1); cross3(nh, d10, g2);
@@ -320,9 +355,9 @@ static void membrane_forces(const omesh *m, const double *X, double *F, double *
         sub3(x0, ctr, r0); sub3(x1, ctr, r1); sub3(x2, ctr, r2);
         cross3(r1, r2, v0); cross3(r2, r0, v1); cross3(r0, r1, v2);
         for (int k = 0; k < 3; ++k) {
-            F[3 * i0 + k] -= ca * 0.5 * g0[k] + cv * v0[k] / 6.0;
-            F[3 * i1 + k] -= ca * 0.5 * g1[k] + cv * v1[k] / 6.0;
-            F[3 * i2 + k] -= ca * 0.5 * g2[k] + cv * v2[k] / 6.0;
+            F[3 * i0 + k] -= ct * 0.5 * g0[k] + cv * v0[k] / 6.0;
+            F[3 * i1 + k] -= ct * 0.5 * g1[k] + cv * v1[k] / 6.0;
+            F[3 * i2 + k] -= ct * 0.5 * g2[k] + cv * v2[k] / 6.0;
         }
     }
     if (E4) { E4[0] = El; E4[1] = Eb; E4[2] = Ea; E4[3] = Ev; }

@@ -327,6 +327,8 @@ class MeshType:
     kbt: float
     persistence: float        # LU
     max_strain: float
+    k_local: float = 0.0      # local (per-triangle) area modulus, lattice energy per lattice area; 0 = off
+    theta_m: float = 0.0      # maximum bending deviation of the nonlinear bending term (rad); 0 = harmonic
 
 
 @dataclasses.dataclass
