@@ -94,7 +94,15 @@ enum { HEMO_OPT_STAGED_COLLISION = 1u };
  *                    angle between the outward normals of the edge's triangles
  *   area   per cell  1/2 k_area ((A - A0) / A0)^2
  *   volume per cell  1/2 k_volume ((V - V0) / V0)^2
- * with L0, theta0, A0, V0 taken from rest_xyz. */
+ * with L0, theta0, A0, V0 taken from rest_xyz.  Two optional terms for large
+ * deformations (Sec. 2.3: the response is highly non-linear; the paper
+ * prints no formula, these are this library's forms), off when 0:
+ *   nonlinear bending (theta_m > 0) replaces the bending term by
+ *                    k_bend kbt theta_m^2 (-1/2) ln(1 - (theta - theta0)^2 /
+ *                    theta_m^2): harmonic for small deviations, stiffening
+ *                    without bound as |theta - theta0| approaches theta_m
+ *   local area       per triangle 1/2 k_local (A_t - A_t0)^2 / A_t0
+ * The differentiation form (hemo_record) supports the four-term model only. */
 typedef struct {
     int nv, nt;                  /* vertices and triangles; closed, oriented      */
     const int32_t *tri;          /* host, nt*3, counter-clockwise seen from outside */
@@ -104,6 +112,9 @@ typedef struct {
     double kbt;                  /* k_B T in lattice energy units                 */
     double persistence;          /* spectrin persistence length p (lattice units) */
     double max_strain;           /* link strain at which the energy diverges      */
+    double k_local;              /* local area modulus, lattice energy per lattice
+                                    area; 0 = off                                 */
+    double theta_m;              /* maximum bending deviation (rad); 0 = harmonic */
 } hemo_mesh_desc;
 
 /* Create a simulation: allocates the lattice, sets every fluid node to rest
@@ -226,8 +237,9 @@ int hemo_get_bins(hemo_sim *sim, int32_t *key, int32_t *perm, int32_t *start);
  * (even, >= 2), and take the current cell centroids as the reference of the
  * loss's drift term.  The current step count must be even.  Checkpoints are
  * device memory owned by the library: (steps / checkpoint_every + 1) copies
- * of the state.  Needs the default time scales (forces every step, Euler):
- * HEMO_ERR_STATE otherwise. */
+ * of the state.  Needs the default time scales (forces every step, Euler)
+ * and the four-term membrane model (k_local = theta_m = 0 for every mesh
+ * type): HEMO_ERR_STATE otherwise. */
 int hemo_record(hemo_sim *sim, int checkpoint_every);
 
 /* Deformation loss of the current vertices (its own definition; the paper

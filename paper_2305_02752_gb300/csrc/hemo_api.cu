@@ -33,9 +33,10 @@ int fail(int code, const std::string &msg) {
 struct HostMesh {
     int nv = 0, nt = 0, ne = 0;
     std::vector<int> tri, edge;
-    std::vector<double> L0, th0;
+    std::vector<double> L0, th0, At0;
     double A0 = 0, V0 = 0;
     double k_link = 0, k_bend = 0, k_area = 0, k_volume = 0, kbt = 0, persistence = 1, max_strain = 1;
+    double k_local = 0, theta_m = 0;
 };
 
 // Edge table of a closed oriented triangle mesh: edges numbered by first
@@ -376,10 +377,12 @@ int finalize_impl(hemo_sim *s) {
         const int se = coprime_stride(m.ne), st3 = coprime_stride(m.nt);
         std::vector<int> edge_p(4 * (size_t)m.ne), tri_p(3 * (size_t)m.nt), tpos(m.nt), etri_p(2 * (size_t)m.ne);
         std::vector<R> invL0(m.ne), th0(m.ne);
+        std::vector<R> At0_p(m.nt);
         for (int q = 0; q < m.nt; ++q) {
             const int t = (int)(((long long)q * st3) % m.nt);
             for (int j = 0; j < 3; ++j) tri_p[3 * (size_t)q + j] = m.tri[3 * (size_t)t + j];
             tpos[t] = q;
+            At0_p[q] = R(m.At0[t]);
         }
         // triangle of each directed edge: (v0, v1) -> triangle containing it
         std::unordered_map<long long, int> dir_tri;
@@ -489,6 +492,12 @@ int finalize_impl(hemo_sim *s) {
         d.vwing = dvwing;
         d.vtri = dvtri;
         d.vfan = dvfan;
+        R *dAt0 = (R *)dalloc(s, rs * m.nt);
+        if (!dAt0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
+        HEMO_CU(cudaMemcpy(dAt0, At0_p.data(), rs * m.nt, cudaMemcpyHostToDevice));
+        d.At0 = dAt0;
+        d.k_local = R(m.k_local);
+        d.thm2i = m.theta_m > 0 ? R(1.0 / (m.theta_m * m.theta_m)) : R(0);
         d.A0 = m.A0;
         d.V0 = m.V0;
         d.K = R(m.k_link * m.kbt / m.persistence);
@@ -863,6 +872,9 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
     if (s->steps_done & 1) return fail(HEMO_ERR_STATE, "hemo_record: start at an even step count");
     if (s->force_every != 1 || s->integrator != HEMO_EULER)
         return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form needs forces every step and Euler");
+    for (const HostMesh &m : s->meshes)
+        if (m.k_local > 0 || m.theta_m > 0)
+            return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form supports the four-term membrane model only");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     s->rec = true;
     s->ck_every = checkpoint_every;
@@ -1097,7 +1109,8 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     if (m->nv < 4 || m->nt < 4 || !m->tri || !m->rest_xyz) return fail(HEMO_ERR_ARG, "mesh needs >= 4 vertices and triangles");
     if (ncells < 0 || (ncells > 0 && (!centers || !rot))) return fail(HEMO_ERR_ARG, "bad cell placement arguments");
     if ((long long)s->nv + (long long)ncells * m->nv > 0x3fffffffLL) return fail(HEMO_ERR_ARG, "too many vertices");
-    if (!(m->persistence > 0) || !(m->max_strain > 0) || !(m->kbt >= 0)) return fail(HEMO_ERR_ARG, "bad membrane parameters");
+    if (!(m->persistence > 0) || !(m->max_strain > 0) || !(m->kbt >= 0) || !(m->k_local >= 0) || !(m->theta_m >= 0))
+        return fail(HEMO_ERR_ARG, "bad membrane parameters");
     HostMesh hm;
     hm.nv = m->nv;
     hm.nt = m->nt;
@@ -1126,10 +1139,13 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     }
     c = {c.x / hm.nv, c.y / hm.nv, c.z / hm.nv};
     double A = 0, V = 0;
+    hm.At0.resize(hm.nt);
     for (int t = 0; t < hm.nt; ++t) {
         const D3 p0 = P(hm.tri[3 * t]), p1 = P(hm.tri[3 * t + 1]), p2 = P(hm.tri[3 * t + 2]);
         const D3 n = crs(sub(p1, p0), sub(p2, p0));
-        A += 0.5 * std::sqrt(dt3(n, n));
+        hm.At0[t] = 0.5 * std::sqrt(dt3(n, n));
+        if (m->k_local > 0 && !(hm.At0[t] > 0)) return fail(HEMO_ERR_ARG, "zero-area rest triangle");
+        A += hm.At0[t];
         V += dt3(sub(p0, c), crs(sub(p1, c), sub(p2, c))) / 6.0;
     }
     hm.A0 = A;
@@ -1142,6 +1158,8 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     hm.kbt = m->kbt;
     hm.persistence = m->persistence;
     hm.max_strain = m->max_strain;
+    hm.k_local = m->k_local;
+    hm.theta_m = m->theta_m;
     const int type = (int)s->meshes.size();
     s->meshes.push_back(hm);
     s->max_nv = std::max(s->max_nv, hm.nv);

@@ -88,6 +88,12 @@ template <typename R> struct MeshDev {
     // then -1; entry {T_k, j_k, edge (i, j_k) << 1 | role, edge (j_k, j_k+1)}
     // with T_k = (i, j_k, j_k+1) as oriented
     const int4 *vfan;
+    // optional terms for large deformations (0 = off): per-triangle rest area
+    // (processing order) and local area modulus; 1 / theta_m^2 of the
+    // nonlinear bending term
+    const R *At0;
+    R k_local;
+    R thm2i;
     double A0, V0;
     R K;                // k_link * kbt / persistence
     R m2;               // max_strain^2
@@ -195,7 +201,7 @@ void launch_build_links(int nx, int ny, int nz, const int *per, uint8_t *ntype, 
 template <typename R> void launch_cell_forces(const View<R> &v, int mode, double *stats, cudaStream_t st);
 template <typename R> cudaError_t set_cell_smem_limit(size_t bytes);
 template <typename R> size_t cell_smem_bytes(int max_nv, int max_nt, int max_ne) {
-    return (4 * (size_t)max_nv + 4 * (size_t)max_nt + 4 * (size_t)max_ne) * sizeof(R);
+    return (4 * (size_t)max_nv + 5 * (size_t)max_nt + 4 * (size_t)max_ne) * sizeof(R);
 }
 template <typename R> void launch_bins(const View<R> &v, cudaStream_t st, bool stable);
 // the bin ranges and the (unstable) order once the step's membrane kernel

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
     R *xs = reinterpret_cast<R *>(smem_raw);  // nv*4: offsets from the (new) centroid, padded
     R *tn = xs + 4 * v.max_nv;                  // nt*4: n / |n|^2 and |n|
     R *es = tn + 4 * v.max_nt;                  // ne*4 per-edge force coefficients
+    R *tl = es + 4 * v.max_ne;                  // nt: 1/2 dE_local/dA_t (local area term, if on)
     __shared__ double scratch[6][32];
     __shared__ R rscratch[3][32];
     __shared__ double cnew[3];
@@ -273,6 +274,10 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
             const V3<R> n = cross(p1 - p0, p2 - p0);
             const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
             st4(tn + 4 * t, iq * n.x, iq * n.y, iq * n.z, ln);
+            if (m.k_local > R(0)) {
+                const R a0 = __ldg(m.At0 + t);
+                tl[t] = R(0.5) * m.k_local * (R(0.5) * ln - a0) / a0;
+            }
             av[0].add(R(0.5) * ln);
             av[1].add(dot(p0, cross(p1, p2)) / R(6));
         }
@@ -351,7 +356,13 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         const R dEdL = m.K * (eps + eps / den);
         const V3<R> a1 = xyz(ld4(tn + 4 * T.x)), a2 = xyz(ld4(tn + 4 * T.y));  // n / |n|^2
         const R th = atan2_r(dot(cross(a1, a2), ed) * iL, dot(a1, a2));
-        const R cb = m.kb * (th - th0);
+        const R dth = th - th0;
+        R cb = m.kb * dth;  // dE/dtheta
+        if (m.thm2i > R(0)) {  // nonlinear bending
+            const R r2 = dth * dth * m.thm2i;
+            if (!(r2 < R(1))) atomicOr(v.status, ST_NUMERIC);
+            cb = cb / (R(1) - r2);
+        }
         st4(es + 4 * e, dEdL * iL, cb * L, cb * (dot(pa - p1, ed) * iL), cb * (dot(pb - p1, ed) * iL));
     }
     __syncthreads();
@@ -369,6 +380,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         Q4<R> ap = ld4(tn + 4 * g.x);  // T_k-1: n / |n|^2 and |n|
         V3<R> xp = xyz(ld4(xs + 4 * g.y));  // position of j_k-1
         int op = g.w;  // edge of T_k-1 opposite i
+        int tp = g.x;  // T_k-1
         for (int k = 1; k <= m.maxv; ++k) {
             g = __ldg(m.vfan + (size_t)k * m.nv + i);
             if (g.x < 0) break;
@@ -383,10 +395,12 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
             f = r1 ? f + lk - ((cf.z + cf.y) * a1 + (cf.w + cf.y) * a2) : f + lk + (cf.z * a1 + cf.w * a2);
             f = f + es[4 * op + 1] * xyz(ap);
             const V3<R> nh = ap.w * xyz(ap);  // unit normal of T_k-1
-            f = f - (ha * cross(nh, xk - xp) + sv * cross(xp, xk));
+            const R hk = m.k_local > R(0) ? ha + tl[tp] : ha;  // global and local area terms
+            f = f - (hk * cross(nh, xk - xp) + sv * cross(xp, xk));
             ap = ak;
             xp = xk;
             op = g.w;
+            tp = g.x;
         }
         R *o = v.Fv + 3 * (size_t)(first + i);
         o[0] = f.x;

@@ -41,7 +41,7 @@ class hemo_mesh_desc(C.Structure):
     _fields_ = [('nv', C.c_int), ('nt', C.c_int), ('tri', C.c_void_p), ('rest_xyz', C.c_void_p),
                 ('k_link', C.c_double), ('k_bend', C.c_double), ('k_area', C.c_double),
                 ('k_volume', C.c_double), ('kbt', C.c_double), ('persistence', C.c_double),
-                ('max_strain', C.c_double)]
+                ('max_strain', C.c_double), ('k_local', C.c_double), ('theta_m', C.c_double)]
 
 
 class HemoError(RuntimeError):
@@ -234,7 +234,8 @@ class Simulation:
         centers = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, 3)
         rots = np.ascontiguousarray(rots, dtype=np.float64).reshape(-1, 3, 3)
         m = hemo_mesh_desc(len(rest), len(tri), tri.ctypes.data, rest.ctypes.data, mesh.k_link, mesh.k_bend,
-                           mesh.k_area, mesh.k_volume, mesh.kbt, mesh.persistence, mesh.max_strain)
+                           mesh.k_area, mesh.k_volume, mesh.kbt, mesh.persistence, mesh.max_strain,
+                           getattr(mesh, 'k_local', 0.0), getattr(mesh, 'theta_m', 0.0))
         first = C.c_int(-1)
         check(lib().hemo_add_cells(self.handle, C.byref(m), len(centers), centers.ctypes.data,
                                    rots.ctypes.data, C.byref(first)))
