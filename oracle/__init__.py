@@ -80,6 +80,10 @@ def lib():
         L.ora_num_vertices.restype = C.c_long
         L.ora_num_cells.argtypes = [C.c_void_p]
         L.ora_num_cells.restype = C.c_int
+        L.ora_inside.argtypes = [C.c_void_p, _bp]
+        L.ora_set_viscosity_ratio.argtypes = [C.c_void_p, C.c_double]
+        L.ora_set_viscosity_ratio.restype = C.c_int
+        L.ora_force_inside.argtypes = [C.c_void_p, C.c_void_p]
         L.ora_set_threads.argtypes = [C.c_int]
         L.ora_get_threads.restype = C.c_int
         L.ora_set_threads(1)
@@ -223,6 +227,27 @@ class OracleSim:
         rc = lib().ora_set_time_scales(self.h, int(force_every), INTEGRATORS[integrator])
         if rc != 0:
             raise ValueError('force_every must be >= 1')
+
+    def set_viscosity_ratio(self, ratio):
+        """Internal viscosity ratio: nodes inside cells relax with
+        tau_in = 1/2 + ratio (tau - 1/2); 1 = off."""
+        if lib().ora_set_viscosity_ratio(self.h, float(ratio)) != 0:
+            raise ValueError('ratio must be > 0')
+
+    def inside(self):
+        """Inside/outside indicator of the current vertex positions [z, y, x]."""
+        out = np.zeros(self.N, np.uint8)
+        lib().ora_inside(self.h, out)
+        return out.reshape(self.shape)
+
+    def force_inside(self, ind):
+        """Tests: use the given indicator instead of the cells' (None: back
+        to the cells')."""
+        if ind is None:
+            lib().ora_force_inside(self.h, None)
+        else:
+            self._forced = _c(ind, np.uint8).ravel()
+            lib().ora_force_inside(self.h, self._forced.ctypes.data)
 
     def step(self, n=1):
         lib().ora_step(self.h, int(n))

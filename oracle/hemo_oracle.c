@@ -58,6 +58,17 @@
  *     without bound as |theta - theta0| approaches theta_m; with k_local > 0
  *     each triangle adds 1/2 k_local (A_t - A_t0)^2 / A_t0 (A_t0 its rest
  *     area; lattice energy per lattice area);
+ *   - internal viscosity (Sec. 1: the cytosol is five times as viscous as the
+ *     plasma; Sec. 3: the RBC model has an internal viscosity ratio): with a
+ *     ratio lambda != 1, nodes inside a cell membrane at X^n relax with tau_in
+ *     = 1/2 + lambda (tau - 1/2) (nu_in = lambda nu).  A node is inside when
+ *     the upward ray from it crosses the cell's surface with a net signed
+ *     count (sign of the outward normal's z component) of one; a node whose
+ *     column passes exactly through a projected triangle edge belongs to the
+ *     triangle for which the edge, traversed counter-clockwise as seen from
+ *     +z, points in -y, or in +x when horizontal (each shared edge is
+ *     evaluated in one canonical vertex order, so its two triangles agree);
+ *     a crossing at exactly the node's height counts as below it;
  *   - area / volume: per cell, in strain form 1/2 k_area ((A - A0)/A0)^2 and
  *     1/2 k_volume ((V - V0)/V0)^2 with k in lattice energy units.  (The form
  *     1/2 k (V - V0)^2 / V0 with k_volume = 20 makes the explicit coupling
@@ -409,6 +420,10 @@ typedef struct {
     long nstep, ts_origin; /* steps taken; step at which the setting was made */
     int have_prev;         /* Up holds U^{n-1} */
     double *Up;            /* nvtot*3 */
+    /* internal viscosity */
+    double visc_ratio;     /* 1: off */
+    unsigned char *inside; /* N, indicator of the current step */
+    unsigned char *forced; /* N or NULL: indicator given by the caller (tests) */
 } osim;
 
 #define ORA_EULER 0
@@ -435,10 +450,12 @@ void *ora_create(int nx, int ny, int nz, double tau, const int *periodic, const 
     s->rho_c = (double *)malloc(sizeof(double) * s->N);
     s->force_every = 1;
     s->integrator = ORA_EULER;
+    s->visc_ratio = 1.0;
+    s->inside = (unsigned char *)calloc(s->N, 1);
     s->F = (double *)calloc(3 * s->N, sizeof(double));
     s->u = (double *)calloc(3 * s->N, sizeof(double));
     for (long n = 0; n < s->N; ++n) {
-        for (int i = 0; i < Q; ++i) s->f[n * Q + i] = W[i];
+        for (int i = 0; i < Q; ++i) s->f[n * Q + i] = s->fn[n * Q + i] = W[i];  /* (wall nodes keep w) */
         if (s->mask[n]) for (int d = 0; d < 3; ++d) s->u[3 * n + d] = s->uw[s->mask[n]][d];
     }
     return s;
@@ -450,6 +467,7 @@ void ora_destroy(void *p) {
     for (int t = 0; t < s->ntypes; ++t) mesh_free(&s->types[t]);
     free(s->mask); free(s->f); free(s->fn); free(s->rho_c); free(s->F); free(s->u);
     free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c); free(s->Up);
+    free(s->inside); free(s->forced);
     free(s);
 }
 
@@ -545,6 +563,121 @@ static long neighbour(const osim *s, int x, int y, int z, int cx, int cy, int cz
     return q[0] + (long)s->nx * (q[1] + (long)s->ny * q[2]);
 }
 
+/* ---- inside/outside indicator (internal viscosity) ------------------- */
+/* twice the signed area of the xy-projection, edge u -> v against point p,
+ * always computed from the lower-numbered vertex so that the two triangles
+ * of an edge get exactly opposite values */
+static double edge_fn(const double *X, int iu, int iv, double px, double py) {
+    if (iu < iv) {
+        const double *u = X + 3 * iu, *v = X + 3 * iv;
+        return (v[0] - u[0]) * (py - u[1]) - (v[1] - u[1]) * (px - u[0]);
+    }
+    const double *u = X + 3 * iv, *v = X + 3 * iu;
+    return -((v[0] - u[0]) * (py - u[1]) - (v[1] - u[1]) * (px - u[0]));
+}
+
+/* does the xy-projection of triangle (i0, i1, i2) (positions X) contain
+ * (px, py)?  sgn receives the sign of the outward normal's z component, zc
+ * the height of the triangle's plane at (px, py) */
+static int tri_column(const double *X, int i0, int i1, int i2, double px, double py, int *sgn, double *zc) {
+    const double *a = X + 3 * i0, *b = X + 3 * i1, *c = X + 3 * i2;
+    double e1[3], e2[3], n[3];
+    sub3(b, a, e1); sub3(c, a, e2); cross3(e1, e2, n);
+    if (n[2] == 0) return 0;
+    /* counter-clockwise seen from +z */
+    int v[3] = {i0, i1, i2};
+    if (n[2] < 0) { v[1] = i2; v[2] = i1; }
+    for (int k = 0; k < 3; ++k) {
+        int iu = v[k], iv = v[(k + 1) % 3];
+        double e = edge_fn(X, iu, iv, px, py);
+        if (e < 0) return 0;
+        if (e == 0) {
+            double dx = X[3 * iv] - X[3 * iu], dy = X[3 * iv + 1] - X[3 * iu + 1];
+            if (!(dy < 0 || (dy == 0 && dx > 0))) return 0;
+        }
+    }
+    *sgn = n[2] > 0 ? 1 : -1;
+    *zc = a[2] - (n[0] * (px - a[0]) + n[1] * (py - a[1])) / n[2];
+    return 1;
+}
+
+/* indicator of the current vertex positions: per cell, every node of the
+ * lattice within the bounding box of the cell or of one of its periodic
+ * images sums, over the triangles whose projection contains its column,
+ * the signs of the crossings above it */
+static void compute_inside(osim *s, unsigned char *in) {
+    memset(in, 0, s->N);
+    const long dims[3] = {s->nx, s->ny, s->nz};
+    for (int c = 0; c < s->ncell; ++c) {
+        const omesh *m = &s->types[s->cell_type[c]];
+        const double *X = s->X + 3 * (long)s->cell_first[c];
+        double lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) { lo[d] = X[d]; hi[d] = X[d]; }
+        for (int v = 1; v < m->nv; ++v)
+            for (int d = 0; d < 3; ++d) {
+                if (X[3 * v + d] < lo[d]) lo[d] = X[3 * v + d];
+                if (X[3 * v + d] > hi[d]) hi[d] = X[3 * v + d];
+            }
+        int kmin[3], kmax[3];
+        for (int d = 0; d < 3; ++d) { kmin[d] = s->periodic[d] ? -1 : 0; kmax[d] = s->periodic[d] ? 1 : 0; }
+        for (int kx = kmin[0]; kx <= kmax[0]; ++kx)
+            for (int ky = kmin[1]; ky <= kmax[1]; ++ky)
+                for (int kz = kmin[2]; kz <= kmax[2]; ++kz) {
+                    const long k[3] = {kx, ky, kz};
+                    long j0[3], j1[3];
+                    int empty = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        j0[d] = (long)ceil(lo[d] + k[d] * dims[d]);
+                        j1[d] = (long)floor(hi[d] + k[d] * dims[d]);
+                        if (j0[d] < 0) j0[d] = 0;
+                        if (j1[d] > dims[d] - 1) j1[d] = dims[d] - 1;
+                        if (j0[d] > j1[d]) empty = 1;
+                    }
+                    if (empty) continue;
+                    for (long jz = j0[2]; jz <= j1[2]; ++jz)
+                        for (long jy = j0[1]; jy <= j1[1]; ++jy)
+                            for (long jx = j0[0]; jx <= j1[0]; ++jx) {
+                                /* the node in the cell's own (unwrapped) frame */
+                                double px = (double)(jx - kx * dims[0]), py = (double)(jy - ky * dims[1]);
+                                double pz = (double)(jz - kz * dims[2]);
+                                int w = 0;
+                                for (int t = 0; t < m->nt; ++t) {
+                                    int sg;
+                                    double zc;
+                                    if (tri_column(X, m->tri[3 * t], m->tri[3 * t + 1], m->tri[3 * t + 2], px, py, &sg, &zc)
+                                        && zc > pz)
+                                        w += sg;
+                                }
+                                if (w != 0) in[jx + s->nx * (jy + s->ny * jz)] = 1;
+                            }
+                }
+    }
+}
+
+/* indicator at the current positions (N bytes) */
+void ora_inside(void *p, unsigned char *out) {
+    compute_inside((osim *)p, out);
+}
+
+/* internal viscosity ratio (1 = off) */
+int ora_set_viscosity_ratio(void *p, double ratio) {
+    if (!(ratio > 0)) return -1;
+    ((osim *)p)->visc_ratio = ratio;
+    return 0;
+}
+
+/* tests: take the indicator from the caller (N bytes) instead of the cells;
+ * NULL returns to the computed one */
+void ora_force_inside(void *p, const unsigned char *ind) {
+    osim *s = (osim *)p;
+    free(s->forced);
+    s->forced = NULL;
+    if (ind) {
+        s->forced = (unsigned char *)malloc(s->N);
+        memcpy(s->forced, ind, s->N);
+    }
+}
+
 /* node index of lattice coordinate j along each axis, -1 if outside */
 static long node_at(const osim *s, long jx, long jy, long jz) {
     long q[3] = {jx, jy, jz};
@@ -613,11 +746,18 @@ static void step_once(osim *s) {
                     }
                 }
     }
-    /* 4: BGK collision with the Guo forcing term (in place in f) */
-    double om = 1.0 / s->tau;
+    /* 4: BGK collision with the Guo forcing term (in place in f); inside
+     * cells tau_in = 1/2 + lambda (tau - 1/2) */
+    const double om_out = 1.0 / s->tau, om_in = 1.0 / (0.5 + s->visc_ratio * (s->tau - 0.5));
+    const int contrast = s->visc_ratio != 1.0;
+    if (contrast) {
+        if (s->forced) memcpy(s->inside, s->forced, N);
+        else compute_inside(s, s->inside);
+    }
     #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (s->mask[n]) continue;
+        const double om = contrast && s->inside[n] ? om_in : om_out;
         double *f = s->f + n * Q;
         const double *Fn = s->F + 3 * n;
         double rho = 0, m[3] = {0, 0, 0};
