@@ -167,6 +167,25 @@ enum hemo_integrator {
  * refuses other settings). */
 int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
 
+/* Internal viscosity (Sec. 1: the cytosol is five times as viscous as the
+ * plasma; Sec. 3: the red-cell model carries an internal viscosity ratio).
+ * From the next step on, fluid nodes inside a cell membrane (at the vertex
+ * positions X^n of the step) relax with tau_in = 1/2 + ratio (tau - 1/2),
+ * i.e. viscosity ratio * nu; 1 (the default) turns it off.  A node is inside
+ * when the upward (+z) ray from it crosses the membrane with a net signed
+ * count of one (tie rules: hemo_get_inside).  Errors: HEMO_ERR_ARG for a
+ * ratio that is not finite and > 0; HEMO_ERR_STATE while recording for
+ * hemo_backward (hemo_record refuses a ratio other than 1). */
+int hemo_set_viscosity_ratio(hemo_sim *sim, double ratio);
+
+/* The inside/outside indicator of the current vertex positions: inside
+ * (any, N bytes, [z][y][x]) receives 1 for nodes inside a cell membrane, 0
+ * elsewhere.  A column passing exactly through a projected triangle edge
+ * belongs to the triangle for which that edge, counter-clockwise seen from
+ * +z, points in -y (in +x when horizontal); a crossing exactly at a node's
+ * height counts as below the node.  Synchronises. */
+int hemo_get_inside(hemo_sim *sim, uint8_t *inside);
+
 /* Wait for the stream and return the device status of all steps so far. */
 int hemo_sync(hemo_sim *sim);
 

@@ -162,6 +162,10 @@ struct hemo_sim {
     bool have_prev = false;       // Uprev holds the previous step's vertex velocity
     void *Uprev = nullptr;
     void *csp = nullptr;          // per cell: centroid of the last re-base as R hi, lo
+    // internal viscosity (Sec. 1, Sec. 3): ratio of the viscosity inside cells
+    double visc_ratio = 1.0;      // 1: off
+    uint8_t *ind = nullptr;       // N: inside a cell
+    int *tog = nullptr;           // N: toggle counts (zero between steps)
     // graphs, one per step variant: parity + 2 force step + 4 integrator mode
     cudaStream_t cap = nullptr;
     static constexpr int NGRAPH = 12;
@@ -291,6 +295,11 @@ View<R> make_view(hemo_sim *s) {
     v.integ = 0;
     v.Uprev = (R *)s->Uprev;
     v.csp = (R *)s->csp;
+    if (s->visc_ratio != 1.0) {
+        v.ind = s->ind;
+        v.tog = s->tog;
+        v.omega_in = R(1.0 / (0.5 + s->visc_ratio * (s->tau - 0.5)));
+    }
     return v;
 }
 
@@ -307,6 +316,7 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStr
         if (force) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
         else launch_hold_bins<R>(v, st);                        // F_v held: anchors and bin counts only
     }
+    if (v.ind) launch_inside<R>(v, st);  // cell interiors at X^n (internal viscosity)
     mark(HEMO_PHASE_BINS);
     if (s->ncell) launch_bin_ranges<R>(v, st);  // counting sort by block
     mark(HEMO_PHASE_SPREAD);
@@ -875,6 +885,7 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
     for (const HostMesh &m : s->meshes)
         if (m.k_local > 0 || m.theta_m > 0)
             return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form supports the four-term membrane model only");
+    if (s->visc_ratio != 1.0) return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form needs a viscosity ratio of 1");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     s->rec = true;
     s->ck_every = checkpoint_every;
@@ -1223,6 +1234,55 @@ int hemo_set_time_scales(hemo_sim *s, int force_every, int integrator) {
     s->ts_origin = s->steps_done;
     s->have_prev = false;
     return HEMO_OK;
+}
+
+int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (!(ratio > 0) || !std::isfinite(ratio)) return fail(HEMO_ERR_ARG, "viscosity ratio must be finite and > 0");
+    if (!(0.5 + ratio * (s->tau - 0.5) > 0.5)) return fail(HEMO_ERR_ARG, "viscosity ratio gives tau_in <= 1/2");
+    if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_viscosity_ratio: not while recording for the reverse sweep");
+    HEMO_CU(cudaStreamSynchronize(s->stream));
+    if (ratio != 1.0 && !s->ind) {
+        s->ind = (uint8_t *)dalloc(s, (size_t)s->N);
+        s->tog = (int *)dalloc(s, sizeof(int) * (size_t)s->N);
+        if (!s->ind || !s->tog) return fail(HEMO_ERR_OOM, "indicator allocation failed");
+        HEMO_CU(cudaMemsetAsync(s->tog, 0, sizeof(int) * (size_t)s->N, s->stream));
+        HEMO_CU(cudaMemsetAsync(s->ind, 0, (size_t)s->N, s->stream));
+    }
+    s->visc_ratio = ratio;
+    for (int k = 0; k < hemo_sim::NGRAPH; ++k)  // the step graphs carry the relaxation rates
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    s->last_graph = -1;
+    return HEMO_OK;
+}
+
+int hemo_get_inside(hemo_sim *s, uint8_t *inside) {
+    if (!s || !inside) return fail(HEMO_ERR_ARG, "null pointer");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (!s->tog) {
+        s->ind = (uint8_t *)dalloc(s, (size_t)s->N);
+        s->tog = (int *)dalloc(s, sizeof(int) * (size_t)s->N);
+        if (!s->ind || !s->tog) return fail(HEMO_ERR_OOM, "indicator allocation failed");
+        HEMO_CU(cudaMemsetAsync(s->tog, 0, sizeof(int) * (size_t)s->N, s->stream));
+    }
+    if (is_f64(s)) {
+        View<double> v = make_view<double>(s);
+        v.ind = s->ind;
+        v.tog = s->tog;
+        launch_inside<double>(v, s->stream);
+    } else {
+        View<float> v = make_view<float>(s);
+        v.ind = s->ind;
+        v.tog = s->tog;
+        launch_inside<float>(v, s->stream);
+    }
+    HEMO_CU(cudaGetLastError());
+    HEMO_CU(cudaMemcpyAsync(inside, s->ind, (size_t)s->N, cudaMemcpyDefault, s->stream));
+    return hemo_sync(s);
 }
 
 int hemo_sync(hemo_sim *s) {

@@ -146,6 +146,11 @@ template <typename R> struct View {
     // Uprev; 2 Adams-Bashforth X += 3/2 U - 1/2 Uprev and U kept in Uprev
     int integ;
     R *Uprev;                  // nv*3 interpolated velocity of the previous step
+    // internal viscosity (null when off): per-node indicator of the cell
+    // interiors and the toggle counts it is built from; relaxation rate inside
+    uint8_t *ind;
+    int *tog;
+    R omega_in;
     R *csp;                    // ncell*6 centroid of the last re-base as R hi (3), lo (3)
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
@@ -186,6 +191,8 @@ template <typename R> struct AdjView {
 // launchers (R = double for HEMO_F64, float otherwise)
 template <typename R> void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st);
 template <typename R> void launch_hold_bins(const View<R> &v, cudaStream_t st);
+// inside/outside indicator at the current vertex positions into v.ind
+template <typename R> void launch_inside(const View<R> &v, cudaStream_t st);
 // allows the staged collision kernels of a precision `bytes` of dynamic shared memory
 cudaError_t set_tile_smem_limit(int precision, int bytes);
 template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);

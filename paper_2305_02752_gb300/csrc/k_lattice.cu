@@ -148,7 +148,8 @@ __device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr 
     load_pops<T, R, PARITY, LINKS, I>(v, n, lk, o, d);
     const size_t N = (size_t)v.N;
     R rho, ux, uy, uz;
-    bgk_guo<R>(d, v.F[n], v.F[N + n], v.F[2 * N + n], v.omega, p, rho, ux, uy, uz);
+    const R om = (v.ind && v.ind[n]) ? v.omega_in : v.omega;  // inside a cell: internal viscosity
+    bgk_guo<R>(d, v.F[n], v.F[N + n], v.F[2 * N + n], om, p, rho, ux, uy, uz);
     if (v.rec) {
         v.rec[n] = rho;
         v.rec[N + n] = ux;
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
 #pragma unroll
             for (int i = 0; i < Q; ++i) d[i] = Store<T>::ld(at(i));
             R rho, ux, uy, uz;
-            bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], v.omega, p, rho, ux, uy, uz);
+            const R om = (v.ind && v.ind[(size_t)tl.x * nx + L]) ? v.omega_in : v.omega;
+            bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], om, p, rho, ux, uy, uz);
             if (v.rec) {
                 const size_t n = (size_t)tl.x * nx + L;
                 v.rec[n] = rho;

@@ -70,6 +70,8 @@ def lib():
         'hemo_add_cells': ([vp, C.POINTER(hemo_mesh_desc), i, vp, vp, C.POINTER(i)], i),
         'hemo_step': ([vp, i], i),
         'hemo_set_time_scales': ([vp, i, i], i),
+        'hemo_set_viscosity_ratio': ([vp, d], i),
+        'hemo_get_inside': ([vp, vp], i),
         'hemo_sync': ([vp], i),
         'hemo_get_fields': ([vp, C.c_uint, vp, vp, vp, vp, vp], i),
         'hemo_get_sizes': ([vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(i), C.POINTER(i)], i),
@@ -100,7 +102,7 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the load test)."""
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_set_time_scales',
-            'hemo_sync',
+            'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
             'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
@@ -250,6 +252,17 @@ class Simulation:
         """Membrane forces every `force_every` steps, held in between, and
         the vertex integrator 'euler' or 'ab2' (Sec. 2.6), from this step on."""
         check(lib().hemo_set_time_scales(self.handle, int(force_every), INTEGRATORS[integrator]))
+
+    def set_viscosity_ratio(self, ratio):
+        """Viscosity inside cells relative to the plasma (1 = off): inside
+        nodes relax with tau_in = 1/2 + ratio (tau - 1/2)."""
+        check(lib().hemo_set_viscosity_ratio(self.handle, float(ratio)))
+
+    def inside(self):
+        """Inside/outside indicator of the current vertex positions [z, y, x]."""
+        out = np.zeros(self.shape, np.uint8)
+        check(lib().hemo_get_inside(self.handle, out.ctypes.data))
+        return out
 
     def sync(self):
         return check(lib().hemo_sync(self.handle))

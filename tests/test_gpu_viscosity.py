@@ -1,0 +1,114 @@
+"""Internal viscosity (Sec. 1: cytosol five times as viscous as the plasma)
+on the CUDA path against the oracle: the inside/outside indicator bit for
+bit in FP64 (identical tie rules, positions equal to rounding), the coupled
+state with a viscosity ratio of 5 (FP64 relative L2 <= 1e-12; FP32 velocity
+relative L2 <= 1e-5 after 200 steps)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_02752_gb300 import hemo
+from paper_2305_02752_gb300 import inputs as I
+from tests.helpers import forces_close, rel_l2, small_cell_shear
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+F32_TOL = 1e-5
+
+
+def _channel():
+    return I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100)
+
+
+CASES = {
+    'shear': lambda: small_cell_shear(n=24, steps=9),
+    'periodic_edges': lambda: small_cell_shear(n=24, steps=9, center=[0.3, 23.6, 11.5]),
+    'channel': _channel,
+}
+
+
+@pytest.mark.parametrize('case', sorted(CASES))
+@pytest.mark.parametrize('steps', [0, 6])
+def test_indicator_bit_exact_f64(case, steps):
+    cfg = CASES[case]()
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    ref = O.from_config(cfg)
+    sim.step(steps)
+    ref.step(steps)
+    got, exp = sim.inside(), ref.inside()
+    sim.close()
+    assert exp.sum() > 50
+    assert np.array_equal(got, exp)
+
+
+def test_indicator_f32_agrees_but_near_the_surface():
+    """FP32 positions differ from the oracle's by rounding, so nodes within
+    about 1e-5 of a membrane may be classified differently; all others
+    agree."""
+    cfg = _channel()
+    sim = hemo.Simulation.from_config(cfg, 'f32')
+    got = sim.inside()
+    sim.close()
+    exp = O.from_config(cfg).inside()
+    assert (got != exp).sum() <= 1e-4 * exp.sum()
+
+
+@pytest.mark.parametrize('steps', [20, 21])
+def test_coupled_ratio5_f64(steps):
+    cfg = small_cell_shear(steps=steps)
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    sim.set_viscosity_ratio(5.0)
+    sim.step(steps)
+    got = sim.get_fields()
+    sim.close()
+    ref = O.from_config(cfg)
+    ref.set_viscosity_ratio(5.0)
+    ref.step(steps)
+    exp = ref.get()
+    for k in ('u', 'X', 'rho'):
+        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+    assert forces_close(got['Fv'], exp['Fv'], cfg)
+    # the ratio changes the flow at this tolerance
+    plain = O.from_config(cfg)
+    plain.step(steps)
+    assert rel_l2(plain.get()['u'], exp['u']) > 1e-6
+
+
+def test_channel_ratio5_f32_200_steps():
+    cfg = _channel()
+    sim = hemo.Simulation.from_config(cfg, 'f32')
+    sim.set_viscosity_ratio(5.0)
+    sim.step(200)
+    got = sim.get_fields()
+    sim.close()
+    ref = O.from_config(cfg)
+    ref.set_viscosity_ratio(5.0)
+    ref.step(200)
+    exp = ref.get()
+    assert rel_l2(got['u'], exp['u']) < F32_TOL
+    assert rel_l2(got['X'], exp['X']) < F32_TOL
+
+
+def test_ratio_one_is_the_default_and_arguments():
+    cfg = small_cell_shear(steps=6)
+    a = hemo.Simulation.from_config(cfg, 'f32')
+    a.set_viscosity_ratio(1.0)
+    a.step(6)
+    b = hemo.Simulation.from_config(cfg, 'f32')
+    b.step(6)
+    fa, fb = a.get_fields(), b.get_fields()
+    for k in ('u', 'X'):
+        assert np.array_equal(fa[k], fb[k]), k
+    for bad in (0.0, -1.0, float('nan')):
+        with pytest.raises(hemo.HemoError) as e:
+            a.set_viscosity_ratio(bad)
+        assert e.value.code == hemo.HEMO_ERR_ARG
+    a.close()
+    b.close()
+    c = hemo.Simulation.from_config(small_cell_shear(steps=4), 'f64')
+    c.set_viscosity_ratio(5.0)
+    with pytest.raises(hemo.HemoError) as e:
+        c.record(2)
+    assert e.value.code == hemo.HEMO_ERR_STATE
+    c.close()
