@@ -215,6 +215,26 @@ def time_scales(cfg, precision, warmup, steps, torch, flush):
     return {'precision': precision, 'steps': warmup + steps, 'timed_steps': steps, 'results': out}
 
 
+def model_variants(cfg, precision, warmup, steps, torch, flush):
+    """Throughput of the same workload with the optional model terms on: the
+    internal viscosity (ratio 5, cytosol against plasma) and the
+    large-deformation membrane terms (theta_m = 0.5, k_local = 0.05)."""
+    import dataclasses
+    from paper_2305_02752_gb300 import hemo
+    out = []
+    nl = dataclasses.replace(cfg, meshes=[dataclasses.replace(mt, theta_m=0.5, k_local=0.05) for mt in cfg.meshes])
+    for name, c, ratio in (('plain', cfg, 1.0), ('internal viscosity ratio 5', cfg, 5.0),
+                           ('nonlinear bending and local area', nl, 1.0)):
+        sim = hemo.Simulation.from_config(c, precision)
+        sim.set_viscosity_ratio(ratio)
+        sim.step(warmup)
+        sim.sync()
+        total, _, _ = timed_steps(sim, torch, steps, flush, phase_every=0)
+        sim.close()
+        out.append({'variant': name, 'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps})
+    return {'precision': precision, 'timed_steps': steps, 'results': out}
+
+
 def adjoint_cost(torch, steps=200, every=100):
     """Differentiation form on the 48^3 shear box with 4 red cells: device
     time per recorded forward step and per step of the reverse sweep
@@ -378,6 +398,7 @@ def main():
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-adjoint', action='store_true')
     ap.add_argument('--no-time-scales', action='store_true')
+    ap.add_argument('--no-variants', action='store_true')
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -466,6 +487,8 @@ def main():
         line['forms'] = {'steps': args.warmup + fsteps, 'timed_steps': fsteps, 'results': forms}
     if not args.no_time_scales and args.workload in ('channel', 'vessel'):
         line['time_scales'] = time_scales(cfg, precision, args.warmup, min(args.steps, 200), torch, flush)
+    if not args.no_variants and args.workload in ('channel', 'vessel'):
+        line['model_variants'] = model_variants(cfg, precision, args.warmup, min(args.steps, 200), torch, flush)
     if not args.no_e2e:
         line['e2e'] = e2e_job(cfg, precision, torch)
     if not args.no_adjoint:

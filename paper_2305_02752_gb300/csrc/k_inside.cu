@@ -13,10 +13,11 @@
 //      the edge, counter-clockwise seen from +z, points in -y, or in +x when
 //      horizontal) and adds -sign at the first node at or above the crossing
 //      height, atomically, into a per-node toggle count;
-//   2. one thread per column sums the toggles upwards; on a periodic z axis a
-//      cell may wrap around, and the column's count is the running sum minus
-//      its minimum (a column always passes outside every cell somewhere).
-//      The indicator is count > 0; the toggles are reset for the next step.
+//   2. the toggles of each column are summed upwards (segments of the column
+//      in parallel); on a periodic z axis a cell may wrap around, and the
+//      column's count is the running sum minus its minimum (a column always
+//      passes outside every cell somewhere).  The indicator is count > 0; the
+//      toggles are reset for the next step.
 #include "hemo_internal.cuh"
 
 namespace hemo {
@@ -31,6 +32,7 @@ __device__ __forceinline__ R edge_fn(const R (*P)[3], const int *id, int u, int 
     return -((P[u][0] - P[w][0]) * (py - P[w][1]) - (P[u][1] - P[w][1]) * (px - P[w][0]));
 }
 
+// one thread per triangle: grid (cells, triangle blocks of 256)
 template <typename R>
 __global__ void __launch_bounds__(256) inside_toggle_kernel(View<R> v) {
     const int c = blockIdx.x;
@@ -38,7 +40,9 @@ __global__ void __launch_bounds__(256) inside_toggle_kernel(View<R> v) {
     const int first = v.cell_first[c];
     const int dims[3] = {v.nx, v.ny, v.nz};
     const double C[3] = {v.ctr[3 * c], v.ctr[3 * c + 1], v.ctr[3 * c + 2]};
-    for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
+    {
+        const int t = blockIdx.y * blockDim.x + threadIdx.x;
+        if (t >= m.nt) return;
         int id[3];
         R P[3][3];
 #pragma unroll
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(256) inside_toggle_kernel(View<R> v) {
         const R e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
         const R e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
         const R nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
-        if (nz == R(0)) continue;
+        if (nz == R(0)) return;
         const int sgn = nz > R(0) ? 1 : -1;
         // corners counter-clockwise seen from +z
         const int o0 = 0, o1 = sgn > 0 ? 1 : 2, o2 = sgn > 0 ? 2 : 1;
@@ -98,20 +102,41 @@ __global__ void __launch_bounds__(256) inside_toggle_kernel(View<R> v) {
     }
 }
 
+// 32 consecutive columns (x) per CTA, their z range split into SCAN_G
+// segments: each thread sums its segment (loads coalesced across the x
+// lanes), the segment offsets and the column minimum come from shared
+// memory, then each thread writes its segment's indicator.
+constexpr int SCAN_G = 8;
 template <typename R>
-__global__ void __launch_bounds__(256) inside_scan_kernel(View<R> v) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ncol = v.nx * v.ny;
-    if (col >= ncol) return;
-    const size_t stride = (size_t)ncol;
+__global__ void __launch_bounds__(32 * SCAN_G) inside_scan_kernel(View<R> v) {
+    __shared__ int ssum[SCAN_G][32], smin[SCAN_G][32];
+    const int lx = threadIdx.x, g = threadIdx.y;
+    const int x = blockIdx.x * 32 + lx, y = blockIdx.y;
+    const bool col_ok = x < v.nx;
+    const size_t stride = (size_t)v.nx * v.ny;
+    const size_t base = (size_t)x + (size_t)v.nx * y;
+    const int seg = (v.nz + SCAN_G - 1) / SCAN_G, z0 = g * seg, z1 = min(v.nz, z0 + seg);
     int p = 0, mn = 0;
-    for (int z = 0; z < v.nz; ++z) {
-        p += v.tog[col + stride * z];
-        mn = min(mn, p);
+    if (col_ok)
+        for (int z = z0; z < z1; ++z) {
+            p += v.tog[base + stride * z];
+            mn = min(mn, p);
+        }
+    ssum[g][lx] = p;
+    smin[g][lx] = mn;
+    __syncthreads();
+    // running sum before this segment, and the column minimum (at least 0:
+    // the count before z = 0 is the starting point)
+    int off = 0, cmin = 0, run = 0;
+    for (int k = 0; k < SCAN_G; ++k) {
+        if (k == g) off = run;
+        cmin = min(cmin, run + smin[k][lx]);
+        run += ssum[k][lx];
     }
-    p = -mn;  // the count below z = 0
-    for (int z = 0; z < v.nz; ++z) {
-        const size_t n = col + stride * z;
+    if (!col_ok) return;
+    p = off - cmin;  // the count just below z0
+    for (int z = z0; z < z1; ++z) {
+        const size_t n = base + stride * z;
         p += v.tog[n];
         v.tog[n] = 0;
         v.ind[n] = p > 0 ? 1 : 0;
@@ -122,9 +147,8 @@ __global__ void __launch_bounds__(256) inside_scan_kernel(View<R> v) {
 
 template <typename R>
 void launch_inside(const View<R> &v, cudaStream_t st) {
-    if (v.ncell) inside_toggle_kernel<R><<<v.ncell, 256, 0, st>>>(v);
-    const int ncol = v.nx * v.ny;
-    inside_scan_kernel<R><<<(ncol + 255) / 256, 256, 0, st>>>(v);
+    if (v.ncell) inside_toggle_kernel<R><<<dim3(v.ncell, (v.max_nt + 255) / 256), 256, 0, st>>>(v);
+    inside_scan_kernel<R><<<dim3((v.nx + 31) / 32, v.ny), dim3(32, SCAN_G), 0, st>>>(v);
 }
 
 template void launch_inside<double>(const View<double> &, cudaStream_t);
