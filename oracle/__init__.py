@@ -84,6 +84,8 @@ def lib():
         L.ora_set_viscosity_ratio.argtypes = [C.c_void_p, C.c_double]
         L.ora_set_viscosity_ratio.restype = C.c_int
         L.ora_force_inside.argtypes = [C.c_void_p, C.c_void_p]
+        L.ora_set_lees_edwards.argtypes = [C.c_void_p, C.c_double]
+        L.ora_set_lees_edwards.restype = C.c_int
         L.ora_set_threads.argtypes = [C.c_int]
         L.ora_get_threads.restype = C.c_int
         L.ora_set_threads(1)
@@ -227,6 +229,13 @@ class OracleSim:
         rc = lib().ora_set_time_scales(self.h, int(force_every), INTEGRATORS[integrator])
         if rc != 0:
             raise ValueError('force_every must be >= 1')
+
+    def set_lees_edwards(self, U):
+        """Lees-Edwards boundary along z: the image above the box is displaced
+        by U n (mod nx) in x at step n and moves with U x^ (before the first
+        step; fully periodic lattice without walls)."""
+        if lib().ora_set_lees_edwards(self.h, float(U)) != 0:
+            raise ValueError('Lees-Edwards needs a fully periodic lattice without walls, before the first step')
 
     def set_viscosity_ratio(self, ratio):
         """Internal viscosity ratio: nodes inside cells relax with

@@ -69,6 +69,21 @@
  *     +z, points in -y, or in +x when horizontal (each shared edge is
  *     evaluated in one canonical vertex order, so its two triangles agree);
  *     a crossing at exactly the node's height counts as below it;
+ *   - Lees-Edwards boundary (Sec. 2.5: periodic in every direction with
+ *     opposing velocities imposed on two parallel boundaries, cells crossing
+ *     it are moved to the other side): along z, the periodic image above the
+ *     box is displaced by +D_n in x and moves with +U x^ (the image below by
+ *     -D_n, -U), D_n = U n mod nx at step n.  A population streaming across
+ *     the plane comes from the image: its value is the linear interpolation
+ *     in x, at the displaced position, of the post-collision values of the
+ *     two bracketing nodes of the opposite plane, each Galilean-shifted by
+ *     f_eq(rho*, u* +/- U) - f_eq(rho*, u*) (rho*, u* the moments of that
+ *     node's post-collision populations).  Interpolation and spreading treat
+ *     each z-layer of the 4x4x4 stencil that falls in an image with the
+ *     vertex's position displaced by -/+D_n in x (and, for interpolation,
+ *     the image's velocity +/-U x^).  At the start of a step a cell whose
+ *     centroid lies above the box (z >= nz) moves by (-D_n, 0, -nz), below it
+ *     by (+D_n, 0, +nz).  Requires a fully periodic lattice without walls;
  *   - area / volume: per cell, in strain form 1/2 k_area ((A - A0)/A0)^2 and
  *     1/2 k_volume ((V - V0)/V0)^2 with k in lattice energy units.  (The form
  *     1/2 k (V - V0)^2 / V0 with k_volume = 20 makes the explicit coupling
@@ -420,6 +435,9 @@ typedef struct {
     long nstep, ts_origin; /* steps taken; step at which the setting was made */
     int have_prev;         /* Up holds U^{n-1} */
     double *Up;            /* nvtot*3 */
+    /* Lees-Edwards boundary along z */
+    int le_on;
+    double le_U;           /* velocity of the image above relative to the box */
     /* internal viscosity */
     double visc_ratio;     /* 1: off */
     unsigned char *inside; /* N, indicator of the current step */
@@ -666,6 +684,24 @@ int ora_set_viscosity_ratio(void *p, double ratio) {
     return 0;
 }
 
+/* Lees-Edwards boundary with image velocity U (before the first step; needs
+ * a fully periodic lattice without walls) */
+int ora_set_lees_edwards(void *p, double U) {
+    osim *s = (osim *)p;
+    if (s->nstep != 0) return -1;
+    for (int d = 0; d < 3; ++d) if (!s->periodic[d]) return -1;
+    for (long n = 0; n < s->N; ++n) if (s->mask[n]) return -1;
+    s->le_on = 1;
+    s->le_U = U;
+    return 0;
+}
+
+/* image displacement of the current step, in [0, nx) */
+static double le_shift(const osim *s) {
+    double D = fmod(s->le_U * (double)s->nstep, (double)s->nx);
+    return D < 0 ? D + s->nx : D;
+}
+
 /* tests: take the indicator from the caller (N bytes) instead of the cells;
  * NULL returns to the computed one */
 void ora_force_inside(void *p, const unsigned char *ind) {
@@ -713,6 +749,21 @@ void ora_wall_links(void *p, uint32_t *links) {
  * velocity, interpolate and move */
 static void step_once(osim *s) {
     const long N = s->N;
+    const double D = s->le_on ? le_shift(s) : 0.0;
+    /* 0: Lees-Edwards: cells whose centroid left the box through the sheared
+     * plane move to the other side */
+    if (s->le_on)
+        for (int c = 0; c < s->ncell; ++c) {
+            const omesh *m = &s->types[s->cell_type[c]];
+            double *X = s->X + 3 * (long)s->cell_first[c];
+            double ctr[3];
+            centroid(X, m->nv, ctr);
+            double dx = 0, dz = 0;
+            if (ctr[2] >= s->nz) { dx = -D; dz = -s->nz; }
+            else if (ctr[2] < 0) { dx = D; dz = s->nz; }
+            if (dz != 0)
+                for (int v = 0; v < m->nv; ++v) { X[3 * v] += dx; X[3 * v + 2] += dz; }
+        }
     /* 1-2: membrane forces at the current positions (per cell), on every
      * N-th step only; the last ones are held in between */
     if ((s->nstep - s->ts_origin) % s->force_every == 0) {
@@ -733,11 +784,18 @@ static void step_once(osim *s) {
         const double *X = s->X + 3 * v;
         long i0[3];
         for (int d = 0; d < 3; ++d) i0[d] = (long)floor(X[d]);
-        for (int a = -1; a <= 2; ++a)
-            for (int b = -1; b <= 2; ++b)
-                for (int c = -1; c <= 2; ++c) {
-                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
-                    double dl = ora_phi(X[0] - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
+        for (int c = -1; c <= 2; ++c) {
+            long jz = i0[2] + c;
+            /* Lees-Edwards: a layer in the image above (below) takes the
+             * position displaced by -D (+D) */
+            double xp = X[0];
+            if (s->le_on && jz >= s->nz) xp = X[0] - D;
+            else if (s->le_on && jz < 0) xp = X[0] + D;
+            long ix = (long)floor(xp);
+            for (int a = -1; a <= 2; ++a)
+                for (int b = -1; b <= 2; ++b) {
+                    long jx = ix + a, jy = i0[1] + b;
+                    double dl = ora_phi(xp - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
                     long n = node_at(s, jx, jy, jz);
                     for (int d = 0; d < 3; ++d) {
                         double add = s->Fv[3 * v + d] * dl;
@@ -745,6 +803,7 @@ static void step_once(osim *s) {
                         else s->discarded[d] += add;
                     }
                 }
+        }
     }
     /* 4: BGK collision with the Guo forcing term (in place in f); inside
      * cells tau_in = 1/2 + lambda (tau - 1/2) */
@@ -786,6 +845,32 @@ static void step_once(osim *s) {
                 long n = x + (long)s->nx * (y + (long)s->ny * z);
                 if (s->mask[n]) continue;
                 for (int i = 0; i < Q; ++i) {
+                    int zs = z - C[i][2];
+                    if (s->le_on && (zs < 0 || zs >= s->nz)) {
+                        /* from the image above (zs = nz) or below (zs = -1) */
+                        int up = zs >= s->nz;
+                        double xs = x - C[i][0] + (up ? -D : D);
+                        long xa = (long)floor(xs);
+                        double wb = xs - xa;
+                        int ys = y - C[i][1], zb = up ? 0 : s->nz - 1;
+                        double val = 0;
+                        for (int k = 0; k < 2; ++k) {
+                            long sn = node_at(s, xa + k, ys, zb);
+                            const double *fs = s->f + sn * Q;
+                            double r = 0, mm[3] = {0, 0, 0};
+                            for (int j = 0; j < Q; ++j) {
+                                r += fs[j];
+                                for (int d = 0; d < 3; ++d) mm[d] += fs[j] * C[j][d];
+                            }
+                            double us[3] = {mm[0] / r, mm[1] / r, mm[2] / r}, ush[3] = {us[0] + (up ? s->le_U : -s->le_U), us[1], us[2]};
+                            double e0[Q], e1[Q];
+                            ora_equilibrium(r, us, e0);
+                            ora_equilibrium(r, ush, e1);
+                            val += (k ? wb : 1.0 - wb) * (fs[i] + (e1[i] - e0[i]));
+                        }
+                        s->fn[n * Q + i] = val;
+                        continue;
+                    }
                     long src = neighbour(s, x, y, z, -C[i][0], -C[i][1], -C[i][2]);
                     if (src >= 0 && !s->mask[src]) {
                         s->fn[n * Q + i] = s->f[src * Q + i];
@@ -819,15 +904,25 @@ static void step_once(osim *s) {
         long i0[3];
         for (int d = 0; d < 3; ++d) i0[d] = (long)floor(X[d]);
         double U[3] = {0, 0, 0};
-        for (int a = -1; a <= 2; ++a)
-            for (int b = -1; b <= 2; ++b)
-                for (int c = -1; c <= 2; ++c) {
-                    long jx = i0[0] + a, jy = i0[1] + b, jz = i0[2] + c;
-                    double dl = ora_phi(X[0] - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
+        for (int c = -1; c <= 2; ++c) {
+            long jz = i0[2] + c;
+            /* Lees-Edwards: a layer in the image above (below) takes the
+             * displaced position and the image's velocity +U (-U) */
+            double xp = X[0], du = 0;
+            if (s->le_on && jz >= s->nz) { xp = X[0] - D; du = s->le_U; }
+            else if (s->le_on && jz < 0) { xp = X[0] + D; du = -s->le_U; }
+            long ix = (long)floor(xp);
+            for (int a = -1; a <= 2; ++a)
+                for (int b = -1; b <= 2; ++b) {
+                    long jx = ix + a, jy = i0[1] + b;
+                    double dl = ora_phi(xp - jx) * ora_phi(X[1] - jy) * ora_phi(X[2] - jz);
                     long n = node_at(s, jx, jy, jz);
                     if (n < 0) continue; /* resting wall outside the domain */
-                    for (int d = 0; d < 3; ++d) U[d] += s->u[3 * n + d] * dl;
+                    U[0] += (s->u[3 * n] + du) * dl;
+                    U[1] += s->u[3 * n + 1] * dl;
+                    U[2] += s->u[3 * n + 2] * dl;
                 }
+        }
         double *Up = s->Up + 3 * v;
         for (int d = 0; d < 3; ++d) {
             X[d] += ab2 ? 1.5 * U[d] - 0.5 * Up[d] : U[d];
