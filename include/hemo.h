@@ -178,6 +178,28 @@ int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
  * hemo_backward (hemo_record refuses a ratio other than 1). */
 int hemo_set_viscosity_ratio(hemo_sim *sim, double ratio);
 
+/* Lees-Edwards boundary along z (Sec. 2.5: the domain is periodic in every
+ * direction while opposing velocities are imposed on two parallel
+ * boundaries, a uniform shear without walls; cells crossing the boundary
+ * continue on the other side).  The periodic image above the box is
+ * displaced by D_n = U n (mod nx) in x at step n and moves with U x^; the
+ * image below by -D_n and -U.  A population streaming across the plane z = 0
+ * / nz takes the linear interpolation in x, at the displaced position, of
+ * the post-collision populations of the two bracketing nodes of the
+ * opposite plane, each shifted by f_eq(rho*, u* +/- U) - f_eq(rho*, u*) (rho*,
+ * u* that node's post-collision moments).  Interpolation and spreading treat
+ * every z-layer of a vertex's 4x4x4 stencil that falls in an image with the
+ * vertex's position displaced by -/+D_n in x (and, interpolating, the image
+ * velocity +/-U x^).  At the start of a step a cell whose centroid lies
+ * above the box moves by (-D_n, 0, -nz), below it by (+D_n, 0, +nz).  The
+ * lattice uses two population arrays from then on.  Call once, before the
+ * first step, on a lattice periodic on every axis without walls, with the
+ * default time scales.  Errors: HEMO_ERR_ARG (|U| >= 0.3, walls or a
+ * non-periodic axis), HEMO_ERR_STATE (after the first step, twice, time
+ * scales other than every step with Euler, recording), HEMO_ERR_OOM.
+ * hemo_record refuses a simulation with the boundary. */
+int hemo_set_lees_edwards(hemo_sim *sim, double U);
+
 /* The inside/outside indicator of the current vertex positions: inside
  * (any, N bytes, [z][y][x]) receives 1 for nodes inside a cell membrane, 0
  * elsewhere.  A column passing exactly through a projected triangle edge

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 BUILD = os.path.join(HERE, '_build')
 LIB = os.path.join(HERE, 'libhemo.so')
-SOURCES = ['hemo_api.cu', 'k_lattice.cu', 'k_ibm.cu', 'k_membrane.cu', 'k_adjoint.cu', 'k_inside.cu']
-HEADERS = [os.path.join(CSRC, 'hemo_internal.cuh'),
+SOURCES = ['hemo_api.cu', 'k_lattice.cu', 'k_ibm.cu', 'k_membrane.cu', 'k_adjoint.cu', 'k_inside.cu', 'k_lees.cu']
+HEADERS = [os.path.join(CSRC, 'hemo_internal.cuh'), os.path.join(CSRC, 'lattice_core.cuh'),
            os.path.join(os.path.dirname(HERE), 'include', 'hemo.h')]
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-Xcompiler', '-fno-strict-aliasing']

@@ -166,6 +166,12 @@ struct hemo_sim {
     double visc_ratio = 1.0;      // 1: off
     uint8_t *ind = nullptr;       // N: inside a cell
     int *tog = nullptr;           // N: toggle counts (zero between steps)
+    // Lees-Edwards boundary along z (Sec. 2.5)
+    bool has_walls = false;
+    bool le = false;
+    double le_U = 0;
+    void *f2 = nullptr, *le_aux = nullptr;
+    long long *le_n = nullptr;
     // graphs, one per step variant: parity + 2 force step + 4 integrator mode
     cudaStream_t cap = nullptr;
     static constexpr int NGRAPH = 12;
@@ -300,6 +306,13 @@ View<R> make_view(hemo_sim *s) {
         v.tog = s->tog;
         v.omega_in = R(1.0 / (0.5 + s->visc_ratio * (s->tau - 0.5)));
     }
+    if (s->le) {
+        v.le = 1;
+        v.le_U = s->le_U;
+        v.le_n = s->le_n;
+        v.f2 = s->f2;
+        v.le_aux = (R *)s->le_aux;
+    }
     return v;
 }
 
@@ -312,7 +325,7 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStr
     };
     mark(HEMO_PHASE_MEMBRANE);
     if (s->ncell) {
-        cudaMemsetAsync(v.counts, 0, sizeof(int) * v.nbins, st);
+        cudaMemsetAsync(v.counts, 0, sizeof(int) * (v.nbins + (v.le ? 1 : 0)), st);
         if (force) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
         else launch_hold_bins<R>(v, st);                        // F_v held: anchors and bin counts only
     }
@@ -321,7 +334,20 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStr
     if (s->ncell) launch_bin_ranges<R>(v, st);  // counting sort by block
     mark(HEMO_PHASE_SPREAD);
     if (s->ncell) launch_spread<R>(v, st);  // F = g + sum F_v delta
+    if (s->ncell && v.le) launch_le_spread<R>(v, st);  // vertices at the Lees-Edwards plane
     mark(HEMO_PHASE_COLLIDE);
+    if (v.le) {  // Lees-Edwards: two-array collision and streaming, then the coupling at the plane
+        launch_le_lattice<R>(v, s->precision, st);
+        mark(HEMO_PHASE_MOMENTS);
+        mark(HEMO_PHASE_INTERP);
+        if (s->ncell) {
+            launch_interpolate<R>(v, st);
+            launch_le_interp<R>(v, st);
+        }
+        launch_le_advance(v.le_n, st);
+        mark(HEMO_NUM_PHASES);
+        return;
+    }
     View<R> vc = v;  // the spreading tiles are dead once F is gathered
     if (s->ncell) {
         vc.dead = s->tiles;
@@ -356,9 +382,10 @@ int finalize_impl(hemo_sim *s) {
     s->perm = (int *)dalloc(s, sizeof(int) * std::max(nv, 1));
     s->anc_i = (int *)dalloc(s, sizeof(int) * 3 * std::max(nv, 1));
     s->anc_t = dalloc(s, rs * 3 * std::max(nv, 1));
-    s->counts = (int *)dalloc(s, sizeof(int) * s->nbins);
-    s->cursor = (int *)dalloc(s, sizeof(int) * s->nbins);
-    s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
+    // one more bin than the lattice has: the vertices at the Lees-Edwards plane
+    s->counts = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
+    s->cursor = (int *)dalloc(s, sizeof(int) * (s->nbins + 1));
+    s->start = (int *)dalloc(s, sizeof(int) * (s->nbins + 2));
     s->tiles = dalloc(s, rs * 3 * TILE_NODES3 * s->nbins);
     s->Uprev = dalloc(s, rs * 3 * std::max(nv, 1));
     s->csp = dalloc(s, rs * 6 * std::max(nc, 1));
@@ -367,7 +394,7 @@ int finalize_impl(hemo_sim *s) {
         !s->counts || !s->cursor || !s->start)
         return fail(HEMO_ERR_OOM, "device allocation of cell and bin buffers failed");
     cudaStream_t st = s->stream;
-    HEMO_CU(cudaMemsetAsync(s->start, 0, sizeof(int) * (s->nbins + 1), st));
+    HEMO_CU(cudaMemsetAsync(s->start, 0, sizeof(int) * (s->nbins + 2), st));
     HEMO_CU(cudaMemsetAsync(s->Fv, 0, rs * 3 * std::max(nv, 1), st));
 
     // mesh tables
@@ -663,7 +690,7 @@ int save_checkpoint(hemo_sim *s) {
         s->ck_off.push_back(o);
     }
     View<R> v = make_view<R>(s);
-    launch_copy_natural<R>(v, s->precision, (int)(s->steps_done & 1), (R *)s->ck_f[k], s->stream);
+    launch_copy_natural<R>(v, s->precision, s->le ? 0 : (int)(s->steps_done & 1), (R *)s->ck_f[k], s->stream);
     HEMO_CU(cudaMemcpyAsync(s->ck_ctr[k], s->ctr, sizeof(double) * 3 * s->ncell, cudaMemcpyDeviceToDevice, s->stream));
     HEMO_CU(cudaMemcpyAsync(s->ck_off[k], s->off, rsize(s) * 3 * s->nv, cudaMemcpyDeviceToDevice, s->stream));
     HEMO_CU(cudaGetLastError());
@@ -886,6 +913,7 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
         if (m.k_local > 0 || m.theta_m > 0)
             return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form supports the four-term membrane model only");
     if (s->visc_ratio != 1.0) return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form needs a viscosity ratio of 1");
+    if (s->le) return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form does not support the Lees-Edwards boundary");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     s->rec = true;
     s->ck_every = checkpoint_every;
@@ -1030,11 +1058,15 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
     for (int k = 0; k < 3; ++k)
         if (d->periodic[k] != 0 && d->periodic[k] != 1) return fail(HEMO_ERR_ARG, "periodic flags must be 0 or 1");
     if ((d->alloc == nullptr) != (d->release == nullptr)) return fail(HEMO_ERR_ARG, "alloc and release must be given together");
+    bool walls = false;
     if (d->wall_mask)
-        for (long long n = 0; n < N; ++n)
+        for (long long n = 0; n < N; ++n) {
             if (d->wall_mask[n] > 3) return fail(HEMO_ERR_ARG, "wall mask values must be 0..3");
+            walls |= d->wall_mask[n] != 0;
+        }
 
     hemo_sim *s = new hemo_sim();
+    s->has_walls = walls;
     s->precision = d->precision;
     s->nx = d->nx;
     s->ny = d->ny;
@@ -1229,6 +1261,8 @@ int hemo_set_time_scales(hemo_sim *s, int force_every, int integrator) {
     if (force_every < 1) return fail(HEMO_ERR_ARG, "force_every must be >= 1");
     if (integrator != HEMO_EULER && integrator != HEMO_AB2) return fail(HEMO_ERR_ARG, "integrator must be HEMO_EULER or HEMO_AB2");
     if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_time_scales: not while recording for the reverse sweep");
+    if (s->le && (force_every != 1 || integrator != HEMO_EULER))
+        return fail(HEMO_ERR_STATE, "hemo_set_time_scales: the Lees-Edwards boundary supports forces every step with Euler only");
     s->force_every = force_every;
     s->integrator = integrator;
     s->ts_origin = s->steps_done;
@@ -1257,6 +1291,31 @@ int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
         }
     s->last_graph = -1;
     return HEMO_OK;
+}
+
+int hemo_set_lees_edwards(hemo_sim *s, double U) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (!std::isfinite(U) || !(std::fabs(U) < 0.3)) return fail(HEMO_ERR_ARG, "Lees-Edwards velocity must be finite and below 0.3 in magnitude");
+    if (s->steps_done || s->le) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: only once, before the first step");
+    if (!s->per[0] || !s->per[1] || !s->per[2] || s->has_walls)
+        return fail(HEMO_ERR_ARG, "hemo_set_lees_edwards: needs a lattice periodic on every axis without walls");
+    if (s->force_every != 1 || s->integrator != HEMO_EULER)
+        return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: needs forces every step with Euler (hemo_set_time_scales)");
+    if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: not while recording");
+    s->f2 = dalloc(s, tsize(s) * Q * (size_t)s->N);
+    s->le_aux = dalloc(s, rsize(s) * 4 * 2 * (size_t)s->nx * s->ny);
+    s->le_n = (long long *)dalloc(s, sizeof(long long));
+    if (!s->f2 || !s->le_aux || !s->le_n) return fail(HEMO_ERR_OOM, "Lees-Edwards buffers");
+    HEMO_CU(cudaMemsetAsync(s->le_n, 0, sizeof(long long), s->stream));
+    s->le = true;
+    s->le_U = U;
+    for (int k = 0; k < hemo_sim::NGRAPH; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+    s->last_graph = -1;
+    return hemo_sync(s);
 }
 
 int hemo_get_inside(hemo_sim *s, uint8_t *inside) {
@@ -1319,7 +1378,7 @@ int hemo_get_fields(hemo_sim *s, unsigned what, void *rho, void *u, double *vert
     int rc = ensure_ready(s);
     if (rc) return rc;
     const size_t N = (size_t)s->N, rs = rsize(s);
-    const int layout = (int)(s->steps_done & 1);
+    const int layout = s->le ? 0 : (int)(s->steps_done & 1);  // (two-array streaming: natural order)
     size_t need = std::max<size_t>({rs * 3 * N, sizeof(double) * 6 * (size_t)std::max(s->nv, 1),
                                     sizeof(double) * 6 * (size_t)std::max(s->ncell, 1)});
     rc = ensure_staging(s, need);
@@ -1357,7 +1416,7 @@ int hemo_get_populations(hemo_sim *s, double *f) {
     if (rc) return rc;
     rc = ensure_staging(s, sizeof(double) * Q * (size_t)s->N);
     if (rc) return rc;
-    const int layout = (int)(s->steps_done & 1);
+    const int layout = s->le ? 0 : (int)(s->steps_done & 1);  // (two-array streaming: natural order)
     if (is_f64(s)) launch_populations_out<double>(make_view<double>(s), s->precision, layout, (double *)s->staging, s->stream);
     else launch_populations_out<float>(make_view<float>(s), s->precision, layout, (double *)s->staging, s->stream);
     HEMO_CU(cudaGetLastError());

@@ -151,6 +151,15 @@ template <typename R> struct View {
     uint8_t *ind;
     int *tog;
     R omega_in;
+    // Lees-Edwards boundary along z (le = 0: off): image velocity, the
+    // device step counter of the displacement D_n = U n mod nx, the second
+    // population array of the two-array streaming and the post-collision
+    // moments (rho, u) of the planes z = 0 and z = nz - 1 ([2][ny][nx][4])
+    int le;
+    double le_U;
+    long long *le_n;
+    void *f2;
+    R *le_aux;
     R *csp;                    // ncell*6 centroid of the last re-base as R hi (3), lo (3)
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
@@ -193,6 +202,12 @@ template <typename R> void launch_collide(const View<R> &v, int precision, int p
 template <typename R> void launch_hold_bins(const View<R> &v, cudaStream_t st);
 // inside/outside indicator at the current vertex positions into v.ind
 template <typename R> void launch_inside(const View<R> &v, cudaStream_t st);
+// Lees-Edwards boundary: two-array collision and streaming, the coupling of
+// the vertices in the extra bin, and the step counter of the displacement
+template <typename R> void launch_le_lattice(const View<R> &v, int precision, cudaStream_t st);
+template <typename R> void launch_le_spread(const View<R> &v, cudaStream_t st);
+template <typename R> void launch_le_interp(const View<R> &v, cudaStream_t st);
+void launch_le_advance(long long *n, cudaStream_t st);
 // allows the staged collision kernels of a precision `bytes` of dynamic shared memory
 cudaError_t set_tile_smem_limit(int precision, int bytes);
 template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);
@@ -349,6 +364,22 @@ __device__ __forceinline__ void anchor_of(double c, double, double o, int &j, do
     t = X - fl;
 }
 
+// z = c + o as R (Lees-Edwards binning: the plane crossing is decided on it)
+__device__ __forceinline__ float anchor_z_unwrapped(float ch, float cl, float o) {
+    int j;
+    float t;
+    anchor_of(ch, cl, o, j, t);
+    return (float)j + t;
+}
+__device__ __forceinline__ double anchor_z_unwrapped(double c, double, double o) { return c + o; }
+
+// displacement of the Lees-Edwards image above at the current step, in [0, nx)
+template <typename R>
+__device__ __forceinline__ double le_shift(const View<R> &v) {
+    double D = fmod(v.le_U * (double)(*v.le_n), (double)v.nx);
+    return D < 0 ? D + v.nx : D;
+}
+
 // Stencil anchor (wrapped floor and fraction per axis), bin key and bin
 // count of vertex g at X = (ch + cl) + o; flags a vertex outside a
 // non-periodic axis.  Bin counts are added once per group of lanes with the
@@ -372,7 +403,16 @@ __device__ __forceinline__ void bin_vertex(const View<R> &v, size_t g, const R *
         const int jc = j < 0 ? 0 : (j >= dims[d] ? dims[d] - 1 : j);
         b[d] = jc / BLK;
     }
-    const int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
+    int key = b[0] + v.nb[0] * (b[1] + v.nb[1] * b[2]);
+    if (v.le) {  // Lees-Edwards: stencils reaching across z = 0 or z = nz go to the extra bin, with z unwrapped
+        const R zu = anchor_z_unwrapped(ch[2], cl[2], o[2]);
+        const int jz = (int)floor(zu);
+        if (jz < 1 || jz + 2 >= v.nz) {
+            key = v.nbins;
+            v.anc_i[3 * g + 2] = jz;
+            v.anc_t[3 * g + 2] = zu - R(jz);
+        }
+    }
     v.key[g] = key;
     const unsigned act = __activemask();
     const unsigned grp = __match_any_sync(act, key);

@@ -962,7 +962,7 @@ void launch_bins(const View<R> &v, cudaStream_t st, bool stable) {
 
 template <typename R>
 void launch_bin_ranges(const View<R> &v, cudaStream_t st) {
-    scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins);
+    scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins + (v.le ? 1 : 0));  // (+ the Lees-Edwards bin)
     scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv);
 }
 

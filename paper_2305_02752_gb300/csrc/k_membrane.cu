@@ -242,9 +242,21 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         const R ol[3] = {o[0], o[1], o[2]};
         rebase(i, ol);
     }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) cnew[k] = v.ctr[3 * c + k] + (double)mean[k];
+        if (v.le && mode == 0) {  // Lees-Edwards: a centroid that left through z = 0 or nz moves to the other side
+            const double D = le_shift(v);
+            if (cnew[2] >= v.nz) {
+                cnew[0] -= D;
+                cnew[2] -= v.nz;
+            } else if (cnew[2] < 0) {
+                cnew[0] += D;
+                cnew[2] += v.nz;
+            }
+        }
+    }
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; ++k) {
-            cnew[k] = v.ctr[3 * c + k] + (double)mean[k];
             csplit[0][k] = R(cnew[k]);
             csplit[1][k] = R(cnew[k] - (double)csplit[0][k]);
             if (mode == 0) {

@@ -71,6 +71,7 @@ def lib():
         'hemo_step': ([vp, i], i),
         'hemo_set_time_scales': ([vp, i, i], i),
         'hemo_set_viscosity_ratio': ([vp, d], i),
+        'hemo_set_lees_edwards': ([vp, d], i),
         'hemo_get_inside': ([vp, vp], i),
         'hemo_sync': ([vp], i),
         'hemo_get_fields': ([vp, C.c_uint, vp, vp, vp, vp, vp], i),
@@ -102,7 +103,7 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the load test)."""
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_set_time_scales',
-            'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_sync',
+            'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_set_lees_edwards', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
             'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
@@ -257,6 +258,11 @@ class Simulation:
         """Viscosity inside cells relative to the plasma (1 = off): inside
         nodes relax with tau_in = 1/2 + ratio (tau - 1/2)."""
         check(lib().hemo_set_viscosity_ratio(self.handle, float(ratio)))
+
+    def set_lees_edwards(self, U):
+        """Lees-Edwards boundary along z with image velocity U (before the
+        first step; lattice periodic on every axis without walls)."""
+        check(lib().hemo_set_lees_edwards(self.handle, float(U)))
 
     def inside(self):
         """Inside/outside indicator of the current vertex positions [z, y, x]."""

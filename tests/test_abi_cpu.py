@@ -93,6 +93,7 @@ def test_null_handles():
     assert L.hemo_set_time_scales(None, 2, hemo.HEMO_AB2) == hemo.HEMO_ERR_ARG
     assert L.hemo_set_viscosity_ratio(None, 5.0) == hemo.HEMO_ERR_ARG
     assert L.hemo_get_inside(None, None) == hemo.HEMO_ERR_ARG
+    assert L.hemo_set_lees_edwards(None, 0.01) == hemo.HEMO_ERR_ARG
     L.hemo_destroy(None)
 
 
