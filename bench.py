@@ -235,6 +235,28 @@ def model_variants(cfg, precision, warmup, steps, torch, flush):
     return {'precision': precision, 'timed_steps': steps, 'results': out}
 
 
+def lees_edwards_cost(torch, flush, steps=200, warmup=10):
+    """The shear workload of the differentiation form (48^3, 4 red cells,
+    FP32) with its moving walls, and the same cells in a wall-free box with
+    the Lees-Edwards boundary (image velocity 0.02, the walls' velocity
+    difference): fluid-node updates per second of each."""
+    import dataclasses
+    from paper_2305_02752_gb300 import hemo
+    cfg = I.shear_cell(n=48, ncell=4, seed=20230503, steps=steps)
+    le = dataclasses.replace(cfg, mask=None, periodic=(1, 1, 1), wall_velocity=np.zeros((2, 3)))
+    out = []
+    for name, c in (('moving walls', cfg), ('Lees-Edwards', le)):
+        sim = hemo.Simulation.from_config(c, 'f32')
+        if c is le:
+            sim.set_lees_edwards(0.02)
+        sim.step(warmup)
+        sim.sync()
+        total, _, _ = timed_steps(sim, torch, steps, flush, phase_every=0)
+        sim.close()
+        out.append({'boundary': name, 'mlups': c.n_fluid * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps})
+    return {'workload': 'shear 48^3, 4 RBC x 642 vertices, FP32', 'timed_steps': steps, 'results': out}
+
+
 def adjoint_cost(torch, steps=200, every=100):
     """Differentiation form on the 48^3 shear box with 4 red cells: device
     time per recorded forward step and per step of the reverse sweep
@@ -489,6 +511,7 @@ def main():
         line['time_scales'] = time_scales(cfg, precision, args.warmup, min(args.steps, 200), torch, flush)
     if not args.no_variants and args.workload in ('channel', 'vessel'):
         line['model_variants'] = model_variants(cfg, precision, args.warmup, min(args.steps, 200), torch, flush)
+        line['lees_edwards'] = lees_edwards_cost(torch, flush, steps=min(args.steps, 200))
     if not args.no_e2e:
         line['e2e'] = e2e_job(cfg, precision, torch)
     if not args.no_adjoint:

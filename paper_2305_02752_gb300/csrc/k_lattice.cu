@@ -53,13 +53,13 @@ __device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, 
 // collision and streaming of fluid node n with neighbour offsets o,
 // reading and writing the global array directly; LINKS false for a node
 // without wall neighbours (most of them: that path carries no wall terms)
-template <typename T, typename R, int PARITY, bool LINKS, typename I>
+template <typename T, typename R, int PARITY, bool LINKS, typename I, bool VISC = true>
 __device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr &o, uint64_t lk) {
     R d[Q], p[Q];
     load_pops<T, R, PARITY, LINKS, I>(v, n, lk, o, d);
     const size_t N = (size_t)v.N;
     R rho, ux, uy, uz;
-    const R om = (v.ind && v.ind[n]) ? v.omega_in : v.omega;  // inside a cell: internal viscosity
+    const R om = (VISC && v.ind && v.ind[n]) ? v.omega_in : v.omega;  // inside a cell: internal viscosity
     bgk_guo<R>(d, v.F[n], v.F[N + n], v.F[2 * N + n], om, p, rho, ux, uy, uz);
     if (v.rec) {
         v.rec[n] = rho;
@@ -88,13 +88,13 @@ __device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr 
     }
 }
 
-// node (x, y, z) = index n
-template <typename T, typename R, int PARITY, typename I>
+// node (x, y, z) = index n; VISC: the internal viscosity may be on
+template <typename T, typename R, int PARITY, typename I, bool VISC>
 __device__ __forceinline__ void collide_at(const View<R> &v, int n, int x, int y, int z) {
     const uint8_t nt = v.ntype[n];
     if (nt & 0x7f) return;  // wall node
-    if (nt & 0x80) collide_core<T, R, PARITY, true, I>(v, n, nbr_at(v, x, y, z), v.links[n]);
-    else collide_core<T, R, PARITY, false, I>(v, n, nbr_at(v, x, y, z), 0ull);
+    if (nt & 0x80) collide_core<T, R, PARITY, true, I, VISC>(v, n, nbr_at(v, x, y, z), v.links[n]);
+    else collide_core<T, R, PARITY, false, I, VISC>(v, n, nbr_at(v, x, y, z), 0ull);
 }
 
 // any node given by its index (walls included), one code path for nodes
@@ -108,12 +108,12 @@ __device__ __forceinline__ void collide_node(const View<R> &v, int n) {
 }
 
 // all nodes, grid of NODE_BX x NODE_BY blocks over (x, y, z)
-template <typename T, typename R, int PARITY, typename I>
+template <typename T, typename R, int PARITY, typename I, bool VISC>
 __global__ void __launch_bounds__(NODE_BX * NODE_BY, sizeof(R) == 4 ? 4 : 1) collide_stream_kernel(View<R> v) {
     drop_dead_lines(v);
     const int x = blockIdx.x * NODE_BX + threadIdx.x, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
     if (x >= v.nx || y >= v.ny) return;
-    collide_at<T, R, PARITY, I>(v, x + v.nx * (y + v.ny * z), x, y, z);
+    collide_at<T, R, PARITY, I, VISC>(v, x + v.nx * (y + v.ny * z), x, y, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -578,16 +578,28 @@ void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st
         }
     }
     const dim3 g = node_grid(v), b(NODE_BX, NODE_BY);
-    if (narrow_index(v)) {
+    if (v.ind) {  // internal viscosity on
+        if (narrow_index(v)) {
+            if (parity == 0)
+                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned, true><<<g, b, 0, st>>>(v)));
+            else
+                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned, true><<<g, b, 0, st>>>(v)));
+        } else {
+            if (parity == 0)
+                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t, true><<<g, b, 0, st>>>(v)));
+            else
+                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t, true><<<g, b, 0, st>>>(v)));
+        }
+    } else if (narrow_index(v)) {
         if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned><<<g, b, 0, st>>>(v)));
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned, false><<<g, b, 0, st>>>(v)));
         else
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned><<<g, b, 0, st>>>(v)));
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned, false><<<g, b, 0, st>>>(v)));
     } else {
         if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t><<<g, b, 0, st>>>(v)));
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t, false><<<g, b, 0, st>>>(v)));
         else
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t><<<g, b, 0, st>>>(v)));
+            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t, false><<<g, b, 0, st>>>(v)));
     }
 }
 
