@@ -367,7 +367,8 @@ def traffic_from_profile(precision, workload):
     try:
         with open(path) as f:
             prof = json.load(f)
-        src = open(os.path.join(ROOT, 'paper_2305_02752_gb300', 'csrc', 'k_lattice.cu'), 'rb').read()
+        csrc = os.path.join(ROOT, 'paper_2305_02752_gb300', 'csrc')
+        src = b''.join(open(os.path.join(csrc, f), 'rb').read() for f in ('k_lattice.cu', 'lattice_core.cuh'))
         if prof.get('source_sha256') != hashlib.sha256(src).hexdigest():
             return None
         return prof.get('dram_bytes_per_launch')
