@@ -94,3 +94,41 @@ def test_arguments_and_state():
     assert e.value.code == hemo.HEMO_ERR_STATE
     sim.step(1)
     sim.close()
+
+
+def test_all_optional_terms_together_f64():
+    """Lees-Edwards with the internal viscosity (ratio 5) and the
+    large-deformation terms on, a cell across the plane: FP64 against the
+    oracle with the same settings."""
+    steps = 20
+    cfg = _le_config(center=(11.3, 12.1, 23.2), steps=steps)
+    cfg.meshes = [dataclasses.replace(mt, k_local=0.05, theta_m=0.5) for mt in cfg.meshes]
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    sim.set_lees_edwards(0.02)
+    sim.set_viscosity_ratio(5.0)
+    sim.step(steps)
+    got = sim.get_fields()
+    sim.close()
+    ref = O.from_config(cfg)
+    ref.set_lees_edwards(0.02)
+    ref.set_viscosity_ratio(5.0)
+    ref.step(steps)
+    exp = ref.get()
+    for k in ('u', 'X', 'rho'):
+        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+
+
+@pytest.mark.parametrize('prec', ['f16', 'bf16'])
+def test_16bit_storage_against_fp32(prec):
+    """The two-array streaming with 16-bit deviations stays within the
+    precision form's error of the FP32 run (1e-3 FP16, 1e-2 BF16 after 100
+    steps)."""
+    cfg = _le_config(center=(11.3, 12.1, 23.2), steps=100)
+    out = {}
+    for p in ('f32', prec):
+        sim = hemo.Simulation.from_config(cfg, p)
+        sim.set_lees_edwards(0.02)
+        sim.step(100)
+        out[p] = sim.get_fields(hemo.HEMO_U)['u'].astype(np.float64)
+        sim.close()
+    assert rel_l2(out[prec], out['f32']) < (1e-3 if prec == 'f16' else 1e-2)
