@@ -325,7 +325,7 @@ void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStr
     };
     mark(HEMO_PHASE_MEMBRANE);
     if (s->ncell) {
-        cudaMemsetAsync(v.counts, 0, sizeof(int) * (v.nbins + (v.le ? 1 : 0)), st);
+        // (the bin counts start at zero: the previous scan reset them)
         if (force) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
         else launch_hold_bins<R>(v, st);                        // F_v held: anchors and bin counts only
     }
@@ -395,6 +395,7 @@ int finalize_impl(hemo_sim *s) {
         return fail(HEMO_ERR_OOM, "device allocation of cell and bin buffers failed");
     cudaStream_t st = s->stream;
     HEMO_CU(cudaMemsetAsync(s->start, 0, sizeof(int) * (s->nbins + 2), st));
+    HEMO_CU(cudaMemsetAsync(s->counts, 0, sizeof(int) * (s->nbins + 1), st));
     HEMO_CU(cudaMemsetAsync(s->Fv, 0, rs * 3 * std::max(nv, 1), st));
 
     // mesh tables

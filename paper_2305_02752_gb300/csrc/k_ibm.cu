@@ -101,8 +101,9 @@ __global__ void anchor_count_kernel(View<R> v) {
     if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
 }
 
-// exclusive scan of the block counts by one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) scan_kernel(const int *counts, int *start, int *cursor, int nbins) {
+// exclusive scan of the block counts by one CTA of 1024 threads; the counts
+// are reset to zero for the next binning
+__global__ void __launch_bounds__(1024) scan_kernel(int *counts, int *start, int *cursor, int nbins) {
     __shared__ int part[1024];
     const int per = (nbins + 1023) / 1024;
     const int lo = threadIdx.x * per;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int *counts, int *star
         start[k] = run;
         cursor[k] = run;
         run += counts[k];
+        counts[k] = 0;
     }
     if (threadIdx.x == 1023) start[nbins] = part[1023];
 }
