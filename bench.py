@@ -376,6 +376,21 @@ def traffic_from_profile(precision, workload):
         return None
 
 
+def max_over_ranks(torch, dist, value, device):
+    """The largest value over the ranks (a replicated job takes as long as
+    its slowest rank); dist None: the value itself."""
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, secs):
+    """Whole-job rate in millions of units per second: every rank processes
+    its own replica, the job's time is the slowest rank's."""
+    return world * units_per_rank / secs / 1e6
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -465,17 +480,14 @@ def main():
     ptotal, phases, kps = timed_steps(sim, torch, PHASE_STEPS, flush, phase_every=1)
     sim.sync()
     sim.close()
-    t = torch.tensor([total_ms], dtype=torch.float64, device='cuda')
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(torch, dist, total_ms, 'cuda')
     if rank != 0:
         dist.destroy_process_group()
         return
 
     nf, nv = cfg.n_fluid, cfg.n_vertices
     secs = total_ms * 1e-3
-    value = world * nf * args.steps / secs / 1e6
+    value = job_rate(nf * args.steps, world, secs)
     peak, peak_kind = hbm_peak()
     bpn = bytes_per_node(precision)
     coll = phases.get('collide')
