@@ -188,6 +188,13 @@ __global__ void __launch_bounds__(128) sort_bins_kernel(const int *start, const 
     }
 }
 
+// 4-byte asynchronous copy global -> shared (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // four consecutive values from 16-byte aligned shared memory
 __device__ __forceinline__ void ld4v(const float *p, float *o) {
     const float4 q = *reinterpret_cast<const float4 *>(p);
@@ -665,18 +672,23 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
     }
     __syncthreads();
     const size_t N = (size_t)v.N;
+    // asynchronous copies (no register round trip: all of a thread's loads
+    // are in flight at once); nodes beyond a non-periodic edge are a
+    // resting wall
     for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
         const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
         const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);  // beyond a non-periodic edge: resting wall
+        float4 *dst = tile + (l0 + TS_Y * l1 + TS_Z * l2);
         if ((jx | jy | jz) >= 0) {
             const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
-            t.x = v.u[n];
-            t.y = v.u[N + n];
-            t.z = v.u[2 * N + n];
+            cp_async4(&dst->x, v.u + n);
+            cp_async4(&dst->y, v.u + N + n);
+            cp_async4(&dst->z, v.u + 2 * N + n);
+        } else {
+            *dst = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        tile[l0 + TS_Y * l1 + TS_Z * l2] = t;
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int j = jf; j < e; j += blockDim.x) {
         int i;
