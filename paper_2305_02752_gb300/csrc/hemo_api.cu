@@ -437,34 +437,17 @@ int finalize_impl(hemo_sim *s) {
             invL0[q] = R(1.0 / m.L0[e]);
             th0[q] = R(m.th0[e]);
         }
-        // incidence of each vertex: the edges it ends, the edges it is a
-        // wing of, its triangles (processing order), stored slot-major
-        std::vector<std::vector<int4>> ends(m.nv), tris(m.nv);
-        std::vector<std::vector<int2>> wings(m.nv);
-        for (int q = 0; q < m.ne; ++q) {
-            const int *E = &edge_p[4 * (size_t)q];
-            const int t1 = etri_p[2 * (size_t)q], t2 = etri_p[2 * (size_t)q + 1];
-            ends[E[0]].push_back(make_int4(q << 1, E[1], t1, t2));
-            ends[E[1]].push_back(make_int4((q << 1) | 1, E[0], t1, t2));
-            wings[E[2]].push_back(make_int2(q, t1));
-            wings[E[3]].push_back(make_int2(q, t2));
-        }
+        // the triangles of each vertex (processing order): {triangle, next
+        // corner, the one after}
+        std::vector<std::vector<int4>> tris(m.nv);
         std::vector<int4> tri4(m.nt);
         for (int q = 0; q < m.nt; ++q) {
             const int *T = &tri_p[3 * (size_t)q];
             tri4[q] = make_int4(T[0], T[1], T[2], 0);
             for (int r = 0; r < 3; ++r) tris[T[r]].push_back(make_int4(q, T[(r + 1) % 3], T[(r + 2) % 3], 0));
         }
-        int maxv = 0;
-        for (int i = 0; i < m.nv; ++i)
-            maxv = std::max(maxv, (int)std::max(ends[i].size(), std::max(wings[i].size(), tris[i].size())));
-        std::vector<int4> vend((size_t)maxv * m.nv, make_int4(-1, 0, 0, 0)), vtri((size_t)maxv * m.nv, make_int4(-1, 0, 0, 0));
-        std::vector<int2> vwing((size_t)maxv * m.nv, make_int2(-1, 0));
-        for (int i = 0; i < m.nv; ++i) {
-            for (size_t k = 0; k < ends[i].size(); ++k) vend[k * m.nv + i] = ends[i][k];
-            for (size_t k = 0; k < wings[i].size(); ++k) vwing[k * m.nv + i] = wings[i][k];
-            for (size_t k = 0; k < tris[i].size(); ++k) vtri[k * m.nv + i] = tris[i][k];
-        }
+        int maxv = 0;  // largest valence (on a closed manifold: triangles = edges per vertex)
+        for (int i = 0; i < m.nv; ++i) maxv = std::max(maxv, (int)tris[i].size());
         // the fan of each vertex i in cyclic order: triangles T_k = (i, j_k,
         // j_k+1) as oriented, so that consecutive T_k share the edge (i, j_k).
         // Slot 0 repeats the last entry (the loop's carried values start
@@ -502,13 +485,6 @@ int finalize_impl(hemo_sim *s) {
         int4 *dvfan = (int4 *)dalloc(s, sizeof(int4) * vfan.size());
         if (!dvfan) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
         HEMO_CU(cudaMemcpy(dvfan, vfan.data(), sizeof(int4) * vfan.size(), cudaMemcpyHostToDevice));
-        int4 *dvend = (int4 *)dalloc(s, sizeof(int4) * vend.size());
-        int2 *dvwing = (int2 *)dalloc(s, sizeof(int2) * vwing.size());
-        int4 *dvtri = (int4 *)dalloc(s, sizeof(int4) * vtri.size());
-        if (!dvend || !dvwing || !dvtri) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");
-        HEMO_CU(cudaMemcpy(dvend, vend.data(), sizeof(int4) * vend.size(), cudaMemcpyHostToDevice));
-        HEMO_CU(cudaMemcpy(dvwing, vwing.data(), sizeof(int2) * vwing.size(), cudaMemcpyHostToDevice));
-        HEMO_CU(cudaMemcpy(dvtri, vtri.data(), sizeof(int4) * vtri.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dtri4, tri4.data(), sizeof(int4) * tri4.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dtri, tri_p.data(), sizeof(int) * tri_p.size(), cudaMemcpyHostToDevice));
         HEMO_CU(cudaMemcpy(dedge, edge_p.data(), sizeof(int) * edge_p.size(), cudaMemcpyHostToDevice));
@@ -526,9 +502,6 @@ int finalize_impl(hemo_sim *s) {
         d.th0 = dth0;
         d.tri4 = dtri4;
         d.maxv = maxv;
-        d.vend = dvend;
-        d.vwing = dvwing;
-        d.vtri = dvtri;
         d.vfan = dvfan;
         R *dAt0 = (R *)dalloc(s, rs * m.nt);
         if (!dAt0) return fail(HEMO_ERR_OOM, "device allocation of mesh tables failed");

@@ -72,18 +72,9 @@ template <typename R> struct MeshDev {
     const R *invL0;     // ne: 1 / rest length
     const R *th0;       // ne: rest dihedral angle
     const int4 *tri4;   // nt: the triangle's corners, padded to 16 bytes
-    // per vertex, the edges and triangles it belongs to, slot-major (entry
-    // [slot * nv + vertex]; slots 0 .. maxv - 1, id -1 = empty), one record
-    // each so that the gather needs no further table lookups; ids in
-    // processing order:
-    //   ends:  {edge << 1 | role (0 = v0, 1 = v1), other end, t1, t2}
-    //   wings: {edge, the triangle (v0, v1, this vertex) or (v1, v0, this)}
-    //   tris:  {triangle, next corner, the one after, -}
-    int maxv;
-    const int4 *vend;
-    const int2 *vwing;
-    const int4 *vtri;
-    // per vertex its fan in cyclic order, slot-major over maxv + 1 slots:
+    int maxv;  // largest valence
+    // per vertex its fan in cyclic order, slot-major (entry [slot * nv +
+    // vertex]) over maxv + 1 slots, ids in processing order:
     // slot 0 = the last entry again, slots 1..deg the entries k = 0..deg-1,
     // then -1; entry {T_k, j_k, edge (i, j_k) << 1 | role, edge (j_k, j_k+1)}
     // with T_k = (i, j_k, j_k+1) as oriented
