@@ -175,7 +175,9 @@ int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
  * when the upward (+z) ray from it crosses the membrane with a net signed
  * count of one (tie rules: hemo_get_inside).  Errors: HEMO_ERR_ARG for a
  * ratio that is not finite and > 0; HEMO_ERR_STATE while recording for
- * hemo_backward (hemo_record refuses a ratio other than 1). */
+ * hemo_backward (hemo_record refuses a ratio other than 1), and with the
+ * Lees-Edwards boundary (the indicator's rays would cross the displaced
+ * plane). */
 int hemo_set_viscosity_ratio(hemo_sim *sim, double ratio);
 
 /* Lees-Edwards boundary along z (Sec. 2.5: the domain is periodic in every
@@ -196,7 +198,8 @@ int hemo_set_viscosity_ratio(hemo_sim *sim, double ratio);
  * first step, on a lattice periodic on every axis without walls, with the
  * default time scales.  Errors: HEMO_ERR_ARG (|U| >= 0.3, walls or a
  * non-periodic axis), HEMO_ERR_STATE (after the first step, twice, time
- * scales other than every step with Euler, recording), HEMO_ERR_OOM.
+ * scales other than every step with Euler, an internal viscosity ratio
+ * other than 1, recording), HEMO_ERR_OOM.
  * hemo_record refuses a simulation with the boundary. */
 int hemo_set_lees_edwards(hemo_sim *sim, double U);
 

@@ -680,6 +680,7 @@ void ora_inside(void *p, unsigned char *out) {
 /* internal viscosity ratio (1 = off) */
 int ora_set_viscosity_ratio(void *p, double ratio) {
     if (!(ratio > 0)) return -1;
+    if (((osim *)p)->le_on && ratio != 1.0) return -1;  /* the rays would cross the displaced plane */
     ((osim *)p)->visc_ratio = ratio;
     return 0;
 }
@@ -691,6 +692,7 @@ int ora_set_lees_edwards(void *p, double U) {
     if (s->nstep != 0) return -1;
     for (int d = 0; d < 3; ++d) if (!s->periodic[d]) return -1;
     for (long n = 0; n < s->N; ++n) if (s->mask[n]) return -1;
+    if (s->visc_ratio != 1.0) return -1;
     s->le_on = 1;
     s->le_U = U;
     return 0;

@@ -1249,6 +1249,8 @@ int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
     if (!(ratio > 0) || !std::isfinite(ratio)) return fail(HEMO_ERR_ARG, "viscosity ratio must be finite and > 0");
     if (!(0.5 + ratio * (s->tau - 0.5) > 0.5)) return fail(HEMO_ERR_ARG, "viscosity ratio gives tau_in <= 1/2");
     if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_viscosity_ratio: not while recording for the reverse sweep");
+    if (s->le && ratio != 1.0)  // the indicator's z-rays would cross the displaced plane
+        return fail(HEMO_ERR_STATE, "hemo_set_viscosity_ratio: not with the Lees-Edwards boundary");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     if (ratio != 1.0 && !s->ind) {
         s->ind = (uint8_t *)dalloc(s, (size_t)s->N);
@@ -1276,6 +1278,7 @@ int hemo_set_lees_edwards(hemo_sim *s, double U) {
     if (s->force_every != 1 || s->integrator != HEMO_EULER)
         return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: needs forces every step with Euler (hemo_set_time_scales)");
     if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: not while recording");
+    if (s->visc_ratio != 1.0) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: not with an internal viscosity ratio other than 1");
     s->f2 = dalloc(s, tsize(s) * Q * (size_t)s->N);
     s->le_aux = dalloc(s, rsize(s) * 4 * 2 * (size_t)s->nx * s->ny);
     s->le_n = (long long *)dalloc(s, sizeof(long long));

@@ -96,22 +96,24 @@ def test_arguments_and_state():
     sim.close()
 
 
-def test_all_optional_terms_together_f64():
-    """Lees-Edwards with the internal viscosity (ratio 5) and the
-    large-deformation terms on, a cell across the plane: FP64 against the
-    oracle with the same settings."""
+def test_with_large_deformation_terms_f64():
+    """Lees-Edwards with the large-deformation terms on, a cell across the
+    plane: FP64 against the oracle with the same settings.  The internal
+    viscosity is refused with the boundary (its rays would cross the
+    displaced plane)."""
     steps = 20
     cfg = _le_config(center=(11.3, 12.1, 23.2), steps=steps)
     cfg.meshes = [dataclasses.replace(mt, k_local=0.05, theta_m=0.5) for mt in cfg.meshes]
     sim = hemo.Simulation.from_config(cfg, 'f64')
     sim.set_lees_edwards(0.02)
-    sim.set_viscosity_ratio(5.0)
+    with pytest.raises(hemo.HemoError) as e:
+        sim.set_viscosity_ratio(5.0)
+    assert e.value.code == hemo.HEMO_ERR_STATE
     sim.step(steps)
     got = sim.get_fields()
     sim.close()
     ref = O.from_config(cfg)
     ref.set_lees_edwards(0.02)
-    ref.set_viscosity_ratio(5.0)
     ref.step(steps)
     exp = ref.get()
     for k in ('u', 'X', 'rho'):

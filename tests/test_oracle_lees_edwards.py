@@ -111,3 +111,11 @@ def test_arguments():
         pass
     else:
         raise AssertionError('a non-periodic z axis must be refused')
+    s = O.OracleSim(4, 4, 4, 1.0, (1, 1, 1))
+    s.set_lees_edwards(0.1)
+    try:
+        s.set_viscosity_ratio(5.0)  # the indicator's rays would cross the displaced plane
+    except ValueError:
+        pass
+    else:
+        raise AssertionError('the internal viscosity must be refused with the boundary')
