@@ -6,8 +6,11 @@
  * One simulation = a D3Q19 BGK plasma lattice (Sec. 2.2) plus triangulated
  * cell membranes coupled to it by the immersed-boundary method (Sec. 2.3),
  * with periodic, resting-wall and moving-wall boundaries (Sec. 2.5) and
- * Euler vertex integration every fluid step (Sec. 2.6).  Every step runs in
- * this library's CUDA kernels for sm_103a; there is no CPU fallback.
+ * Euler vertex integration every fluid step (Sec. 2.6).  Optional: membrane
+ * forces every N fluid steps and the Adams-Bashforth integrator (Sec. 2.6),
+ * nonlinear bending and local area terms (Sec. 2.3), an internal viscosity
+ * ratio (Sec. 1, Sec. 3) and a Lees-Edwards boundary (Sec. 2.5).  Every step
+ * runs in this library's CUDA kernels for sm_103a; there is no CPU fallback.
  *
  * Conventions for every entry point:
  *  - Lattice units: dx = 1, dt = 1.  Lattice arrays are indexed
