@@ -44,7 +44,7 @@ def make_workload(name):
         desc = 'shear box 32^3, 1 RBC x 642 vertices, FP64'
     elif name == 'vessel':
         cfg = I.channel(nx=128, ny=128, nz=512, ncell=4460, seed=20230502, steps=200, platelet_ratio=0.1,
-                        name='vessel', pack_iter=60)
+                        name='vessel', pack_iter=60, exact_iter=0)
         desc = 'channel 128x128x512 (walls y=0,127), 4460 RBC + 446 platelets, 16-bit deviations'
     elif name == 'pipe':
         cfg = I.pipe(pack_iter=20)

@@ -232,7 +232,44 @@ def _ellipsoid_inside(points, center, rot, axes):
     return np.sum((loc / axes[:, None, :]) ** 2, axis=-1)
 
 
-def pack_cells(rng, box_lo, box_hi, periodic, kinds, axes_by_kind, max_iter=400):
+def contact_function(r, rot_a, axes_a, rot_b, axes_b, iters=40):
+    """Perram-Wertheim contact function of pairs of ellipsoids (Perram and
+    Wertheim, J. Comput. Phys. 58, 1985), vectorised over pairs.
+
+    Ellipsoid a is centred at the origin and b at r [n, 3]; rotations
+    [n, 3, 3] (columns = body axes), semi-axes [n, 3].  F = max over lambda in
+    [0, 1] of lambda (1 - lambda) r^T C(lambda)^-1 r with C(lambda) =
+    (1 - lambda) A^-1 + lambda B^-1, A^-1 = R diag(axes^2) R^T: the
+    ellipsoids overlap exactly when F < 1, touch at F = 1, and since F is
+    quadratic in r they touch once the centre distance is scaled by
+    1 / sqrt(F).  The maximum of the single-peaked function of lambda is
+    found by golden-section search (`iters` steps).
+    """
+    ai = np.einsum('nij,nj,nkj->nik', rot_a, axes_a ** 2, rot_a)
+    bi = np.einsum('nij,nj,nkj->nik', rot_b, axes_b ** 2, rot_b)
+
+    def f(lam):
+        c = (1.0 - lam)[:, None, None] * ai + lam[:, None, None] * bi
+        x = np.linalg.solve(c, r[..., None])[..., 0]
+        return lam * (1.0 - lam) * np.einsum('ni,ni->n', r, x)
+
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    lo, hi = np.zeros(len(r)), np.ones(len(r))
+    a, b = hi - g * (hi - lo), lo + g * (hi - lo)
+    fa, fb = f(a), f(b)
+    for _ in range(iters):
+        left = fa > fb                      # the maximum lies in [lo, b]
+        hi = np.where(left, b, hi)
+        lo = np.where(left, lo, a)
+        na = np.where(left, hi - g * (hi - lo), b)
+        nb = np.where(left, a, lo + g * (hi - lo))
+        fa, fb = np.where(left, f(na), fb), np.where(left, fa, f(nb))
+        a, b = na, nb
+    return np.maximum(fa, fb)
+
+
+def pack_cells(rng, box_lo, box_hi, periodic, kinds, axes_by_kind, max_iter=400, exact_iter=0,
+               margin=0.01):
     """Force-bias style packing of bounding ellipsoids (Section 2.4).
 
     Ellipsoids start at random uniform positions and orientations; every
@@ -240,8 +277,16 @@ def pack_cells(rng, box_lo, box_hi, periodic, kinds, axes_by_kind, max_iter=400)
     an amount proportional to its estimated overlap (the mean fraction of one
     ellipsoid's 42 surface samples found inside the other, a proxy for the
     overlap volume), and ellipsoids are pushed back inside the allowed box on
-    non-periodic axes.  Returns (centers [n, 3], rotations [n, 3, 3],
-    number of pairs still overlapping).
+    non-periodic axes.
+
+    The sample proxy misses shallow overlaps.  With `exact_iter` > 0 a second
+    phase follows that detects overlap exactly (`contact_function`) and
+    moves the two centres of every overlapping pair apart along r_j - r_i,
+    each by half the distance that would make the pair touch with a relative
+    gap `margin`, for at most `exact_iter` rounds; the final centres satisfy
+    the box constraints.  Returns (centers [n, 3], rotations [n, 3, 3],
+    number of pairs still overlapping: by the proxy after the first phase
+    alone, exactly when the second phase ran).
     """
     from scipy.spatial import cKDTree
 
@@ -305,6 +350,52 @@ def pack_cells(rng, box_lo, box_hi, periodic, kinds, axes_by_kind, max_iter=400)
             rnd = rng.normal(size=(int(tiny.sum()), 3))
             unit[tiny] = rnd / np.linalg.norm(rnd, axis=1, keepdims=True)
         step = (0.5 * (0.05 + p) * np.minimum(rmax[I], rmax[J]))[:, None] * unit
+        disp = np.zeros_like(centers)
+        np.add.at(disp, I, -step)
+        np.add.at(disp, J, step)
+        centers += disp
+    if exact_iter <= 0 or n < 2:
+        return centers, rots, residual
+    ext = np.sqrt(np.einsum('njk,nk->nj', rots ** 2, axes ** 2))
+    for it in range(exact_iter + 1):
+        for d in range(3):
+            if per[d]:
+                centers[:, d] = box_lo[d] + np.mod(centers[:, d] - box_lo[d], span[d])
+            else:
+                lo = box_lo[d] + ext[:, d]
+                hi = box_hi[d] - ext[:, d]
+                centers[:, d] = np.where(lo > hi, 0.5 * (box_lo[d] + box_hi[d]),
+                                         np.clip(centers[:, d], lo, hi))
+        local = centers - box_lo
+        local = np.where(per, np.mod(local, span), local + 1.5 * span + cutoff)
+        local = np.minimum(local, np.nextafter(boxsize, 0))
+        pairs = cKDTree(local, boxsize=boxsize).query_pairs(cutoff, output_type='ndarray')
+        residual = 0
+        if len(pairs) == 0:
+            break
+        I, J = pairs[:, 0], pairs[:, 1]
+        dvec = centers[J] - centers[I]
+        dvec = np.where(per, dvec - span * np.round(dvec / span), dvec)
+        dist = np.linalg.norm(dvec, axis=1)
+        close = dist < rmax[I] + rmax[J]
+        I, J, dvec, dist = I[close], J[close], dvec[close], dist[close]
+        if len(I) == 0:
+            break
+        F = contact_function(dvec, rots[I], axes[I], rots[J], axes[J])
+        ov = F < 1.0
+        residual = int(ov.sum())
+        if residual == 0 or it == exact_iter:
+            break
+        I, J, F, dvec, dist = I[ov], J[ov], F[ov], dvec[ov], dist[ov]
+        unit = dvec / np.maximum(dist, 1e-9)[:, None]
+        tiny = dist < 1e-6
+        if tiny.any():
+            rnd = rng.normal(size=(int(tiny.sum()), 3))
+            unit[tiny] = rnd / np.linalg.norm(rnd, axis=1, keepdims=True)
+            dist = np.where(tiny, 1e-6, dist)
+            F = np.where(tiny, 1e-12, F)
+        grow = (1.0 + margin) / np.sqrt(np.maximum(F, 1e-12)) - 1.0
+        step = (0.5 * grow * dist)[:, None] * unit
         disp = np.zeros_like(centers)
         np.add.at(disp, I, -step)
         np.add.at(disp, J, step)
@@ -382,7 +473,7 @@ PLATELET_BOUND = (3.6, 3.6, 1.0)
 
 
 def shear_cell(n=32, ncell=1, seed=20230500, steps=500, wall_speed=0.01, tau=1.0,
-               k=(15.0, 80.0, 5.0, 20.0), name='shear'):
+               k=(15.0, 80.0, 5.0, 20.0), name='shear', exact_iter=400):
     """Parallel plates at z=0 and z=n-1 moving at -/+ wall_speed along x."""
     rng = np.random.default_rng(seed)
     kbt = kbt_lattice(1.0)
@@ -394,15 +485,17 @@ def shear_cell(n=32, ncell=1, seed=20230500, steps=500, wall_speed=0.01, tau=1.0
         rots = random_rotation(rng)[None]
     else:
         centers, rots, _ = pack_cells(rng, (0, 0, 1.5), (n, n, n - 2.5), (1, 1, 0),
-                                      [0] * ncell, {0: RBC_BOUND})
+                                      [0] * ncell, {0: RBC_BOUND}, exact_iter=exact_iter)
     return Config(name, n, n, n, tau, (1, 1, 0), mask, wv, np.zeros(3), None, [mt],
                   np.zeros(len(centers), np.int64), centers, rots, steps, seed)
 
 
 def channel(nx=64, ny=64, nz=256, ncell=440, seed=20230501, steps=1000, umax=0.02,
-            tau=1.0, platelet_ratio=0.0, name='channel', pack_iter=400):
+            tau=1.0, platelet_ratio=0.0, name='channel', pack_iter=400, exact_iter=400):
     """Walls at y=0 and y=ny-1, periodic in x and z, body force along x giving
-    centreline velocity `umax` (effective walls at y=0.5 and y=ny-1.5)."""
+    centreline velocity `umax` (effective walls at y=0.5 and y=ny-1.5).
+    `pack_iter` and `exact_iter` bound the two phases of `pack_cells`; the
+    note records the bounding-ellipsoid pairs still overlapping."""
     rng = np.random.default_rng(seed)
     kbt = kbt_lattice(tau)
     mask = plate_mask(nx, ny, nz, axis=1)
@@ -417,7 +510,7 @@ def channel(nx=64, ny=64, nz=256, ncell=440, seed=20230501, steps=1000, umax=0.0
         kinds += [1] * nplt
     bounds = {0: RBC_BOUND, 1: PLATELET_BOUND}
     centers, rots, resid = pack_cells(rng, (0, 2.5, 0), (nx, ny - 3.5, nz), (1, 0, 1),
-                                      kinds, bounds, max_iter=pack_iter)
+                                      kinds, bounds, max_iter=pack_iter, exact_iter=exact_iter)
     u0 = channel_profile(nx, ny, nz, 1, 0.5, ny - 1.5, umax)
     return Config(name, nx, ny, nz, tau, (1, 0, 1), mask, np.zeros((2, 3)), g, u0, meshes,
                   np.array(kinds, np.int64), centers, rots, steps, seed,

@@ -109,7 +109,7 @@ def test_bins_bit_exact():
     """Vertex binning (key, stable permutation, block starts) against the
     oracle on identical positions, including positions exactly on lattice
     planes and wrapped across periodic edges."""
-    cfg = I.channel(nx=40, ny=32, nz=48, ncell=6, seed=11, platelet_ratio=0.5, pack_iter=50)
+    cfg = I.channel(nx=40, ny=32, nz=48, ncell=6, seed=11, platelet_ratio=0.5, pack_iter=50, exact_iter=0)
     sim = hemo.Simulation.from_config(cfg, 'f32')
     rng = np.random.default_rng(2)
     X = I.cell_vertices(cfg)
@@ -162,7 +162,7 @@ def test_coupled_c0_f64_500_steps():
 def test_coupled_channel_f32_200_steps():
     """Small channel suspension with red cells and platelets, FP32 storage
     and arithmetic: velocity relative L2 <= 1e-5 after 200 steps."""
-    cfg = I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100)
+    cfg = I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100, exact_iter=0)
     got, exp = run_both(cfg, 'f32', 200)
     assert rel_l2(got['u'], exp['u']) < F32_TOL
     assert rel_l2(got['X'], exp['X']) < F32_TOL

@@ -23,7 +23,7 @@ def channel_cfg():
 @pytest.fixture(scope='module')
 def vessel_runs():
     cfg = I.channel(nx=128, ny=128, nz=512, ncell=4460, seed=20230502, steps=200, platelet_ratio=0.1,
-                    name='vessel', pack_iter=60)
+                    name='vessel', pack_iter=60, exact_iter=0)
     out = {}
     for prec in ('f64', 'f32', 'f16', 'bf16'):
         sim = hemo.Simulation.from_config(cfg, prec)

@@ -18,7 +18,7 @@ F32_TOL = 1e-5
 
 
 def _channel():
-    return I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100)
+    return I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100, exact_iter=0)
 
 
 CASES = {

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 def test_noalloc_bins_match_simulation_bins_twice():
     import torch
-    cfg = I.channel(nx=40, ny=32, nz=48, ncell=6, seed=11, platelet_ratio=0.5, pack_iter=50)
+    cfg = I.channel(nx=40, ny=32, nz=48, ncell=6, seed=11, platelet_ratio=0.5, pack_iter=50, exact_iter=0)
     sim = hemo.Simulation.from_config(cfg, 'f64')
     _, nv, _, nbins = sim.sizes()
     key = torch.empty(nv, dtype=torch.int32, device='cuda')
