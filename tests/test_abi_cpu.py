@@ -99,3 +99,72 @@ def test_null_handles():
 
 def test_build_entry_point_exists():
     assert callable(__graft_entry__.build) and callable(__graft_entry__.smoke)
+
+
+def test_binding_layouts_match_the_header(tmp_path):
+    """The ctypes structures and constants of the binding against the C
+    header, as a C compiler lays them out (sizes, field offsets, enum
+    values)."""
+    lat = [f for f, _ in hemo.hemo_lattice_desc._fields_]
+    mesh = [f for f, _ in hemo.hemo_mesh_desc._fields_]
+    consts = ['HEMO_OK', 'HEMO_ERR_ARG', 'HEMO_ERR_OOM', 'HEMO_ERR_CUDA', 'HEMO_ERR_NUMERIC', 'HEMO_ERR_DOMAIN',
+              'HEMO_ERR_STATE', 'HEMO_RHO', 'HEMO_U', 'HEMO_VERTS', 'HEMO_FORCES', 'HEMO_CELLSTATS',
+              'HEMO_OPT_STAGED_COLLISION', 'HEMO_EULER', 'HEMO_AB2']
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hemo.h"', 'int main(void) {',
+             'printf("lat %zu\\n", sizeof(hemo_lattice_desc));', 'printf("mesh %zu\\n", sizeof(hemo_mesh_desc));']
+    lines += [f'printf("lat.{f} %zu\\n", offsetof(hemo_lattice_desc, {f}));' for f in lat]
+    lines += [f'printf("mesh.{f} %zu\\n", offsetof(hemo_mesh_desc, {f}));' for f in mesh]
+    lines += [f'printf("{c} %d\\n", (int){c});' for c in consts]
+    lines += ['printf("prec %d %d %d %d\\n", HEMO_F64, HEMO_F32, HEMO_F16DEV, HEMO_BF16DEV);',
+              'printf("phases %d\\n", HEMO_NUM_PHASES);', 'return 0; }']
+    src = tmp_path / 'layout.c'
+    src.write_text('\n'.join(lines) + '\n')
+    exe = tmp_path / 'layout'
+    import subprocess
+    subprocess.run(['gcc', '-std=c99', '-Wall', '-Werror', '-I', os.path.join(ROOT, 'include'), str(src), '-o', str(exe)],
+                   check=True)
+    got = dict(line.split(' ', 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                            text=True).stdout.splitlines())
+    assert int(got['lat']) == C.sizeof(hemo.hemo_lattice_desc)
+    assert int(got['mesh']) == C.sizeof(hemo.hemo_mesh_desc)
+    for f in lat:
+        assert int(got[f'lat.{f}']) == getattr(hemo.hemo_lattice_desc, f).offset, f
+    for f in mesh:
+        assert int(got[f'mesh.{f}']) == getattr(hemo.hemo_mesh_desc, f).offset, f
+    for c in consts:
+        assert int(got[c]) == getattr(hemo, c), c
+    assert [int(x) for x in got['prec'].split()] == [hemo.PRECISIONS[p] for p in ('f64', 'f32', 'f16', 'bf16')]
+    assert int(got['phases']) == len(hemo.Simulation.PHASES)
+
+
+def _c_kind(param):
+    p = param.strip()
+    if '*' in p or '[' in p:
+        return 'ptr'
+    p = re.sub(r'\b(const|enum|struct)\b', '', p).split()
+    if p[:2] == ['long', 'long']:
+        return 'll'
+    return {'int': 'int', 'unsigned': 'uint', 'double': 'double', 'void': 'void'}[p[0]]
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return 'void'
+    if t in (C.c_void_p, C.c_char_p) or hasattr(t, '_type_') and isinstance(t._type_, type):
+        return 'ptr'
+    return {C.c_int: 'int', C.c_uint: 'uint', C.c_double: 'double', C.c_longlong: 'll'}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Argument count and kinds (pointer, int, unsigned, long long, double)
+    and the return kind of every prototype in the header against the
+    binding's ctypes declarations."""
+    src = re.sub(r'/\*.*?\*/', '', open(os.path.join(ROOT, 'include', 'hemo.h')).read(), flags=re.S)
+    protos = re.findall(r'\b(int|void|const char\s*\*)\s*(hemo_[a-z0-9_]+)\s*\(([^)]*)\)\s*;', src)
+    assert len(protos) == len(header_functions())
+    L = hemo.lib()
+    for ret, name, params in protos:
+        fn = getattr(L, name)
+        want = [] if params.strip() in ('', 'void') else [_c_kind(p) for p in params.split(',')]
+        assert [_ctypes_kind(t) for t in fn.argtypes] == want, name
+        assert _ctypes_kind(fn.restype) == ('ptr' if '*' in ret else _c_kind(ret)), name
