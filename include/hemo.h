@@ -121,7 +121,11 @@ typedef struct {
 } hemo_mesh_desc;
 
 /* Create a simulation: allocates the lattice, sets every fluid node to rest
- * (f_i = w_i), builds the wall links.  *out receives the handle. */
+ * (f_i = w_i), builds the wall links.  *out receives the handle, or NULL on
+ * failure.  HEMO_ERR_ARG for sizes below 1 or nx*ny*nz >= 2^30, tau <= 1/2
+ * or NaN, an unknown precision, periodic flags other than 0/1, wall mask
+ * values above 3, or only one of alloc / release; HEMO_ERR_OOM when a
+ * device allocation fails. */
 int hemo_create_lattice(const hemo_lattice_desc *desc, hemo_sim **out);
 
 /* Set the populations of every fluid node to the equilibrium (Sec. 2.2)

@@ -1026,7 +1026,7 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
     *out = nullptr;
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(HEMO_ERR_ARG, "lattice sizes must be >= 1");
     const long long N = (long long)d->nx * d->ny * d->nz;
-    if (N > 0x7fffffffLL / 2) return fail(HEMO_ERR_ARG, "lattice too large (more than 2^30 nodes)");
+    if (N > 0x7fffffffLL / 2) return fail(HEMO_ERR_ARG, "lattice too large (2^30 nodes or more)");
     if (!(d->tau > 0.5)) return fail(HEMO_ERR_ARG, "tau must exceed 1/2");
     if (d->precision < HEMO_F64 || d->precision > HEMO_BF16DEV) return fail(HEMO_ERR_ARG, "unknown precision");
     for (int k = 0; k < 3; ++k)

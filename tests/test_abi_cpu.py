@@ -62,6 +62,8 @@ def _desc(**kw):
     (dict(nx=0), 'sizes'),
     (dict(tau=0.5), 'tau'),
     (dict(precision=7), 'precision'),
+    (dict(tau=float('nan')), 'tau'),
+    (dict(nx=1024, ny=1024, nz=1024), 'too large'),  # 2^30 nodes: one past the limit
 ])
 def test_create_rejects_bad_arguments(kw, msg):
     L = hemo.lib()
@@ -82,6 +84,31 @@ def test_create_rejects_bad_mask_and_flags():
     d.periodic[1] = 2
     assert L.hemo_create_lattice(C.byref(d), C.byref(h)) == hemo.HEMO_ERR_ARG
     assert L.hemo_create_lattice(None, C.byref(h)) == hemo.HEMO_ERR_ARG
+
+
+def test_create_rejects_half_an_allocator():
+    L = hemo.lib()
+    h = C.c_void_p()
+    d = _desc()
+    d.alloc = hemo.ALLOC_FN(lambda n, ctx: None)
+    assert L.hemo_create_lattice(C.byref(d), C.byref(h)) == hemo.HEMO_ERR_ARG
+    assert 'alloc and release' in L.hemo_last_error().decode()
+    assert not h.value
+
+
+def test_noalloc_binning_limits():
+    """The allocation-free binning refuses sizes beyond its fixed scratch
+    (1,048,576 vertices, 131,072 blocks of 8^3) and missing outputs before
+    touching the GPU."""
+    L = hemo.lib()
+    per = (C.c_int * 3)(1, 1, 1)
+    dummy = C.c_void_p(16)  # never dereferenced: the arguments are refused first
+    args = lambda nv, nx, ny, nz, start=dummy: (dummy, nv, nx, ny, nz, per, dummy, dummy, start, None)  # noqa: E731
+    assert L.hemo_bin_vertices_noalloc(*args(1048577, 64, 64, 64)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, 8 * 64, 8 * 64, 8 * 33)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, 64, 64, 64, start=None)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(-1, 64, 64, 64)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, 0, 64, 64)) == hemo.HEMO_ERR_ARG
 
 
 def test_null_handles():
