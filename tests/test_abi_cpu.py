@@ -96,6 +96,43 @@ def test_create_rejects_half_an_allocator():
     assert not h.value
 
 
+def test_allocation_failure_is_oom():
+    """A device memory provider that refuses makes create return
+    HEMO_ERR_OOM with no handle (no CUDA call is reached)."""
+    L = hemo.lib()
+    h = C.c_void_p()
+    calls = []
+    d = _desc()
+    d.alloc = hemo.ALLOC_FN(lambda n, ctx: calls.append(n) or None)
+    d.release = hemo.FREE_FN(lambda p, ctx: None)
+    assert L.hemo_create_lattice(C.byref(d), C.byref(h)) == hemo.HEMO_ERR_OOM
+    assert not h.value and len(calls) >= 1
+
+
+@pytest.mark.skipif(__import__('torch').cuda.is_available(), reason='hands the library placeholder device addresses')
+def test_partial_allocation_failure_releases_everything():
+    """The provider grants the first allocations (placeholder addresses the
+    library never dereferences: the lattice's allocations all come before
+    its first CUDA call) and refuses the last: every granted block is
+    released exactly once."""
+    L = hemo.lib()
+    granted, released = [], []
+
+    def alloc(n, ctx):
+        if len(granted) == 5:
+            return None
+        granted.append(0x10000 * (len(granted) + 1))
+        return granted[-1]
+
+    d = _desc()
+    d.alloc = hemo.ALLOC_FN(alloc)
+    d.release = hemo.FREE_FN(lambda p, ctx: released.append(p))
+    h = C.c_void_p()
+    assert L.hemo_create_lattice(C.byref(d), C.byref(h)) == hemo.HEMO_ERR_OOM
+    assert not h.value
+    assert sorted(released) == granted
+
+
 def test_noalloc_binning_limits():
     """The allocation-free binning refuses sizes beyond its fixed scratch
     (1,048,576 vertices, 131,072 blocks of 8^3) and missing outputs before
