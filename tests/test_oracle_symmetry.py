@@ -1,5 +1,5 @@
 """Pin of the oracle's whole coupled step: equivariance under the symmetries
-of the cubic lattice.
+of the cubic lattice and under integer translations of a periodic box.
 
 D3Q19 (Sec. 2.2), the BGK collision with Guo forcing, halfway bounce-back,
 the 4-point Peskin kernel (a product of even 1-D kernels, Sec. 2.3) and the
@@ -171,3 +171,18 @@ def test_a_planted_axis_swap_is_caught():
     ref = _run(cfg, 4)
     got = _run(bad, 4)
     assert rel_l2(got['u'], _field(ref['u'], A, b, cfg.nx, True)) > 1e-3
+
+
+def test_periodic_translation():
+    """An integer translation of everything on the periodic box translates
+    the result (the wrap of stencils and streaming across every edge)."""
+    cfg = _periodic_case()
+    n, shift = cfg.nx, np.array([7, -5, 13])
+    moved = dataclasses.replace(cfg, centers=cfg.centers + shift,
+                                init_velocity=np.roll(cfg.init_velocity, shift=tuple(shift[::-1]), axis=(0, 1, 2)))
+    ref, got = _run(cfg, 8), _run(moved, 8)
+    roll = lambda a: np.roll(a, shift=tuple(shift[::-1]), axis=(0, 1, 2))  # noqa: E731
+    assert rel_l2(got['u'], roll(ref['u'])) < 1e-13
+    assert rel_l2(got['rho'], roll(ref['rho'])) < 1e-15
+    assert _periodic_close(got['X'], ref['X'] + shift, n, (1, 1, 1), 1e-13)
+    assert forces_close(got['Fv'], ref['Fv'], cfg)
