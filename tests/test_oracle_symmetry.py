@@ -186,3 +186,41 @@ def test_periodic_translation():
     assert rel_l2(got['rho'], roll(ref['rho'])) < 1e-15
     assert _periodic_close(got['X'], ref['X'] + shift, n, (1, 1, 1), 1e-13)
     assert forces_close(got['Fv'], ref['Fv'], cfg)
+
+
+# Lees-Edwards along z (Sec. 2.5): a reflection of x or of z turns the image
+# above the box into one displaced and moving the other way, i.e. the same
+# boundary with -U; reflecting y, or both x and z, keeps U.
+LE_TRANSFORMS = {
+    'reflect_x': (((0, 1, 2), (-1, 1, 1)), -1.0),
+    'reflect_y': (((0, 1, 2), (1, -1, 1)), 1.0),
+    'reflect_z': (((0, 1, 2), (1, 1, -1)), -1.0),
+    'rotate_y_180': (((0, 1, 2), (-1, 1, -1)), 1.0),
+}
+
+
+@pytest.mark.parametrize('name', sorted(LE_TRANSFORMS))
+def test_lees_edwards(name):
+    """A red cell across the bottom plane in a sheared periodic box."""
+    cfg = dataclasses.replace(_periodic_case(), centers=np.array([[9.3, 10.6, 1.2]]))
+    (perm, sign), flip = LE_TRANSFORMS[name]
+    A, b = _map(perm, sign, cfg.nx)
+    U = 0.03
+
+    def run(c, u_le):
+        s = O.from_config(c)
+        s.set_lees_edwards(u_le)
+        s.step(9)
+        out = s.get()
+        s.close()
+        return out
+
+    ref, got = run(cfg, U), run(_transform(cfg, A, b), flip * U)
+    n = cfg.nx
+    assert rel_l2(got['u'], _field(ref['u'], A, b, n, True)) < 1e-12
+    assert rel_l2(got['rho'], _field(ref['rho'], A, b, n, False)) < 1e-14
+    # positions: the images differ by the plane's displacement, so compare x
+    # modulo the box only where no plane was crossed (this cell's centroid
+    # stays inside the box)
+    assert _periodic_close(got['X'], ref['X'] @ A.T + b, n, (1, 1, 0), 1e-13)
+    assert forces_close(got['Fv'], ref['Fv'] @ A.T, cfg)
