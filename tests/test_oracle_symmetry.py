@@ -224,3 +224,29 @@ def test_lees_edwards(name):
     # stays inside the box)
     assert _periodic_close(got['X'], ref['X'] @ A.T + b, n, (1, 1, 0), 1e-13)
     assert forces_close(got['Fv'], ref['Fv'] @ A.T, cfg)
+
+
+@pytest.mark.parametrize('name', ['reflect_x', 'reflect_z', 'rotate_z_90', 'cycle_xyz'])
+def test_internal_viscosity(name):
+    """Viscosity ratio 5 inside the cell: the inside/outside indicator and
+    the per-node relaxation move with the configuration (its tie rules only
+    matter for nodes exactly on the membrane, which these positions avoid)."""
+    cfg = _periodic_case()
+    A, b = _map(*TRANSFORMS[name], cfg.nx)
+
+    def run(c):
+        s = O.from_config(c)
+        s.set_viscosity_ratio(5.0)
+        ins0 = s.inside().copy()
+        s.step(8)
+        out = s.get()
+        out['inside0'] = ins0
+        s.close()
+        return out
+
+    ref, got = run(cfg), run(_transform(cfg, A, b))
+    n = cfg.nx
+    assert ref['inside0'].sum() > 50
+    assert np.array_equal(got['inside0'], _field(ref['inside0'], A, b, n, False))
+    assert rel_l2(got['u'], _field(ref['u'], A, b, n, True)) < 1e-12
+    assert _periodic_close(got['X'], ref['X'] @ A.T + b, n, (1, 1, 1), 1e-13)
