@@ -356,6 +356,45 @@ def test_deformation_index():
         assert abs(O.deformation_index(v * [s, 1, 1]) - (s - 1) / (s + 1)) < 1e-12
 
 
+def test_deformation_loss_closed_form():
+    """The loss of the differentiation form (mean Taylor deformation index
+    plus mean squared centroid drift) in closed form: a round cell
+    (icosphere, DI = 0) and a cell stretched by diag(s, 1, 1)
+    (DI = (s - 1)/(s + 1)), each moved rigidly after placement: cell c by a
+    rotation about its centroid and a translation d_c.  DI is invariant
+    under the rigid motion and the centroid moves by d_c from where the
+    cells were placed, so loss = ((s - 1)/(s + 1) + |d_0|^2 + |d_1|^2) / 2.
+    A wrong sign, a missing 1/ncell or the wrong reference centroid fails."""
+    v, t = I.icosphere(3)
+    s = 1.6
+    params = [1.0, 1.0, 1.0, 1.0, 1e-7, 0.015, 3.0]
+    sim = O.OracleSim(64, 64, 64, 1.0, (1, 1, 1))
+    sim.add_mesh(v * 5.0, t, params)
+    sim.add_mesh(v * [5.0 * s, 5.0, 5.0], t, params)
+    centers = np.array([[20.0, 30.0, 31.0], [40.0, 22.0, 35.0]])
+    sim.add_cells(0, centers[:1], np.eye(3)[None])
+    sim.add_cells(1, centers[1:], np.eye(3)[None])
+    X0 = np.concatenate([v * 5.0 + centers[0], v * [5.0 * s, 5.0, 5.0] + centers[1]])
+    di1 = (s - 1) / (s + 1)
+    assert abs(sim.loss() - di1 / 2) < 1e-12  # no drift at placement
+    rng = np.random.default_rng(3)
+    d = np.array([[1.5, -0.75, 2.0], [-3.0, 0.5, 0.25]])
+    nv = len(v)
+    X = X0.copy()
+    for c in range(2):
+        R = I.random_rotation(rng)
+        Xc = X0[c * nv:(c + 1) * nv]
+        X[c * nv:(c + 1) * nv] = (Xc - centers[c]) @ R.T + centers[c] + d[c]
+    sim.set_vertices(X)
+    expect = (di1 + (d ** 2).sum()) / 2
+    assert abs(sim.loss() - expect) < 1e-12 * max(1.0, expect)
+    # only the drift changes with a further translation of one cell
+    X[:nv] += [0.0, 0.0, 1.0]
+    sim.set_vertices(X)
+    expect2 = (di1 + (d ** 2).sum() - d[0, 2] ** 2 + (d[0, 2] + 1.0) ** 2) / 2
+    assert abs(sim.loss() - expect2) < 1e-12 * max(1.0, expect2)
+
+
 # ---------------------------------------------------------------------------
 # integer work: binning, wall links (brute force)
 # ---------------------------------------------------------------------------
