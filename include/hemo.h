@@ -350,11 +350,17 @@ int hemo_get_phase_times(hemo_sim *sim, float *ms, int *kernels_per_step);
  * implicit device synchronisation is not acceptable, tools that hold vertex
  * positions in their own buffers and no simulation handle).
  *
- * Bins `nv` absolute vertex positions exactly as hemo_get_bins does (same
- * kernels, same key rule: 8^3 lattice blocks of floor(X), wrapped on periodic
- * axes, clamped to the edge block on the others; perm = stable sort by key;
- * start = first position of each block, nbins + 1 entries) and allocates
- * nothing.  verts: device, nv*3 double; periodic: host, 3 ints; key, perm:
+ * Bins `nv` absolute FP64 vertex positions with the key rule and the
+ * counting-sort kernels of hemo_get_bins (8^3 lattice blocks of floor(X),
+ * wrapped on periodic axes, clamped to the edge block on the others; perm =
+ * stable sort by key; start = first position of each block, nbins + 1
+ * entries) and allocates nothing.  Given the positions hemo_get_fields
+ * returns (HEMO_VERTS), the result equals hemo_get_bins bit for bit for a
+ * lattice without the Lees-Edwards boundary (that boundary adds a bin).  The
+ * step's own binning floors X formed from the centroid and an offset in the
+ * arithmetic precision (and, between two force evaluations, from a two-float
+ * centroid), which can fall on the other side of a lattice plane than the
+ * FP64 absolute position does.  verts: device, nv*3 double; periodic: host, 3 ints; key, perm:
  * device, nv int32; start: device, nbins + 1 int32, nbins = ceil(nx/8) *
  * ceil(ny/8) * ceil(nz/8); cuda_stream: cudaStream_t or NULL.  Asynchronous:
  * outputs are ready when the stream reaches the end of the call's work.

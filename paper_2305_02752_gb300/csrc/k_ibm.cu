@@ -1110,8 +1110,12 @@ extern "C" int hemo_bin_vertices_noalloc(const double *verts, int nv, int nx, in
         return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: bad sizes or null pointer");
     if (nv > NOALLOC_MAX_VERTICES)
         return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: more than 1,048,576 vertices");
-    const long long nb0 = (nx + BLK - 1) / BLK, nb1 = (ny + BLK - 1) / BLK, nb2 = (nz + BLK - 1) / BLK;
-    if (nb0 * nb1 * nb2 > NOALLOC_MAX_BINS)
+    // block counts in 64 bits; each factor is checked before the product so
+    // that no intermediate can overflow
+    const long long nb0 = (long long)nx / BLK + (nx % BLK != 0), nb1 = (long long)ny / BLK + (ny % BLK != 0),
+                    nb2 = (long long)nz / BLK + (nz % BLK != 0);
+    if (nb0 > NOALLOC_MAX_BINS || nb1 > NOALLOC_MAX_BINS || nb2 > NOALLOC_MAX_BINS || nb0 * nb1 > NOALLOC_MAX_BINS ||
+        nb0 * nb1 * nb2 > NOALLOC_MAX_BINS)
         return noalloc_fail(HEMO_ERR_ARG, "hemo_bin_vertices_noalloc: more than 131,072 lattice blocks of 8^3 nodes");
     const int nbins = (int)(nb0 * nb1 * nb2);
     int dev = 0;

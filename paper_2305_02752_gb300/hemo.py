@@ -116,15 +116,40 @@ def check(rc):
     return rc
 
 
-def bin_vertices_noalloc(verts, dims, periodic, key, perm, start, stream=None):
+def bin_vertices_noalloc(verts, dims, periodic, key, perm, start, stream=None, _require_cuda=True):
     """Bin absolute vertex positions without any allocation by the library
     (for callers that cannot let it allocate device memory).  verts: CUDA
     float64 tensor [nv, 3]; key, perm: CUDA int32 [nv]; start: CUDA int32
-    [nbins + 1], all caller-owned.  Same binning as Simulation.bins();
-    asynchronous on `stream` (default: current stream)."""
+    [nbins + 1] with nbins = ceil(nx/8) ceil(ny/8) ceil(nz/8), all
+    caller-owned and contiguous.  Same binning as Simulation.bins() for
+    absolute FP64 positions; asynchronous on `stream` (default: current
+    stream).  The C ABI receives bare pointers and cannot check the buffers,
+    so their types, devices and sizes are checked here (HemoError with
+    HEMO_ERR_ARG)."""
     import torch
-    nx, ny, nz = dims
+    nx, ny, nz = (int(x) for x in dims)
+    nb = [(n + 7) // 8 for n in (nx, ny, nz)]
+    nbins = nb[0] * nb[1] * nb[2]
+
+    def need(ok, what):
+        if not ok:
+            raise HemoError(HEMO_ERR_ARG, f'bin_vertices_noalloc: {what}')
+
+    def tensor(t, name, dtype, min_numel):
+        need(isinstance(t, torch.Tensor), f'{name} must be a torch tensor')
+        need(t.dtype == dtype, f'{name} must be {dtype}')
+        need(t.is_contiguous(), f'{name} must be contiguous')
+        need(not _require_cuda or t.is_cuda, f'{name} must be a CUDA tensor')
+        need(t.numel() >= min_numel, f'{name} needs at least {min_numel} entries')
+
+    need(isinstance(verts, torch.Tensor) and verts.dim() == 2 and verts.shape[1] == 3, 'verts must be [nv, 3]')
+    nv = int(verts.shape[0])
+    tensor(verts, 'verts', torch.float64, 3 * nv)
+    tensor(key, 'key', torch.int32, nv)
+    tensor(perm, 'perm', torch.int32, nv)
+    tensor(start, 'start', torch.int32, nbins + 1)
     per = np.ascontiguousarray(periodic, dtype=np.int32)
+    need(per.shape == (3,), 'periodic must have 3 entries')
     st = (stream or torch.cuda.current_stream()).cuda_stream
     check(lib().hemo_bin_vertices_noalloc(verts.data_ptr(), int(verts.shape[0]), nx, ny, nz, per.ctypes.data,
                                           key.data_ptr(), perm.data_ptr(), start.data_ptr(), st))

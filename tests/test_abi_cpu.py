@@ -146,6 +146,43 @@ def test_noalloc_binning_limits():
     assert L.hemo_bin_vertices_noalloc(*args(10, 64, 64, 64, start=None)) == hemo.HEMO_ERR_ARG
     assert L.hemo_bin_vertices_noalloc(*args(-1, 64, 64, 64)) == hemo.HEMO_ERR_ARG
     assert L.hemo_bin_vertices_noalloc(*args(10, 0, 64, 64)) == hemo.HEMO_ERR_ARG
+    # block counts whose product would overflow 64 bits, or one axis alone
+    # beyond the limit (the sizes are checked axis by axis before the product)
+    big = 2 ** 31 - 1
+    assert L.hemo_bin_vertices_noalloc(*args(10, big, big, big)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, 2 ** 30, 2 ** 30, 2 ** 30)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, big, 1, 1)) == hemo.HEMO_ERR_ARG
+    assert L.hemo_bin_vertices_noalloc(*args(10, 1, 1, 8 * 131073)) == hemo.HEMO_ERR_ARG
+
+
+def test_noalloc_binding_checks_buffers():
+    """The binding is the only place that can check the caller's buffers
+    (the C ABI takes bare pointers): wrong dtypes, host tensors,
+    non-contiguous or too-small buffers are refused with HEMO_ERR_ARG
+    before the library is called."""
+    import torch
+    nv, dims = 10, (16, 16, 16)
+    nbins = 8
+    good = dict(verts=torch.zeros((nv, 3), dtype=torch.float64), key=torch.zeros(nv, dtype=torch.int32),
+                perm=torch.zeros(nv, dtype=torch.int32), start=torch.zeros(nbins + 1, dtype=torch.int32))
+    bad_cases = [
+        dict(verts=torch.zeros((nv, 3), dtype=torch.float32)),
+        dict(verts=torch.zeros((nv, 2), dtype=torch.float64)),
+        dict(verts=torch.zeros((3, nv), dtype=torch.float64).t()),
+        dict(key=torch.zeros(nv - 1, dtype=torch.int32)),
+        dict(perm=torch.zeros(nv, dtype=torch.int64)),
+        dict(start=torch.zeros(nbins, dtype=torch.int32)),
+    ]
+    for case in bad_cases:
+        a = dict(good, **case)
+        with pytest.raises(hemo.HemoError) as e:
+            hemo.bin_vertices_noalloc(a['verts'], dims, (1, 1, 1), a['key'], a['perm'], a['start'],
+                                      _require_cuda=False)
+        assert e.value.code == hemo.HEMO_ERR_ARG, case
+    # host tensors are refused too (the kernels need device memory)
+    with pytest.raises(hemo.HemoError) as e:
+        hemo.bin_vertices_noalloc(good['verts'], dims, (1, 1, 1), good['key'], good['perm'], good['start'])
+    assert e.value.code == hemo.HEMO_ERR_ARG
 
 
 def test_null_handles():
