@@ -13,6 +13,22 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def assert_close(got, exp, tol, what=''):
+    """Parity check of one field: relative L2 error <= tol (the measure the
+    tolerances are stated in) and, so that an error confined to a few
+    elements (next to a wall, on a bin face, across a periodic or shifted
+    boundary) is not diluted by the whole-field norm, the largest
+    per-element error <= tol times the field's largest magnitude."""
+    a = np.asarray(got, float)
+    b = np.asarray(exp, float)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    err = rel_l2(a, b)
+    assert err < tol, (what, 'relative L2', err, tol)
+    scale = np.abs(b).max() if b.size else 0.0
+    worst = np.abs(a - b).max() if b.size else 0.0
+    assert worst <= tol * (scale if scale > 0 else 1.0), (what, 'max abs', worst, tol * scale)
+
+
 def direction_map():
     """perm with oracle_index = perm[library_index] (same velocity vector)."""
     from paper_2305_02752_gb300 import hemo

@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2305_02752_gb300 import hemo
 from paper_2305_02752_gb300 import inputs as I
-from tests.helpers import forces_close, rel_l2, run_both, small_cell_shear
+from tests.helpers import assert_close, forces_close, rel_l2, run_both, small_cell_shear
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def test_single_cell_f64(steps):
     cfg = _with_terms(small_cell_shear(steps=steps))
     got, exp = run_both(cfg, 'f64', steps)
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
     # the terms matter at this tolerance
     ref = O.from_config(small_cell_shear(steps=steps))
@@ -42,15 +42,15 @@ def test_each_term_alone_f64(which):
     cfg = _with_terms(cfg, k_local=0.05 if which == 'local' else 0.0, theta_m=0.5 if which == 'bend' else 0.0)
     got, exp = run_both(cfg, 'f64', 15)
     for k in ('u', 'X'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
 
 
 def test_channel_f32_200_steps():
     cfg = _with_terms(I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100, exact_iter=0))
     got, exp = run_both(cfg, 'f32', 200)
-    assert rel_l2(got['u'], exp['u']) < F32_TOL
-    assert rel_l2(got['X'], exp['X']) < F32_TOL
+    assert_close(got['u'], exp['u'], F32_TOL)
+    assert_close(got['X'], exp['X'], F32_TOL)
 
 
 def test_record_refuses_the_optional_terms():

@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2305_02752_gb300 import hemo
 from paper_2305_02752_gb300 import inputs as I
-from tests.helpers import direction_map, forces_close, rel_l2, run_both, small_cell_shear
+from tests.helpers import assert_close, direction_map, forces_close, rel_l2, run_both, small_cell_shear
 
 pytestmark = pytest.mark.gpu
 
@@ -47,9 +47,9 @@ def test_lattice_only_f64(steps, dims):
     exp = ref.get()
     fo = ref.populations()[..., direction_map()]
     fluid = mask == 0
-    assert rel_l2(fg[fluid], fo[fluid]) < F64_TOL
-    assert rel_l2(got['rho'][fluid], exp['rho'][fluid]) < F64_TOL
-    assert rel_l2(got['u'], exp['u']) < F64_TOL
+    assert_close(fg[fluid], fo[fluid], F64_TOL)
+    assert_close(got['rho'][fluid], exp['rho'][fluid], F64_TOL)
+    assert_close(got['u'], exp['u'], F64_TOL)
 
 
 def test_fully_periodic_no_walls_f64():
@@ -64,8 +64,8 @@ def test_fully_periodic_no_walls_f64():
     ref.set_velocity(u0)
     ref.step(11)
     exp = ref.get()
-    assert rel_l2(got['u'], exp['u']) < F64_TOL
-    assert rel_l2(got['rho'], exp['rho']) < F64_TOL
+    assert_close(got['u'], exp['u'], F64_TOL)
+    assert_close(got['rho'], exp['rho'], F64_TOL)
 
 
 def test_wall_links_bit_exact():
@@ -134,9 +134,9 @@ def test_coupled_small_f64(steps):
     cfg = small_cell_shear(steps=steps)
     got, exp = run_both(cfg, 'f64', steps)
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
-    assert rel_l2(got['cellstats'], exp['cellstats']) < F64_TOL
+    assert_close(got['cellstats'], exp['cellstats'], F64_TOL)
 
 
 def test_coupled_cell_across_periodic_edge_f64():
@@ -144,7 +144,7 @@ def test_coupled_cell_across_periodic_edge_f64():
     cfg = small_cell_shear(n=24, steps=15, center=[0.3, 23.6, 11.5])
     got, exp = run_both(cfg, 'f64', 15)
     for k in ('u', 'X'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
 
 
@@ -154,9 +154,9 @@ def test_coupled_c0_f64_500_steps():
     cfg = I.shear_cell()
     got, exp = run_both(cfg, 'f64', 500)
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
-    assert rel_l2(got['cellstats'], exp['cellstats']) < F64_TOL
+    assert_close(got['cellstats'], exp['cellstats'], F64_TOL)
 
 
 def test_coupled_channel_f32_200_steps():
@@ -164,8 +164,8 @@ def test_coupled_channel_f32_200_steps():
     and arithmetic: velocity relative L2 <= 1e-5 after 200 steps."""
     cfg = I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100, exact_iter=0)
     got, exp = run_both(cfg, 'f32', 200)
-    assert rel_l2(got['u'], exp['u']) < F32_TOL
-    assert rel_l2(got['X'], exp['X']) < F32_TOL
+    assert_close(got['u'], exp['u'], F32_TOL)
+    assert_close(got['X'], exp['X'], F32_TOL)
 
 
 def test_mass_conservation_f64():

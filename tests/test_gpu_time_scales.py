@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2305_02752_gb300 import hemo
 from paper_2305_02752_gb300 import inputs as I
-from tests.helpers import forces_close, rel_l2, small_cell_shear
+from tests.helpers import assert_close, forces_close, rel_l2, small_cell_shear
 
 pytestmark = pytest.mark.gpu
 
@@ -42,9 +42,9 @@ def test_coupled_small_f64(force_every, integrator, steps):
     cfg = small_cell_shear(steps=steps)
     got, exp = run_both(cfg, 'f64', steps, force_every, integrator)
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
-    assert rel_l2(got['cellstats'], exp['cellstats']) < F64_TOL
+    assert_close(got['cellstats'], exp['cellstats'], F64_TOL)
 
 
 def test_switch_after_odd_step_count_f64():
@@ -53,7 +53,7 @@ def test_switch_after_odd_step_count_f64():
     cfg = small_cell_shear(n=24, steps=26, center=[0.3, 23.6, 11.5])
     got, exp = run_both(cfg, 'f64', 26, 4, 'ab2', switch_at=7)
     for k in ('u', 'X'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
 
 
@@ -63,7 +63,7 @@ def test_c0_f64_500_steps_ab2_every_4():
     cfg = I.shear_cell()
     got, exp = run_both(cfg, 'f64', 500, 4, 'ab2')
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
 
 
@@ -71,8 +71,8 @@ def test_channel_f32_200_steps_ab2_every_4():
     """Small channel suspension (red cells and platelets), FP32."""
     cfg = I.channel(nx=32, ny=32, nz=64, ncell=10, seed=3, platelet_ratio=0.5, pack_iter=100, exact_iter=0)
     got, exp = run_both(cfg, 'f32', 200, 4, 'ab2')
-    assert rel_l2(got['u'], exp['u']) < F32_TOL
-    assert rel_l2(got['X'], exp['X']) < F32_TOL
+    assert_close(got['u'], exp['u'], F32_TOL)
+    assert_close(got['X'], exp['X'], F32_TOL)
 
 
 @pytest.mark.parametrize('precision', ['f32', 'bf16'])

@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2305_02752_gb300 import hemo
 from paper_2305_02752_gb300 import inputs as I
-from tests.helpers import forces_close, rel_l2, small_cell_shear
+from tests.helpers import assert_close, forces_close, rel_l2, small_cell_shear
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,7 @@ def test_coupled_ratio5_f64(steps):
     ref.step(steps)
     exp = ref.get()
     for k in ('u', 'X', 'rho'):
-        assert rel_l2(got[k], exp[k]) < F64_TOL, k
+        assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
     # the ratio changes the flow at this tolerance
     plain = O.from_config(cfg)
@@ -86,8 +86,8 @@ def test_channel_ratio5_f32_200_steps():
     ref.set_viscosity_ratio(5.0)
     ref.step(200)
     exp = ref.get()
-    assert rel_l2(got['u'], exp['u']) < F32_TOL
-    assert rel_l2(got['X'], exp['X']) < F32_TOL
+    assert_close(got['u'], exp['u'], F32_TOL)
+    assert_close(got['X'], exp['X'], F32_TOL)
 
 
 def test_ratio_one_is_the_default_and_arguments():

@@ -197,6 +197,39 @@ def test_packer():
     assert (c2[:, 1] - ext[:, 1] >= 2.5 - 1e-9).all() and (c2[:, 1] + ext[:, 1] <= 45.5 + 1e-9).all()
 
 
+def test_packer_cylinder():
+    """With the cylinder constraint every bounding ellipsoid lies inside the
+    cylinder about the x axis (dense surface samples within the radius), in
+    both phases, and a moderately dense pipe is packed free of overlap."""
+    kinds = [0] * 14
+    cy = cz = 20.0
+    radius = 18.0
+    lo, hi, per = np.array([0.0, cy - radius, cz - radius]), np.array([60.0, cy + radius, cz + radius]), (1, 0, 0)
+    axes = np.tile(np.array(I.RBC_BOUND), (14, 1))
+    samples, _ = I.icosphere(4)
+    for exact in (0, 400):
+        c, r, resid = I.pack_cells(np.random.default_rng(5), lo, hi, per, kinds, {0: I.RBC_BOUND},
+                                   max_iter=100, exact_iter=exact, cylinder=(cy, cz, radius))
+        surf = c[:, None, :] + np.einsum('pk,nk,njk->npj', samples, axes, r)
+        rad = np.hypot(surf[..., 1] - cy, surf[..., 2] - cz)
+        assert rad.max() <= radius + 1e-9, exact
+        if exact:
+            assert resid == 0
+            assert _overlap_pairs(c, r, axes, per, hi - lo, samples) == 0
+
+
+def test_pipe_placement_inside_the_wall():
+    """The pipe workload (1000 x 208 x 208, 19,600 red cells): every cell's
+    bounding ellipsoid lies at least 3 nodes inside the voxelised wall."""
+    cy = (208 - 1) / 2.0
+    c, r, _ = I.pipe_placement(np.random.default_rng(20230504), 1000, cy, cy, 97.0, 19600, 1, 0)
+    assert len(c) == 19600
+    axes = np.tile(np.array(I.RBC_BOUND), (len(c), 1))
+    samples, _ = I.icosphere(2)
+    surf = c[:, None, :] + np.einsum('pk,nk,njk->npj', samples, axes, r)
+    assert np.hypot(surf[..., 1] - cy, surf[..., 2] - cy).max() <= 97.0 + 1e-9
+
+
 def _red_cell_overlaps(cfg):
     """Pairs of red cells with a vertex of one inside the other's biconcave
     body (|z| < T(r) in its frame, the Evans-Fung profile)."""
