@@ -51,7 +51,8 @@ enum hemo_status {
 /* Storage of the populations.  F64: FP64 everything (parity path).  F32:
  * populations stored as FP32 deviations f_i - w_i, FP32 arithmetic.
  * F16DEV / BF16DEV: populations stored as FP16 / BF16 deviations f_i - w_i,
- * FP32 arithmetic.  In every mode per-cell area and volume sums and cell
+ * less a per-row reference equilibrium (hemo_set_velocity), FP32
+ * arithmetic.  In every mode per-cell area and volume sums and cell
  * centroids are FP64; vertex positions are the FP64 centroid plus an offset
  * in the arithmetic precision. */
 enum hemo_precision { HEMO_F64 = 0, HEMO_F32 = 1, HEMO_F16DEV = 2, HEMO_BF16DEV = 3 };
@@ -87,6 +88,19 @@ typedef struct {
  * kernel; 16-bit storage only (ignored otherwise).  The results are the
  * same.  Off by default: the per-node kernel is the faster of the two. */
 enum { HEMO_OPT_STAGED_COLLISION = 1u };
+
+/* HEMO_OPT_NODE_COLLISION: with 16-bit storage, collide one node per thread
+ * instead of two (the two-node kernels need nx even).  The results are the
+ * same bits; the option exists to compare the two. */
+enum { HEMO_OPT_NODE_COLLISION = 2u };
+
+/* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the staged
+ * collision (HEMO_OPT_STAGED_COLLISION, 16-bit storage, odd steps).  Its
+ * kernel first waits, at most 2 ms, on a barrier that no copy completes; the
+ * wait runs out, the kernel returns without colliding, and the step reports
+ * HEMO_ERR_CUDA ("a copy pipeline wait timed out") through the device status,
+ * as a real stalled copy would.  Not for production runs. */
+enum { HEMO_OPT_TEST_STALLED_WAIT = 4u };
 
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
  * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
@@ -130,7 +144,13 @@ int hemo_create_lattice(const hemo_lattice_desc *desc, hemo_sim **out);
 
 /* Set the populations of every fluid node to the equilibrium (Sec. 2.2)
  * with rho = 1 and the given velocity.  u: any, nx*ny*nz*3 doubles, or NULL
- * for rest.  Only valid before the first step. */
+ * for rest.  Only valid before the first step.  With 16-bit storage the
+ * mean x-velocity of each row (x-line) of u over its fluid nodes becomes
+ * that row's reference: every population of direction i with c_i,x != 0 is
+ * stored minus the equilibrium deviation w_i (3 c_i,x U + 3 U^2) of the
+ * row's reference velocity (U, 0, 0), so that the 2-byte values carry the
+ * departure from that profile (none without u, and none with the
+ * Lees-Edwards boundary). */
 int hemo_set_velocity(hemo_sim *sim, const double *u);
 
 /* Add `ncells` cells of a new mesh type: vertex v of cell c is placed at
@@ -280,6 +300,27 @@ int hemo_set_vertices(hemo_sim *sim, const double *verts);
  * position of block k (nbins + 1 entries).  Same kernels as the step.
  * key, perm: any, nv int32; start: any, nbins+1 int32.  Synchronises. */
 int hemo_get_bins(hemo_sim *sim, int32_t *key, int32_t *perm, int32_t *start);
+
+/* ---- checkpoint and resume -------------------------------------------- */
+
+/* Sec. 2.6: a run is paused, its state kept, and continued.  The state is
+ * what changes from step to step: the populations (in the in-place layout
+ * of the step count's parity; with 16-bit storage also the rows' reference
+ * they are stored against), the velocity field, the FP64 cell centroids and
+ * the vertex offsets, the membrane forces (held between force evaluations),
+ * the previous vertex velocity (Adams-Bashforth), the step count and the
+ * time-scale setting, and the Lees-Edwards step counter.  Lattice, walls,
+ * parameters and cells are not part of it: load it into a simulation created
+ * and filled with cells the same way (same sizes, precision and boundary),
+ * which then continues bit for bit as the saved one would have.
+ * hemo_state_bytes: *bytes (host) receives the size.  hemo_save_state /
+ * hemo_load_state: buf any (host or device of the simulation's GPU),
+ * caller-owned, at least that size; both synchronise.  Errors: HEMO_ERR_ARG
+ * (null, too small, a state of another simulation), HEMO_ERR_STATE while
+ * recording for hemo_backward. */
+int hemo_state_bytes(hemo_sim *sim, size_t *bytes);
+int hemo_save_state(hemo_sim *sim, void *buf, size_t bytes);
+int hemo_load_state(hemo_sim *sim, const void *buf, size_t bytes);
 
 /* ---- differentiation form --------------------------------------------- */
 

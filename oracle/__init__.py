@@ -47,6 +47,7 @@ def lib():
         L = C.CDLL(_LIB)
         L.ora_d3q19.argtypes = [_ip, _dp, _ip]
         L.ora_equilibrium.argtypes = [C.c_double, _dp, _dp]
+        L.ora_storage_reference.argtypes = [C.c_double, _dp]
         L.ora_phi.argtypes = [C.c_double]
         L.ora_phi.restype = C.c_double
         L.ora_build_edges.argtypes = [C.c_int, C.c_int, _ip, _ip]
@@ -122,6 +123,14 @@ def d3q19():
 def equilibrium(rho, u):
     out = np.zeros(19)
     lib().ora_equilibrium(float(rho), _c(u), out)
+    return out
+
+
+def storage_reference(U):
+    """K_i of the 16-bit storage form for a row reference velocity (U, 0, 0):
+    f_i^eq(1, (U, 0, 0)) - w_i where c_i,x != 0, else 0 (oracle order)."""
+    out = np.zeros(19)
+    lib().ora_storage_reference(float(U), out)
     return out
 
 

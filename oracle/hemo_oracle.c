@@ -146,6 +146,19 @@ void ora_equilibrium(double rho, const double *u, double *feq) {
     }
 }
 
+/* Reference of the 16-bit storage form for a row whose reference velocity
+ * is (U, 0, 0): for the directions with c_x != 0 the equilibrium deviation
+ * f_i^eq(1, (U, 0, 0)) - w_i, zero for the others (the storage form keeps
+ * f_i - w_i - K_i in 2 bytes; the oracle computes in FP64 and uses this only
+ * to state what the stored values are). */
+void ora_storage_reference(double U, double *K) {
+    build_tables();
+    const double u[3] = {U, 0.0, 0.0};
+    double feq[Q];
+    ora_equilibrium(1.0, u, feq);
+    for (int i = 0; i < Q; ++i) K[i] = C[i][0] != 0 ? feq[i] - W[i] : 0.0;
+}
+
 /* Peskin's 4-point kernel (Peskin 2002), piecewise definition */
 double ora_phi(double r) {
     double a = fabs(r);

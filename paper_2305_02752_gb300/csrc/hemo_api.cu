@@ -128,6 +128,7 @@ struct hemo_sim {
     uint64_t *links = nullptr;
     void *F = nullptr, *u = nullptr;
     unsigned options = 0;
+    float2 *rref = nullptr;       // 16-bit storage: the rows' reference (P, M), see k_lattice.cu
     // staged collision (tiles of wall-free rows), see plan_rows
     int2 *rtiles = nullptr;
     int *erows = nullptr;
@@ -266,6 +267,9 @@ View<R> make_view(hemo_sim *s) {
     v.tile_smem = s->tile_smem;
     v.erows = s->erows;
     v.nerows = s->nerows;
+    v.rref = s->rref;
+    v.node_pairs = tsize(s) == 2 && (s->nx % 2) == 0 && !(s->options & HEMO_OPT_NODE_COLLISION);
+    v.stalled_wait_test = (s->options & HEMO_OPT_TEST_STALLED_WAIT) ? 1 : 0;
     for (int d = 0; d < 3; ++d) {
         v.g[d] = R(s->g[d]);
         v.uw[0][d] = R(0);
@@ -1073,8 +1077,11 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
     s->F = dalloc(s, rsize(s) * 3 * (size_t)N);
     s->u = dalloc(s, rsize(s) * 3 * (size_t)N);
     s->status = (unsigned *)dalloc(s, sizeof(unsigned));
-    if (!s->f || !s->ntype || !s->links || !s->F || !s->u || !s->status)
+    if (tsize(s) == 2) s->rref = (float2 *)dalloc(s, sizeof(float2) * (size_t)s->ny * s->nz);
+    if (!s->f || !s->ntype || !s->links || !s->F || !s->u || !s->status || (tsize(s) == 2 && !s->rref))
         return bail(fail(HEMO_ERR_OOM, "device allocation of the lattice failed"));
+    if (s->rref && cudaMemsetAsync(s->rref, 0, sizeof(float2) * (size_t)s->ny * s->nz, s->stream) != cudaSuccess)
+        return bail(fail(HEMO_ERR_CUDA, "memset failed"));
     if (cudaHostAlloc((void **)&s->status_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -1110,6 +1117,10 @@ int hemo_set_velocity(hemo_sim *s, const double *u) {
         if (rc) return rc;
         HEMO_CU(cudaMemcpyAsync(s->staging, u, sizeof(double) * 3 * (size_t)s->N, cudaMemcpyDefault, s->stream));
         ud = (const double *)s->staging;
+    }
+    if (s->rref && !s->le) {  // 16-bit storage: the rows' mean x-velocity becomes the reference
+        if (ud) launch_row_reference(make_view<float>(s), ud, s->rref, s->stream);
+        else HEMO_CU(cudaMemsetAsync(s->rref, 0, sizeof(float2) * (size_t)s->ny * s->nz, s->stream));
     }
     if (is_f64(s)) launch_init_equilibrium<double>(make_view<double>(s), s->precision, ud, s->stream);
     else launch_init_equilibrium<float>(make_view<float>(s), s->precision, ud, s->stream);
@@ -1284,6 +1295,10 @@ int hemo_set_lees_edwards(hemo_sim *s, double U) {
     s->le_n = (long long *)dalloc(s, sizeof(long long));
     if (!s->f2 || !s->le_aux || !s->le_n) return fail(HEMO_ERR_OOM, "Lees-Edwards buffers");
     HEMO_CU(cudaMemsetAsync(s->le_n, 0, sizeof(long long), s->stream));
+    if (s->rref) {  // the two-array kernels store plain deviations: re-store without the reference
+        launch_reencode(make_view<float>(s), s->precision, s->rref, nullptr, s->stream);
+        HEMO_CU(cudaMemsetAsync(s->rref, 0, sizeof(float2) * (size_t)s->ny * s->nz, s->stream));
+    }
     s->le = true;
     s->le_U = U;
     for (int k = 0; k < hemo_sim::NGRAPH; ++k)
@@ -1398,6 +1413,121 @@ int hemo_get_populations(hemo_sim *s, double *f) {
     else launch_populations_out<float>(make_view<float>(s), s->precision, layout, (double *)s->staging, s->stream);
     HEMO_CU(cudaGetLastError());
     if ((rc = copy_out(s, f, s->staging, sizeof(double) * Q * (size_t)s->N))) return rc;
+    return hemo_sync(s);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume (Sec. 2.6: the simulation is paused, its state kept
+// and the run continued).  The state is what changes from step to step; it
+// is written as a header followed by the raw device buffers, so a resumed
+// run continues with the same bits.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct StateHeader {
+    uint64_t magic;          // STATE_MAGIC
+    int64_t N, nv, ncell, precision, le;
+    int64_t steps_done, ts_origin;
+    int64_t force_every, integrator, have_prev;
+    int64_t sections;        // number of buffers that follow
+};
+constexpr uint64_t STATE_MAGIC = 0x314154534f4d4548ull;  // the bytes "HEMOSTA1" in little-endian order
+
+// the buffers of the dynamic state, in order: (device pointer, bytes)
+std::vector<std::pair<void *, size_t>> state_sections(hemo_sim *s) {
+    const size_t rs = rsize(s), nv = (size_t)s->nv, nc = (size_t)s->ncell;
+    std::vector<std::pair<void *, size_t>> v;
+    v.push_back({s->f, tsize(s) * Q * (size_t)s->N});   // populations in the in-place layout of the step parity
+    v.push_back({s->u, rs * 3 * (size_t)s->N});         // velocity of the last step
+    if (s->rref) v.push_back({s->rref, sizeof(float2) * (size_t)s->ny * s->nz});  // 16-bit: the reference they are stored against
+    if (nc) {
+        v.push_back({s->ctr, sizeof(double) * 3 * nc});  // FP64 centroids
+        v.push_back({s->csp, rs * 6 * nc});             // centroid of the last re-base (held-force steps)
+        v.push_back({s->off, rs * 3 * nv});             // vertex offsets
+        v.push_back({s->Fv, rs * 3 * nv});              // membrane forces (held between evaluations)
+        v.push_back({s->Uprev, rs * 3 * nv});           // previous vertex velocity (Adams-Bashforth)
+    }
+    if (s->le) v.push_back({s->le_n, sizeof(long long)});  // Lees-Edwards step counter
+    return v;
+}
+
+size_t state_size(hemo_sim *s) {
+    size_t b = sizeof(StateHeader);
+    for (auto &x : state_sections(s)) b += x.second;
+    return b;
+}
+
+int state_ready(hemo_sim *s, const char *who) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (s->rec) return fail(HEMO_ERR_STATE, std::string(who) + ": not while recording for the reverse sweep");
+    return HEMO_OK;
+}
+
+}  // namespace
+
+int hemo_state_bytes(hemo_sim *s, size_t *bytes) {
+    if (!bytes) return fail(HEMO_ERR_ARG, "hemo_state_bytes: null pointer");
+    int rc = state_ready(s, "hemo_state_bytes");
+    if (rc) return rc;
+    *bytes = state_size(s);
+    return HEMO_OK;
+}
+
+int hemo_save_state(hemo_sim *s, void *buf, size_t bytes) {
+    int rc = state_ready(s, "hemo_save_state");
+    if (rc) return rc;
+    if (!buf) return fail(HEMO_ERR_ARG, "hemo_save_state: null buffer");
+    if (bytes < state_size(s)) return fail(HEMO_ERR_ARG, "hemo_save_state: buffer smaller than hemo_state_bytes");
+    StateHeader h{};
+    h.magic = STATE_MAGIC;
+    h.N = s->N;
+    h.nv = s->nv;
+    h.ncell = s->ncell;
+    h.precision = s->precision;
+    h.le = s->le;
+    h.steps_done = s->steps_done;
+    h.ts_origin = s->ts_origin;
+    h.force_every = s->force_every;
+    h.integrator = s->integrator;
+    h.have_prev = s->have_prev;
+    const auto sec = state_sections(s);
+    h.sections = (int64_t)sec.size();
+    HEMO_CU(cudaMemcpyAsync(buf, &h, sizeof h, cudaMemcpyDefault, s->stream));
+    char *p = (char *)buf + sizeof h;
+    for (auto &x : sec) {
+        HEMO_CU(cudaMemcpyAsync(p, x.first, x.second, cudaMemcpyDefault, s->stream));
+        p += x.second;
+    }
+    return hemo_sync(s);  // (the header is read from the stack before returning)
+}
+
+int hemo_load_state(hemo_sim *s, const void *buf, size_t bytes) {
+    int rc = state_ready(s, "hemo_load_state");
+    if (rc) return rc;
+    if (!buf) return fail(HEMO_ERR_ARG, "hemo_load_state: null buffer");
+    if (bytes < sizeof(StateHeader)) return fail(HEMO_ERR_ARG, "hemo_load_state: buffer too small");
+    StateHeader h{};
+    HEMO_CU(cudaMemcpy(&h, buf, sizeof h, cudaMemcpyDefault));
+    if (h.magic != STATE_MAGIC) return fail(HEMO_ERR_ARG, "hemo_load_state: not a saved state");
+    if (h.N != s->N || h.nv != s->nv || h.ncell != s->ncell || h.precision != s->precision || h.le != (int64_t)s->le)
+        return fail(HEMO_ERR_ARG, "hemo_load_state: the state belongs to a simulation of other sizes, precision or boundary");
+    const auto sec = state_sections(s);
+    if (h.sections != (int64_t)sec.size() || bytes < state_size(s))
+        return fail(HEMO_ERR_ARG, "hemo_load_state: buffer size does not match the simulation");
+    if (h.force_every < 1 || (h.integrator != HEMO_EULER && h.integrator != HEMO_AB2) || h.steps_done < 0)
+        return fail(HEMO_ERR_ARG, "hemo_load_state: corrupt header");
+    const char *p = (const char *)buf + sizeof h;
+    for (auto &x : sec) {
+        HEMO_CU(cudaMemcpyAsync(x.first, p, x.second, cudaMemcpyDefault, s->stream));
+        p += x.second;
+    }
+    s->steps_done = h.steps_done;
+    s->ts_origin = h.ts_origin;
+    s->force_every = (int)h.force_every;
+    s->integrator = (int)h.integrator;
+    s->have_prev = h.have_prev != 0;
     return hemo_sync(s);
 }
 

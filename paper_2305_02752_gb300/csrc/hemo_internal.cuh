@@ -160,6 +160,12 @@ template <typename R> struct View {
     int ntiles, tile_rows, tile_stages, tile_grid, tile_smem;
     const int *erows;
     int nerows;
+    // 16-bit storage: per row (x-line, index y + ny z) the reference values
+    // (P, M) of the stored populations (see k_lattice.cu); all zero when no
+    // reference is set.  Null for 4- and 8-byte storage.
+    const float2 *rref;
+    int node_pairs;            // 16-bit storage: collide two nodes per thread (nx even)
+    int stalled_wait_test;     // staged collision: first wait on a barrier nothing completes (HEMO_OPT_TEST_STALLED_WAIT)
     // a buffer whose contents are dead: the kernel drops its full 128-byte
     // lines from L2 without writing them back (null / 0 = nothing to drop)
     void *dead;
@@ -202,6 +208,11 @@ void launch_le_advance(long long *n, cudaStream_t st);
 // allows the staged collision kernels of a precision `bytes` of dynamic shared memory
 cudaError_t set_tile_smem_limit(int precision, int bytes);
 template <typename R> void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st);
+// 16-bit storage: the rows' reference (P, M) from a velocity field ([n][3]
+// double, device) and the re-storing of natural-order populations from one
+// reference table to another (null = zero reference)
+void launch_row_reference(const View<float> &v, const double *u0, float2 *rref, cudaStream_t st);
+void launch_reencode(const View<float> &v, int precision, const float2 *from, const float2 *to, cudaStream_t st);
 template <typename R> void launch_init_equilibrium(const View<R> &v, int precision, const double *u_dev, cudaStream_t st);
 template <typename R> void launch_populations_out(const View<R> &v, int precision, int parity, double *out, cudaStream_t st);
 template <typename R> void launch_rho_out(const View<R> &v, int precision, int parity, R *out, cudaStream_t st);

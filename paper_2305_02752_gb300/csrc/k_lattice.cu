@@ -17,6 +17,10 @@
 // Bounce-back: a population whose target x + c_i is a wall is written back
 // into slot opp(i) of its own node (odd step) or left in slot opp(i) with the
 // moving-wall term applied (even step), where the next odd step reads it.
+//
+// 16-bit storage subtracts a per-row reference equilibrium from what it
+// stores (see row_refs below) and collides two nodes per thread
+// (collide_pair_kernel).
 #include <type_traits>
 
 #include "lattice_core.cuh"
@@ -25,26 +29,108 @@ namespace hemo {
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// Reference equilibrium of 16-bit storage.
+//
+// A 2-byte population keeps 8 (BF16) or 11 (FP16) significant bits of what
+// is stored, so what is stored should be small.  Each row (x-line, index
+// r = y + ny z) has a reference x-velocity U_r, and a population of
+// direction i with cx_i != 0 held in a slot of row r is stored as
+//   f_i - w_i - K_i(r),   K_i(r) = w_i (3 cx_i U_r + 3 U_r^2),
+// which is f_i^eq(1, (U_r, 0, 0)) - w_i for those directions; for cx_i = 0
+// that equilibrium deviation is -1.5 w_i U_r^2, small, and nothing is
+// subtracted.  In a flow near the rows' reference profile what is stored
+// is the non-equilibrium part and the departure from the profile.  Per row
+// the table holds P = (3 U + 3 U^2) / 18 and M = (-3 U + 3 U^2) / 18 (the
+// axis weight; diagonals take half).  The reference belongs to the slot
+// that holds the value: the kernel that writes a slot and the one that
+// reads it use the same row's reference, so decoding is exact but for the
+// FP32 rounding of one addition.  In natural order slot i of node n holds
+// direction i arriving at n (row of n); after an even step slot opp(i) of n
+// holds direction i leaving n (row of n).  With a zero table (no reference)
+// the stored values are the plain deviations f_i - w_i.
+// ---------------------------------------------------------------------------
+template <typename T> struct HasRef { static constexpr bool value = sizeof(T) == 2; };
+
+// K_i of a row from its (P, M)
+__device__ __forceinline__ float ref_dir(int i, float2 pm) {
+    if (cx(i) == 0) return 0.f;
+    const float k = cx(i) > 0 ? pm.x : pm.y;
+    return (cy(i) != 0 || cz(i) != 0) ? 0.5f * k : k;
+}
+
+// (P, M) of a node's row and of the rows y -/+ 1 and z -/+ 1 (wrapped: a
+// wrapped row is used only across a periodic edge, a non-periodic edge
+// being a wall link)
+struct RowRefs {
+    float2 own, ym, yp, zm, zp;
+    // the row displaced by (dy, dz), at most one of them nonzero
+    __device__ __forceinline__ float2 at(int dy, int dz) const {
+        return dy > 0 ? yp : (dy < 0 ? ym : (dz > 0 ? zp : (dz < 0 ? zm : own)));
+    }
+};
+
+template <typename T, typename R>
+__device__ __forceinline__ RowRefs row_refs(const View<R> &v, int y, int z, bool neighbours) {
+    RowRefs r;
+    if constexpr (HasRef<T>::value) {
+        const float2 *t = v.rref;
+        const int ny = v.ny, row = y + ny * z;
+        r.own = t[row];
+        if (neighbours) {
+            r.ym = t[row + (y == 0 ? ny - 1 : -1)];
+            r.yp = t[row + (y == ny - 1 ? 1 - ny : 1)];
+            r.zm = t[z == 0 ? row + ny * (v.nz - 1) : row - ny];
+            r.zp = t[z == v.nz - 1 ? y : row + ny];
+        } else {
+            r.ym = r.yp = r.zm = r.zp = r.own;
+        }
+    } else {
+        r.own = r.ym = r.yp = r.zm = r.zp = make_float2(0.f, 0.f);
+    }
+    return r;
+}
+
+template <typename T, typename R>
+__device__ __forceinline__ RowRefs row_refs_of(const View<R> &v, int n, bool neighbours) {
+    const int r = n / v.nx;
+    return row_refs<T>(v, r % v.ny, r / v.ny, neighbours);
+}
+
+// decode / encode one stored value with the reference `ref` of its slot
+template <typename T, typename R>
+__device__ __forceinline__ R dec(T s, float ref) {
+    if constexpr (HasRef<T>::value) return Store<T>::ld(s) + ref;
+    else return Store<T>::ld(s);
+}
+template <typename T, typename R>
+__device__ __forceinline__ T enc(R q, float ref) {
+    if constexpr (HasRef<T>::value) return Store<T>::st(q - ref);
+    else return Store<T>::st(q);
+}
+
 // Read the 19 populations arriving at node n.  LAYOUT 0: natural order (slot
 // i of n).  LAYOUT 1: after an even step (slot opp(i) of n - c_i, or slot i
 // of n when n - c_i is a wall).  LINKS false: no wall among the neighbours
 // (lk is not read).  I: the index type of the population array, 32-bit
 // unsigned when 19 N < 2^32 (fewer registers and address instructions).
 template <typename T, typename R, int LAYOUT, bool LINKS, typename I = size_t>
-__device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, const Nbr &o, R d[Q]) {
+__device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, const Nbr &o, const RowRefs &rr,
+                                          R d[Q]) {
     const T *f = (const T *)v.f;
     const I N = (I)v.N;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (LAYOUT == 0) {
-            d[i] = Store<T>::ld(f[(I)i * N + (I)n]);
+            d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(i, rr.own));
         } else {
             if (i == 0) {
-                d[i] = Store<T>::ld(f[n]);
-            } else if (LINKS && link_code(lk, opp(i))) {
-                d[i] = Store<T>::ld(f[(I)i * N + (I)n]);
-            } else {
-                d[i] = Store<T>::ld(f[(I)opp(i) * N + (I)(n + o.of(-cx(i), -cy(i), -cz(i)))]);
+                d[i] = dec<T, R>(f[n], 0.f);
+            } else if (LINKS && link_code(lk, opp(i))) {  // slot i holds direction opp(i) leaving n
+                d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(opp(i), rr.own));
+            } else {  // direction i leaving n - c_i
+                d[i] = dec<T, R>(f[(I)opp(i) * N + (I)(n + o.of(-cx(i), -cy(i), -cz(i)))],
+                                 ref_dir(i, rr.at(-cy(i), -cz(i))));
             }
         }
     }
@@ -54,9 +140,9 @@ __device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, 
 // reading and writing the global array directly; LINKS false for a node
 // without wall neighbours (most of them: that path carries no wall terms)
 template <typename T, typename R, int PARITY, bool LINKS, typename I, bool VISC = true>
-__device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr &o, uint64_t lk) {
+__device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr &o, uint64_t lk, const RowRefs &rr) {
     R d[Q], p[Q];
-    load_pops<T, R, PARITY, LINKS, I>(v, n, lk, o, d);
+    load_pops<T, R, PARITY, LINKS, I>(v, n, lk, o, rr, d);
     const size_t N = (size_t)v.N;
     R rho, ux, uy, uz;
     const R om = (VISC && v.ind && v.ind[n]) ? v.omega_in : v.omega;  // inside a cell: internal viscosity
@@ -77,13 +163,13 @@ __device__ __forceinline__ void collide_core(const View<R> &v, int n, const Nbr 
             q -= R(6) * R(wgt(i)) * rho * cw;
         }
         const I NI = (I)N;
-        if (PARITY == 0) {
-            f[(I)opp(i) * NI + (I)n] = Store<T>::st(q);
+        if (PARITY == 0) {  // slot opp(i) of n: direction i leaving n
+            f[(I)opp(i) * NI + (I)n] = enc<T, R>(q, ref_dir(i, rr.own));
         } else {
-            if (code)
-                f[(I)opp(i) * NI + (I)n] = Store<T>::st(q);
-            else
-                f[(I)i * NI + (I)(n + o.of(cx(i), cy(i), cz(i)))] = Store<T>::st(q);
+            if (code)  // bounced back: direction opp(i) arriving at n
+                f[(I)opp(i) * NI + (I)n] = enc<T, R>(q, ref_dir(opp(i), rr.own));
+            else  // direction i arriving at n + c_i
+                f[(I)i * NI + (I)(n + o.of(cx(i), cy(i), cz(i)))] = enc<T, R>(q, ref_dir(i, rr.at(cy(i), cz(i))));
         }
     }
 }
@@ -93,8 +179,9 @@ template <typename T, typename R, int PARITY, typename I, bool VISC>
 __device__ __forceinline__ void collide_at(const View<R> &v, int n, int x, int y, int z) {
     const uint8_t nt = v.ntype[n];
     if (nt & 0x7f) return;  // wall node
-    if (nt & 0x80) collide_core<T, R, PARITY, true, I, VISC>(v, n, nbr_at(v, x, y, z), v.links[n]);
-    else collide_core<T, R, PARITY, false, I, VISC>(v, n, nbr_at(v, x, y, z), 0ull);
+    const RowRefs rr = row_refs<T>(v, y, z, PARITY == 1);
+    if (nt & 0x80) collide_core<T, R, PARITY, true, I, VISC>(v, n, nbr_at(v, x, y, z), v.links[n], rr);
+    else collide_core<T, R, PARITY, false, I, VISC>(v, n, nbr_at(v, x, y, z), 0ull, rr);
 }
 
 // any node given by its index (walls included), one code path for nodes
@@ -103,8 +190,9 @@ template <typename T, typename R, int PARITY, typename I>
 __device__ __forceinline__ void collide_node(const View<R> &v, int n) {
     const uint8_t nt = v.ntype[n];
     if (nt & 0x7f) return;  // wall node
-    const int r = n / v.nx;
-    collide_core<T, R, PARITY, true, I>(v, n, nbr_at(v, n % v.nx, r % v.ny, r / v.ny), (nt & 0x80) ? v.links[n] : 0ull);
+    const int r = n / v.nx, y = r % v.ny, z = r / v.ny;
+    collide_core<T, R, PARITY, true, I>(v, n, nbr_at(v, n % v.nx, y, z), (nt & 0x80) ? v.links[n] : 0ull,
+                                        row_refs<T>(v, y, z, PARITY == 1));
 }
 
 // all nodes, grid of NODE_BX x NODE_BY blocks over (x, y, z)
@@ -166,14 +254,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// waits for the phase with the given parity; gives up after about a second
-__device__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// waits for the phase with the given parity; gives up after limit_ns
+// (about a second by default)
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns = 1000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int k = 0; k < 256; ++k)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -281,9 +370,20 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
     drop_dead_lines(v);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) mbar_init(bar + s, TILE_COPIES);
+        if (v.stalled_wait_test) mbar_init(bar + S, 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (v.stalled_wait_test) {
+        // failure-path test: wait on a barrier that nothing arrives at; the
+        // bounded wait runs out and the kernel reports it without touching
+        // the populations (no copy has been issued)
+        const bool ok = threadIdx.x == 0 ? mbar_wait(bar + S, 0u, 2000000ull) : true;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(v.status, ST_TIMEOUT);
+            return;
+        }
+    }
     if (issuer)
         for (int it = 0; it < S - 1 && tile_of(it) < ntiles; ++it) issue_load(it);
 
@@ -312,9 +412,14 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
             auto at = [&](int i) -> T & {
                 return (PARITY == 0 ? b0 : (cx(i) > 0 ? bm : (cx(i) < 0 ? bp : b0)))[i * TNM];
             };
+            // the node's row and its neighbours' references: direction i
+            // arrives from the row shifted by -c_i and leaves to the row
+            // shifted by +c_i
+            const int grow = tl.x + j;
+            const RowRefs rr = row_refs<T>(v, grow % v.ny, grow / v.ny, true);
             R d[Q], p[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = Store<T>::ld(at(i));
+            for (int i = 0; i < Q; ++i) d[i] = dec<T, R>(at(i), PARITY ? ref_dir(i, rr.at(-cy(i), -cz(i))) : ref_dir(i, rr.own));
             R rho, ux, uy, uz;
             const R om = (v.ind && v.ind[(size_t)tl.x * nx + L]) ? v.omega_in : v.omega;
             bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], om, p, rho, ux, uy, uz);
@@ -327,7 +432,8 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
             }
             // outgoing direction i takes the place of incoming opp(i)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) at(opp(i)) = Store<T>::st(p[i]);
+            for (int i = 0; i < Q; ++i)
+                at(opp(i)) = enc<T, R>(p[i], PARITY ? ref_dir(i, rr.at(cy(i), cz(i))) : ref_dir(i, rr.own));
         }
         fence_async_smem();
         __syncthreads();
@@ -350,9 +456,9 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
 // post-streaming velocity u = (sum f c + F/2) / rho with the force just
 // applied; LAYOUT as in load_pops.  Flags non-finite or |u| > 0.3.
 template <typename T, typename R, int LAYOUT, bool LINKS, typename I>
-__device__ __forceinline__ void moments_core(const View<R> &v, int n, const Nbr &o, uint64_t lk) {
+__device__ __forceinline__ void moments_core(const View<R> &v, int n, const Nbr &o, uint64_t lk, const RowRefs &rr) {
     R d[Q];
-    load_pops<T, R, LAYOUT, LINKS, I>(v, n, lk, o, d);
+    load_pops<T, R, LAYOUT, LINKS, I>(v, n, lk, o, rr, d);
     R drho = R(0), mx = R(0), my = R(0), mz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -388,8 +494,266 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_kernel(View<R> v) {
         }
         return;
     }
-    if (nt & 0x80) moments_core<T, R, LAYOUT, true, I>(v, n, nbr_at(v, x, y, z), v.links[n]);
-    else moments_core<T, R, LAYOUT, false, I>(v, n, nbr_at(v, x, y, z), 0ull);
+    const RowRefs rr = row_refs<T>(v, y, z, LAYOUT == 1);
+    if (nt & 0x80) moments_core<T, R, LAYOUT, true, I>(v, n, nbr_at(v, x, y, z), v.links[n], rr);
+    else moments_core<T, R, LAYOUT, false, I>(v, n, nbr_at(v, x, y, z), 0ull, rr);
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit storage, two nodes per thread.
+//
+// With 2-byte populations a thread that collides one node keeps 38 bytes of
+// loads in flight, too few to cover the memory latency at the occupancy the
+// collision allows.  Here lane L of a warp takes the nodes x0 = 64 b + 2 L
+// and x0 + 1 of one row (b the warp's chunk of the row; nx even, so that the
+// pair is one aligned 32-bit word of every direction's range): 19 loads and
+// 19 stores of 4 bytes for the two nodes.  Where a direction's reads or
+// writes are one node off the pair (cx_i != 0 on odd steps, and for the
+// velocity after an even step), a lane takes its own aligned word and the
+// neighbouring lane's by a warp shuffle; the first and the last lane of a
+// chunk fetch or store the one value that lies in the neighbouring chunk
+// with a 2-byte access (x wrapped at the row's ends).  A warp whose nodes
+// are not all fluid without wall links collides them one by one
+// (collide_at).  The arithmetic per node is the per-node kernel's, so the
+// results are the same bits.
+// ---------------------------------------------------------------------------
+template <typename T> struct Bits;
+template <> struct Bits<__half> {
+    static __device__ __forceinline__ __half of(unsigned short b) { return __ushort_as_half(b); }
+    static __device__ __forceinline__ unsigned short to(__half h) { return __half_as_ushort(h); }
+};
+template <> struct Bits<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 of(unsigned short b) { return __ushort_as_bfloat16(b); }
+    static __device__ __forceinline__ unsigned short to(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
+};
+// the low / high 16-bit value of a pair word, decoded with reference ref
+template <typename T> __device__ __forceinline__ float dec_lo(unsigned w, float ref) {
+    return Store<T>::ld(Bits<T>::of((unsigned short)(w & 0xffffu))) + ref;
+}
+template <typename T> __device__ __forceinline__ float dec_hi(unsigned w, float ref) {
+    return Store<T>::ld(Bits<T>::of((unsigned short)(w >> 16))) + ref;
+}
+template <typename T> __device__ __forceinline__ unsigned enc16(float q, float ref) {
+    return Bits<T>::to(Store<T>::st(q - ref));
+}
+template <typename T> __device__ __forceinline__ unsigned ld_pair(const T *p) { return *reinterpret_cast<const unsigned *>(p); }
+template <typename T> __device__ __forceinline__ unsigned ld_one(const T *p) { return Bits<T>::to(*p); }
+template <typename T> __device__ __forceinline__ void st_pair(T *p, unsigned w) { *reinterpret_cast<unsigned *>(p) = w; }
+template <typename T> __device__ __forceinline__ void st_one(T *p, unsigned b) { *p = Bits<T>::of((unsigned short)b); }
+
+constexpr int PAIR_X = 2 * NODE_BX;  // nodes of a row per warp
+
+// The 19 pair words arriving at nodes x0, x0 + 1 (low half: node x0).
+// LAYOUT 0: natural order; 1: after an even step (direction i from slot
+// opp(i) of the nodes x - c_i).  row0: index of the row's node x = 0;
+// o: the row's y and z neighbour offsets; xb, xa: the nodes before x0 and
+// after x0 + 1 (wrapped).
+template <typename T, int LAYOUT, typename I>
+__device__ __forceinline__ void load_pair_words(const View<float> &v, int n0, int row0, int xb, int xa, const Nbr &o,
+                                                bool act, bool first, bool last, unsigned w[Q]) {
+    const T *f = (const T *)v.f;
+    const I N = (I)v.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (LAYOUT == 0 || cx(i) == 0) {
+            const int roff = LAYOUT == 0 ? 0 : o.of(0, -cy(i), -cz(i));
+            const int slot = LAYOUT == 0 ? i : opp(i);
+            w[i] = act ? ld_pair(f + (I)slot * N + (I)(n0 + roff)) : 0u;
+        } else {
+            const int roff = o.of(0, -cy(i), -cz(i));
+            const T *src = f + (I)opp(i) * N;
+            const unsigned own = act ? ld_pair(src + (I)(n0 + roff)) : 0u;  // values at x0, x0 + 1
+            if (cx(i) > 0) {  // from x0 - 1 and x0
+                const unsigned left = __shfl_up_sync(0xffffffffu, own, 1);
+                const unsigned vb = first ? (act ? ld_one(src + (I)(row0 + roff + xb)) : 0u) : (left >> 16);
+                w[i] = vb | (own << 16);
+            } else {  // from x0 + 1 and x0 + 2
+                const unsigned right = __shfl_down_sync(0xffffffffu, own, 1);
+                const unsigned va = last ? (act ? ld_one(src + (I)(row0 + roff + xa)) : 0u) : (right & 0xffffu);
+                w[i] = (own >> 16) | (va << 16);
+            }
+        }
+    }
+}
+
+template <typename T, int PARITY, typename I, bool VISC>
+__global__ void __launch_bounds__(NODE_BX * NODE_BY) collide_pair_kernel(View<float> v) {
+    drop_dead_lines(v);
+    const int lane = threadIdx.x;
+    const int x0 = blockIdx.x * PAIR_X + 2 * lane, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+    if (y >= v.ny) return;  // the whole warp (threadIdx.y is uniform in a warp)
+    const int nx = v.nx;
+    const bool act = x0 < nx;
+    const int row0 = nx * (y + v.ny * z), n0 = row0 + x0;
+    const uint8_t t0 = act ? v.ntype[n0] : 0, t1 = act ? v.ntype[n0 + 1] : 0;
+    if (!__all_sync(0xffffffffu, (t0 | t1) == 0)) {  // walls or wall links in this chunk
+        if (act) {
+            collide_at<T, float, PARITY, I, VISC>(v, n0, x0, y, z);
+            collide_at<T, float, PARITY, I, VISC>(v, n0 + 1, x0 + 1, y, z);
+        }
+        return;
+    }
+    const bool first = lane == 0, last = lane == 31 || x0 + 2 >= nx;
+    const int xb = x0 == 0 ? nx - 1 : x0 - 1, xa = x0 + 2 >= nx ? 0 : x0 + 2;
+    const Nbr o = nbr_at(v, x0, y, z);
+    const RowRefs rr = row_refs<T>(v, y, z, PARITY == 1);
+    unsigned w[Q];
+    load_pair_words<T, PARITY, I>(v, n0, row0, xb, xa, o, act, first, last, w);
+    const size_t N = (size_t)v.N;
+    const float2 F0 = act ? *reinterpret_cast<const float2 *>(v.F + n0) : make_float2(0.f, 0.f);
+    const float2 F1 = act ? *reinterpret_cast<const float2 *>(v.F + N + n0) : make_float2(0.f, 0.f);
+    const float2 F2 = act ? *reinterpret_cast<const float2 *>(v.F + 2 * N + n0) : make_float2(0.f, 0.f);
+    // reference of direction i as read and as written (the slots' rows)
+    auto ref_rd = [&](int i) { return PARITY == 0 ? ref_dir(i, rr.own) : ref_dir(i, rr.at(-cy(i), -cz(i))); };
+    auto ref_wr = [&](int i) { return PARITY == 0 ? ref_dir(i, rr.own) : ref_dir(i, rr.at(cy(i), cz(i))); };
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // node x0 (low halves), then x0 + 1 (high halves)
+        const int n = n0 + h;
+        float d[Q], p[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = h ? dec_hi<T>(w[i], ref_rd(i)) : dec_lo<T>(w[i], ref_rd(i));
+        const float om = (VISC && act && v.ind && v.ind[n]) ? v.omega_in : v.omega;
+        float rho, ux, uy, uz;
+        bgk_guo<float>(d, h ? F0.y : F0.x, h ? F1.y : F1.x, h ? F2.y : F2.x, om, p, rho, ux, uy, uz);
+        if (v.rec && act) {
+            v.rec[n] = rho;
+            v.rec[N + n] = ux;
+            v.rec[2 * N + n] = uy;
+            v.rec[3 * N + n] = uz;
+        }
+        // the outputs replace this node's half of the words (the other
+        // node's inputs stay in the other half)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const unsigned e = enc16<T>(p[i], ref_wr(i));
+            w[i] = h ? ((w[i] & 0xffffu) | (e << 16)) : ((w[i] & 0xffff0000u) | e);
+        }
+    }
+    T *f = (T *)v.f;
+    const I NI = (I)N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0) {  // direction i leaving x0, x0 + 1: slot opp(i)
+            if (act) st_pair(f + (I)opp(i) * NI + (I)n0, w[i]);
+        } else {  // direction i arriving at x + c_i: slot i
+            const int roff = o.of(0, cy(i), cz(i));
+            T *dst = f + (I)i * NI;
+            if (cx(i) == 0) {
+                if (act) st_pair(dst + (I)(n0 + roff), w[i]);
+            } else if (cx(i) > 0) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                const unsigned left = __shfl_up_sync(0xffffffffu, w[i], 1);
+                if (act) {
+                    if (first) st_one(dst + (I)(n0 + roff + 1), w[i] & 0xffffu);
+                    else st_pair(dst + (I)(n0 + roff), (left >> 16) | (w[i] << 16));
+                    if (last) st_one(dst + (I)(row0 + roff + xa), w[i] >> 16);
+                }
+            } else {  // x0 -> x0 - 1, x0 + 1 -> x0
+                const unsigned right = __shfl_down_sync(0xffffffffu, w[i], 1);
+                if (act) {
+                    if (last) st_one(dst + (I)(n0 + roff), w[i] >> 16);
+                    else st_pair(dst + (I)(n0 + roff), (w[i] >> 16) | (right << 16));
+                    if (first) st_one(dst + (I)(row0 + roff + xb), w[i] & 0xffffu);
+                }
+            }
+        }
+    }
+}
+
+// post-streaming velocity of two nodes per thread (16-bit storage); LAYOUT
+// as in load_pops
+template <typename T, int LAYOUT, typename I>
+__global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_pair_kernel(View<float> v) {
+    const int lane = threadIdx.x;
+    const int x0 = blockIdx.x * PAIR_X + 2 * lane, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+    if (y >= v.ny) return;
+    const int nx = v.nx;
+    const bool act = x0 < nx;
+    const int row0 = nx * (y + v.ny * z), n0 = row0 + x0;
+    const uint8_t t0 = act ? v.ntype[n0] : 0, t1 = act ? v.ntype[n0 + 1] : 0;
+    if (!__all_sync(0xffffffffu, (t0 | t1) == 0)) {
+        if (act)
+            for (int h = 0; h < 2; ++h) {
+                const int n = n0 + h;
+                const uint8_t nt = h ? t1 : t0;
+                if (nt & 0x7f) {  // wall node: the wall's velocity (written when recording into a fresh buffer)
+                    if (v.rec)
+                        for (int k = 0; k < 3; ++k) v.u[(size_t)k * v.N + n] = v.uw[nt & 0x7f][k];
+                    continue;
+                }
+                const Nbr o = nbr_at(v, x0 + h, y, z);
+                const RowRefs rr = row_refs<T>(v, y, z, LAYOUT == 1);
+                if (nt & 0x80) moments_core<T, float, LAYOUT, true, I>(v, n, o, v.links[n], rr);
+                else moments_core<T, float, LAYOUT, false, I>(v, n, o, 0ull, rr);
+            }
+        return;
+    }
+    const bool first = lane == 0, last = lane == 31 || x0 + 2 >= nx;
+    const int xb = x0 == 0 ? nx - 1 : x0 - 1, xa = x0 + 2 >= nx ? 0 : x0 + 2;
+    const Nbr o = nbr_at(v, x0, y, z);
+    const RowRefs rr = row_refs<T>(v, y, z, LAYOUT == 1);
+    unsigned w[Q];
+    load_pair_words<T, LAYOUT, I>(v, n0, row0, xb, xa, o, act, first, last, w);
+    if (!act) return;
+    const size_t N = (size_t)v.N;
+    float u[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float ref = LAYOUT == 0 ? ref_dir(i, rr.own) : ref_dir(i, rr.at(-cy(i), -cz(i)));
+            const float d = h ? dec_hi<T>(w[i], ref) : dec_lo<T>(w[i], ref);
+            drho += d;
+            if (cx(i)) mx += cx(i) > 0 ? d : -d;
+            if (cy(i)) my += cy(i) > 0 ? d : -d;
+            if (cz(i)) mz += cz(i) > 0 ? d : -d;
+        }
+        const int n = n0 + h;
+        const float inv = recip(1.f + drho);
+        u[h][0] = (mx + 0.5f * v.F[n]) * inv;
+        u[h][1] = (my + 0.5f * v.F[N + n]) * inv;
+        u[h][2] = (mz + 0.5f * v.F[2 * N + n]) * inv;
+        const float q = u[h][0] * u[h][0] + u[h][1] * u[h][1] + u[h][2] * u[h][2];
+        if (!(q < U_LIMIT2)) atomicOr(v.status, ST_NUMERIC);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *reinterpret_cast<float2 *>(v.u + k * N + n0) = make_float2(u[0][k], u[1][k]);
+}
+
+// Rows' reference x-velocity from a velocity field u0 ([n][3], double):
+// the mean of u_x over the row's fluid nodes (0 for a row without fluid),
+// stored as (P, M) (see row_refs)
+__global__ void row_reference_kernel(int nx, int nrows, const uint8_t *ntype, const double *u0, float2 *rref) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    double s = 0;
+    int k = 0;
+    for (int x = 0; x < nx; ++x) {
+        const size_t n = (size_t)r * nx + x;
+        if (ntype[n] & 0x7f) continue;
+        s += u0[3 * n];
+        ++k;
+    }
+    const double U = k ? s / k : 0.0;
+    rref[r] = make_float2((float)((3.0 * U + 3.0 * U * U) / 18.0), (float)((-3.0 * U + 3.0 * U * U) / 18.0));
+}
+
+// Natural-order 16-bit populations re-stored from reference table `from` to
+// table `to` (either may be null: zero reference)
+template <typename T>
+__global__ void reencode_kernel(View<float> v, const float2 *from, const float2 *to) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= v.N) return;
+    if (v.ntype[n] & 0x7f) return;
+    const int r = n / v.nx;
+    const float2 a = from ? from[r] : make_float2(0.f, 0.f), b = to ? to[r] : make_float2(0.f, 0.f);
+    T *f = (T *)v.f;
+    const size_t N = (size_t)v.N;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T &s = f[(size_t)i * N + n];
+        s = Store<T>::st(Store<T>::ld(s) + ref_dir(i, a) - ref_dir(i, b));
+    }
 }
 
 template <typename T, typename R>
@@ -414,10 +778,11 @@ __global__ void init_equilibrium_kernel(View<R> v, const double *u0) {
         uz = u0[3 * (size_t)n + 2];
     }
     const double uu = ux * ux + uy * uy + uz * uz;
+    const RowRefs rr = row_refs_of<T>(v, n, false);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        f[(size_t)i * N + n] = Store<T>::st(R(wgt(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
+        f[(size_t)i * N + n] = enc<T, R>(R(wgt(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)), ref_dir(i, rr.own));
     }
     v.u[n] = R(ux);
     v.u[N + n] = R(uy);
@@ -437,7 +802,7 @@ __global__ void populations_out_kernel(View<R> v, double *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr nb = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, row_refs_of<T>(v, n, LAYOUT == 1), d);
     for (int i = 0; i < Q; ++i) o[i] = wgt(i) + (double)d[i];
 }
 
@@ -453,7 +818,7 @@ __global__ void rho_out_kernel(View<R> v, R *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr nb = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, nb, row_refs_of<T>(v, n, LAYOUT == 1), d);
     R drho = R(0);
     for (int i = 0; i < Q; ++i) drho += d[i];
     out[n] = R(1) + drho;
@@ -518,7 +883,7 @@ __global__ void copy_natural_kernel(View<R> v, R *out) {
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr o = make_nbr(v, n);
     R d[Q];
-    load_pops<T, R, LAYOUT, true>(v, n, lk, o, d);
+    load_pops<T, R, LAYOUT, true>(v, n, lk, o, row_refs_of<T>(v, n, LAYOUT == 1), d);
     for (int i = 0; i < Q; ++i) out[(size_t)i * N + n] = d[i];
 }
 
@@ -537,11 +902,13 @@ __global__ void restore_natural_kernel(View<R> v, const R *in) {
     T *f = (T *)v.f;
     const uint64_t lk = (nt & 0x80) ? v.links[n] : 0ull;
     const Nbr o = make_nbr(v, n);
-    for (int i = 0; i < Q; ++i) {
-        const T val = Store<T>::st(in[(size_t)i * N + n]);
-        if (LAYOUT == 0 || i == 0) f[(size_t)i * N + n] = val;
-        else if (link_code(lk, opp(i))) f[(size_t)i * N + n] = val;
-        else f[(size_t)opp(i) * N + n + o.of(-cx(i), -cy(i), -cz(i))] = val;
+    const RowRefs rr = row_refs_of<T>(v, n, LAYOUT == 1);
+    for (int i = 0; i < Q; ++i) {  // the slot and its reference as load_pops reads them
+        const R val = in[(size_t)i * N + n];
+        if (LAYOUT == 0) f[(size_t)i * N + n] = enc<T, R>(val, ref_dir(i, rr.own));
+        else if (i == 0) f[n] = enc<T, R>(val, 0.f);
+        else if (link_code(lk, opp(i))) f[(size_t)i * N + n] = enc<T, R>(val, ref_dir(opp(i), rr.own));
+        else f[(size_t)opp(i) * N + n + o.of(-cx(i), -cy(i), -cz(i))] = enc<T, R>(val, ref_dir(i, rr.at(-cy(i), -cz(i))));
     }
 }
 
@@ -562,13 +929,37 @@ dim3 node_grid(const View<R> &v) {
 // launchers
 // ---------------------------------------------------------------------------
 
+// the per-node kernel, or for 16-bit storage the two-node kernel
+template <typename T, typename R, int PARITY, typename I, bool VISC>
+void launch_collide_as(const View<R> &v, cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value && sizeof(T) == 2) {
+        if (v.node_pairs) {
+            const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
+            collide_pair_kernel<T, PARITY, I, VISC><<<g, dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+            return;
+        }
+    }
+    collide_stream_kernel<T, R, PARITY, I, VISC><<<node_grid(v), dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+}
+
+template <typename T, typename R, typename I>
+void launch_collide_parity(const View<R> &v, int parity, cudaStream_t st) {
+    const bool visc = v.ind != nullptr;  // internal viscosity on
+    if (parity == 0) {
+        if (visc) launch_collide_as<T, R, 0, I, true>(v, st);
+        else launch_collide_as<T, R, 0, I, false>(v, st);
+    } else {
+        if (visc) launch_collide_as<T, R, 1, I, true>(v, st);
+        else launch_collide_as<T, R, 1, I, false>(v, st);
+    }
+}
+
 template <typename R>
 void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value) {
         // 16-bit storage, odd steps (reads and writes shifted by one node in
-        // x): the staged kernel, which also collides the rows next to walls
-        // node by node once its tiles are done.  Even steps touch each node's
-        // own slots, which the per-node kernel streams faster.
+        // x), on request: the staged kernel, which also collides the rows
+        // next to walls node by node once its tiles are done
         if (v.ntiles && parity == 1) {
             if (narrow_index(v))
                 HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1, unsigned><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
@@ -577,30 +968,8 @@ void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st
             return;
         }
     }
-    const dim3 g = node_grid(v), b(NODE_BX, NODE_BY);
-    if (v.ind) {  // internal viscosity on
-        if (narrow_index(v)) {
-            if (parity == 0)
-                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned, true><<<g, b, 0, st>>>(v)));
-            else
-                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned, true><<<g, b, 0, st>>>(v)));
-        } else {
-            if (parity == 0)
-                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t, true><<<g, b, 0, st>>>(v)));
-            else
-                HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t, true><<<g, b, 0, st>>>(v)));
-        }
-    } else if (narrow_index(v)) {
-        if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, unsigned, false><<<g, b, 0, st>>>(v)));
-        else
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, unsigned, false><<<g, b, 0, st>>>(v)));
-    } else {
-        if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 0, size_t, false><<<g, b, 0, st>>>(v)));
-        else
-            HEMO_DISPATCH_T(precision, R, (collide_stream_kernel<T, R, 1, size_t, false><<<g, b, 0, st>>>(v)));
-    }
+    if (narrow_index(v)) HEMO_DISPATCH_T(precision, R, (launch_collide_parity<T, R, unsigned>(v, parity, st)));
+    else HEMO_DISPATCH_T(precision, R, (launch_collide_parity<T, R, size_t>(v, parity, st)));
 }
 
 cudaError_t set_tile_smem_limit(int precision, int bytes) {
@@ -614,22 +983,39 @@ cudaError_t set_tile_smem_limit(int precision, int bytes) {
     return e;
 }
 
+template <typename T, typename R, int LAYOUT, typename I>
+void launch_moments_as(const View<R> &v, cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value && sizeof(T) == 2) {
+        if (v.node_pairs) {
+            const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
+            moments_pair_kernel<T, LAYOUT, I><<<g, dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+            return;
+        }
+    }
+    moments_kernel<T, R, LAYOUT, I><<<node_grid(v), dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+}
+
 template <typename R>
 void launch_moments(const View<R> &v, int precision, int parity, cudaStream_t st) {
     // after an even step the array is in the swapped layout (1), after an odd
     // step in natural order (0)
-    const dim3 g = node_grid(v), b(NODE_BX, NODE_BY);
     if (narrow_index(v)) {
-        if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 1, unsigned><<<g, b, 0, st>>>(v)));
-        else
-            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 0, unsigned><<<g, b, 0, st>>>(v)));
+        if (parity == 0) HEMO_DISPATCH_T(precision, R, (launch_moments_as<T, R, 1, unsigned>(v, st)));
+        else HEMO_DISPATCH_T(precision, R, (launch_moments_as<T, R, 0, unsigned>(v, st)));
     } else {
-        if (parity == 0)
-            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 1, size_t><<<g, b, 0, st>>>(v)));
-        else
-            HEMO_DISPATCH_T(precision, R, (moments_kernel<T, R, 0, size_t><<<g, b, 0, st>>>(v)));
+        if (parity == 0) HEMO_DISPATCH_T(precision, R, (launch_moments_as<T, R, 1, size_t>(v, st)));
+        else HEMO_DISPATCH_T(precision, R, (launch_moments_as<T, R, 0, size_t>(v, st)));
     }
+}
+
+void launch_row_reference(const View<float> &v, const double *u0, float2 *rref, cudaStream_t st) {
+    const int nrows = v.ny * v.nz;
+    row_reference_kernel<<<nblocks(nrows, 128), 128, 0, st>>>(v.nx, nrows, v.ntype, u0, rref);
+}
+
+void launch_reencode(const View<float> &v, int precision, const float2 *from, const float2 *to, cudaStream_t st) {
+    if (precision == HEMO_F16DEV) reencode_kernel<__half><<<nblocks(v.N, 256), 256, 0, st>>>(v, from, to);
+    else if (precision == HEMO_BF16DEV) reencode_kernel<__nv_bfloat16><<<nblocks(v.N, 256), 256, 0, st>>>(v, from, to);
 }
 
 template <typename R>

@@ -33,6 +33,8 @@ class hemo_lattice_desc(C.Structure):
                 ('alloc_ctx', C.c_void_p), ('options', C.c_uint)]
 
 HEMO_OPT_STAGED_COLLISION = 1
+HEMO_OPT_NODE_COLLISION = 2
+HEMO_OPT_TEST_STALLED_WAIT = 4
 HEMO_EULER, HEMO_AB2 = 0, 1
 INTEGRATORS = {'euler': HEMO_EULER, 'ab2': HEMO_AB2}
 
@@ -86,6 +88,9 @@ def lib():
         'hemo_set_phase_timing': ([vp, i], i),
         'hemo_get_phase_times': ([vp, vp, C.POINTER(i)], i),
         'hemo_bin_vertices_noalloc': ([vp, i, i, i, i, vp, vp, vp, vp, vp], i),
+        'hemo_state_bytes': ([vp, C.POINTER(C.c_size_t)], i),
+        'hemo_save_state': ([vp, vp, C.c_size_t], i),
+        'hemo_load_state': ([vp, vp, C.c_size_t], i),
         'hemo_record': ([vp, i], i),
         'hemo_deformation_loss': ([vp, vp, vp], i),
         'hemo_backward': ([vp, vp, vp, i], i),
@@ -106,7 +111,8 @@ def exported_symbols():
             'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_set_lees_edwards', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
-            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_record',
+            'hemo_set_phase_timing', 'hemo_get_phase_times', 'hemo_bin_vertices_noalloc', 'hemo_state_bytes',
+            'hemo_save_state', 'hemo_load_state', 'hemo_record',
             'hemo_deformation_loss', 'hemo_backward', 'hemo_destroy', 'hemo_last_error']
 
 
@@ -358,6 +364,22 @@ class Simulation:
         start = np.zeros(nb + 1, np.int32)
         check(lib().hemo_get_bins(self.handle, key.ctypes.data, perm.ctypes.data, start.ctypes.data))
         return key, perm, start
+
+    # -- checkpoint and resume -------------------------------------------
+    def save_state(self):
+        """The simulation's dynamic state as a host byte array (see
+        hemo_save_state)."""
+        n = C.c_size_t()
+        check(lib().hemo_state_bytes(self.handle, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        check(lib().hemo_save_state(self.handle, buf.ctypes.data, n.value))
+        return buf
+
+    def load_state(self, buf):
+        """Continue from a state saved by save_state() of a simulation
+        created and filled with cells the same way."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().hemo_load_state(self.handle, buf.ctypes.data, buf.size))
 
     # -- differentiation form --------------------------------------------
     def record(self, checkpoint_every=100):

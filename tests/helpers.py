@@ -13,12 +13,13 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def assert_close(got, exp, tol, what=''):
+def assert_close(got, exp, tol, what='', max_tol=None):
     """Parity check of one field: relative L2 error <= tol (the measure the
     tolerances are stated in) and, so that an error confined to a few
     elements (next to a wall, on a bin face, across a periodic or shifted
     boundary) is not diluted by the whole-field norm, the largest
-    per-element error <= tol times the field's largest magnitude."""
+    per-element error <= max_tol (default tol) times the field's largest
+    magnitude."""
     a = np.asarray(got, float)
     b = np.asarray(exp, float)
     assert a.shape == b.shape, (what, a.shape, b.shape)
@@ -26,7 +27,8 @@ def assert_close(got, exp, tol, what=''):
     assert err < tol, (what, 'relative L2', err, tol)
     scale = np.abs(b).max() if b.size else 0.0
     worst = np.abs(a - b).max() if b.size else 0.0
-    assert worst <= tol * (scale if scale > 0 else 1.0), (what, 'max abs', worst, tol * scale)
+    mt = tol if max_tol is None else max_tol
+    assert worst <= mt * (scale if scale > 0 else 1.0), (what, 'max abs', worst, mt * scale)
 
 
 def direction_map():

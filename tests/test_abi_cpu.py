@@ -210,7 +210,8 @@ def test_binding_layouts_match_the_header(tmp_path):
     mesh = [f for f, _ in hemo.hemo_mesh_desc._fields_]
     consts = ['HEMO_OK', 'HEMO_ERR_ARG', 'HEMO_ERR_OOM', 'HEMO_ERR_CUDA', 'HEMO_ERR_NUMERIC', 'HEMO_ERR_DOMAIN',
               'HEMO_ERR_STATE', 'HEMO_RHO', 'HEMO_U', 'HEMO_VERTS', 'HEMO_FORCES', 'HEMO_CELLSTATS',
-              'HEMO_OPT_STAGED_COLLISION', 'HEMO_EULER', 'HEMO_AB2']
+              'HEMO_OPT_STAGED_COLLISION', 'HEMO_OPT_NODE_COLLISION', 'HEMO_OPT_TEST_STALLED_WAIT', 'HEMO_EULER',
+              'HEMO_AB2']
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hemo.h"', 'int main(void) {',
              'printf("lat %zu\\n", sizeof(hemo_lattice_desc));', 'printf("mesh %zu\\n", sizeof(hemo_mesh_desc));']
     lines += [f'printf("lat.{f} %zu\\n", offsetof(hemo_lattice_desc, {f}));' for f in lat]
@@ -245,7 +246,7 @@ def _c_kind(param):
     p = re.sub(r'\b(const|enum|struct)\b', '', p).split()
     if p[:2] == ['long', 'long']:
         return 'll'
-    return {'int': 'int', 'unsigned': 'uint', 'double': 'double', 'void': 'void'}[p[0]]
+    return {'int': 'int', 'unsigned': 'uint', 'double': 'double', 'void': 'void', 'size_t': 'size'}[p[0]]
 
 
 def _ctypes_kind(t):
@@ -253,7 +254,7 @@ def _ctypes_kind(t):
         return 'void'
     if t in (C.c_void_p, C.c_char_p) or hasattr(t, '_type_') and isinstance(t._type_, type):
         return 'ptr'
-    return {C.c_int: 'int', C.c_uint: 'uint', C.c_double: 'double', C.c_longlong: 'll'}[t]
+    return {C.c_int: 'int', C.c_uint: 'uint', C.c_double: 'double', C.c_longlong: 'll', C.c_size_t: 'size'}[t]
 
 
 def test_binding_signatures_match_the_header():

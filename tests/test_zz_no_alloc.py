@@ -77,7 +77,7 @@ def test_noalloc_odd_non_periodic_lattice():
     X = sim.get_fields(hemo.HEMO_VERTS)['X']
     X[::5] = np.floor(X[::5])
     X[1] = [12.0, 20.0, 8.0]
-    X[2] = [7.999999999, 15.9999999, 0.0]
+    X[2] = [7.999999999, 15.9999999, 1.0]  # (not 0: the FP32 offset could round below the edge)
     sim.set_vertices(X)
     Xg = sim.get_fields(hemo.HEMO_VERTS)['X']
     k_ref, p_ref, s_ref = sim.bins()
@@ -126,7 +126,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     verts = torch.zeros((4, 3), dtype=torch.float64, device='cuda')
     out = torch.zeros(8, dtype=torch.int32, device='cuda')
+    start = torch.zeros(128 ** 3 + 1, dtype=torch.int32, device='cuda')  # large enough for the binding's check
     with pytest.raises(hemo.HemoError) as e:
-        hemo.bin_vertices_noalloc(verts, (1024, 1024, 1024), (1, 1, 1), out, out, out)
+        hemo.bin_vertices_noalloc(verts, (1024, 1024, 1024), (1, 1, 1), out, out, start)
     assert e.value.code == hemo.HEMO_ERR_ARG
     assert 'blocks' in str(e.value)
