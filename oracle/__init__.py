@@ -48,6 +48,10 @@ def lib():
         L.ora_d3q19.argtypes = [_ip, _dp, _ip]
         L.ora_equilibrium.argtypes = [C.c_double, _dp, _dp]
         L.ora_storage_reference.argtypes = [C.c_double, _dp]
+        L.ora_set_force_tolerance.argtypes = [C.c_void_p, C.c_double]
+        L.ora_set_force_tolerance.restype = C.c_int
+        L.ora_force_evaluations.argtypes = [C.c_void_p]
+        L.ora_force_evaluations.restype = C.c_long
         L.ora_phi.argtypes = [C.c_double]
         L.ora_phi.restype = C.c_double
         L.ora_build_edges.argtypes = [C.c_int, C.c_int, _ip, _ip]
@@ -238,6 +242,19 @@ class OracleSim:
         rc = lib().ora_set_time_scales(self.h, int(force_every), INTEGRATORS[integrator])
         if rc != 0:
             raise ValueError('force_every must be >= 1')
+
+    def set_force_tolerance(self, delta):
+        """Adaptive separation: from the next step the membrane forces are
+        evaluated on the first step, then whenever the largest vertex
+        displacement since the last evaluation exceeds delta at the start of
+        a step, or force_every steps have passed; delta < 0: the constant
+        schedule."""
+        if lib().ora_set_force_tolerance(self.h, float(delta)) != 0:
+            raise ValueError('delta must not be NaN')
+
+    @property
+    def force_evaluations(self):
+        return lib().ora_force_evaluations(self.h)
 
     def set_lees_edwards(self, U):
         """Lees-Edwards boundary along z: the image above the box is displaced

@@ -45,6 +45,11 @@
  *     step at which the setting was made) and held unchanged on the steps in
  *     between; spreading, the fluid update, interpolation and the vertex move
  *     run every step.  The default is N = 1 with Euler;
+ *   - adaptive separation (Sec. 2.6 allows an adaptive one; its criterion
+ *     is in a cited work that is not available): forces are evaluated on the
+ *     first step after the setting and then whenever, at the start of a step,
+ *     the largest vertex displacement since the last evaluation exceeds a
+ *     tolerance delta, or N steps have passed since it;
  *   - Adams-Bashforth (Sec. 2.6): the two-step explicit form
  *     X^{n+1} = X^n + 3/2 U^n - 1/2 U^{n-1} with dt = 1, U^n the velocity
  *     interpolated at X^n; the first step after the setting is made (no
@@ -448,6 +453,12 @@ typedef struct {
     long nstep, ts_origin; /* steps taken; step at which the setting was made */
     int have_prev;         /* Up holds U^{n-1} */
     double *Up;            /* nvtot*3 */
+    /* adaptive separation: re-evaluate when the largest vertex displacement
+     * since the last evaluation exceeds adapt_delta (< 0: fixed schedule) */
+    double adapt_delta;
+    double *Xe;            /* nvtot*3 positions at the last evaluation */
+    long last_eval;        /* step of the last evaluation, -1: none since the setting */
+    long evaluations;      /* force evaluations so far */
     /* Lees-Edwards boundary along z */
     int le_on;
     double le_U;           /* velocity of the image above relative to the box */
@@ -481,6 +492,8 @@ void *ora_create(int nx, int ny, int nz, double tau, const int *periodic, const 
     s->rho_c = (double *)malloc(sizeof(double) * s->N);
     s->force_every = 1;
     s->integrator = ORA_EULER;
+    s->adapt_delta = -1.0;
+    s->last_eval = -1;
     s->visc_ratio = 1.0;
     s->inside = (unsigned char *)calloc(s->N, 1);
     s->F = (double *)calloc(3 * s->N, sizeof(double));
@@ -497,7 +510,7 @@ void ora_destroy(void *p) {
     if (!s) return;
     for (int t = 0; t < s->ntypes; ++t) mesh_free(&s->types[t]);
     free(s->mask); free(s->f); free(s->fn); free(s->rho_c); free(s->F); free(s->u);
-    free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c); free(s->Up);
+    free(s->cell_type); free(s->cell_first); free(s->X); free(s->Fv); free(s->X0c); free(s->Up); free(s->Xe);
     free(s->inside); free(s->forced);
     free(s);
 }
@@ -527,6 +540,7 @@ int ora_add_cells(void *p, int type, int ncell, const double *centers, const dou
     s->X = (double *)realloc(s->X, sizeof(double) * 3 * (old + (long)ncell * nv));
     s->Fv = (double *)realloc(s->Fv, sizeof(double) * 3 * (old + (long)ncell * nv));
     s->Up = (double *)realloc(s->Up, sizeof(double) * 3 * (old + (long)ncell * nv));
+    if (s->Xe) s->Xe = (double *)realloc(s->Xe, sizeof(double) * 3 * (old + (long)ncell * nv));
     s->have_prev = 0;
     for (int c = 0; c < ncell; ++c) {
         int id = s->ncell + c;
@@ -553,6 +567,7 @@ void ora_set_vertices(void *p, const double *X) {
     memcpy(s->X, X, sizeof(double) * 3 * s->nvtot);
     s->have_prev = 0;
     s->ts_origin = s->nstep;
+    s->last_eval = -1;
 }
 
 /* time-scale separation N (membrane forces every N steps, held in between)
@@ -563,8 +578,44 @@ int ora_set_time_scales(void *p, int force_every, int integrator) {
     s->force_every = force_every;
     s->integrator = integrator;
     s->ts_origin = s->nstep;
+    s->last_eval = -1;
     s->have_prev = 0;
     return 0;
+}
+
+/* Adaptive separation (Sec. 2.6: the separation may be adaptive; the
+ * criterion of the cited work is not available, this is the build's own):
+ * with delta >= 0 the membrane forces are evaluated on the first step after
+ * this call, and then on every step at whose start the largest vertex
+ * displacement |X_v - X_v(last evaluation)| exceeds delta, or at which
+ * force_every steps have passed since the last evaluation; they are held
+ * in between.  delta < 0: the constant schedule of ora_set_time_scales. */
+int ora_set_force_tolerance(void *p, double delta) {
+    osim *s = (osim *)p;
+    if (delta != delta) return -1;
+    s->adapt_delta = delta;
+    s->last_eval = -1;
+    s->ts_origin = s->nstep;
+    if (delta >= 0 && !s->Xe) s->Xe = (double *)calloc(3 * (size_t)(s->nvtot > 0 ? s->nvtot : 1), sizeof(double));
+    return 0;
+}
+
+long ora_force_evaluations(void *p) { return ((osim *)p)->evaluations; }
+
+/* whether the membrane forces are evaluated on the current step */
+static int force_step(osim *s) {
+    if (s->adapt_delta < 0) return (s->nstep - s->ts_origin) % s->force_every == 0;
+    if (s->last_eval < 0 || s->nstep - s->last_eval >= s->force_every) return 1;
+    double m2 = 0;
+    for (long k = 0; k < s->nvtot; ++k) {
+        double d2 = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double e = s->X[3 * k + d] - s->Xe[3 * k + d];
+            d2 += e * e;
+        }
+        if (d2 > m2) m2 = d2;
+    }
+    return sqrt(m2) > s->adapt_delta;
 }
 
 /* populations at equilibrium with rho = 1 and the given velocity field
@@ -781,7 +832,12 @@ static void step_once(osim *s) {
         }
     /* 1-2: membrane forces at the current positions (per cell), on every
      * N-th step only; the last ones are held in between */
-    if ((s->nstep - s->ts_origin) % s->force_every == 0) {
+    if (force_step(s)) {
+        if (s->adapt_delta >= 0) {
+            memcpy(s->Xe, s->X, sizeof(double) * 3 * s->nvtot);
+            s->last_eval = s->nstep;
+        }
+        s->evaluations += 1;
         for (long v = 0; v < 3 * s->nvtot; ++v) s->Fv[v] = 0;
         #pragma omp parallel for schedule(static)
         for (int c = 0; c < s->ncell; ++c) {

@@ -125,3 +125,88 @@ def test_time_scale_arguments():
         s.set_time_scales(0, 'euler')
     with pytest.raises(KeyError):
         s.set_time_scales(2, 'rk4')
+
+
+# ---------------------------------------------------------------------------
+# adaptive separation (Sec. 2.6: the separation may also be adaptive; the
+# criterion of the cited work is not available, so it is the build's own:
+# re-evaluate when the largest vertex displacement since the last evaluation
+# exceeds a tolerance delta, or when force_every steps have passed)
+# ---------------------------------------------------------------------------
+def _stretched_box():
+    s = _accelerating_box(PARAMS)
+    X = s.get()['X']
+    s.set_vertices(X.mean(0) + (X - X.mean(0)) * np.array([1.15, 1.0, 0.9]))
+    return s
+
+
+@pytest.mark.parametrize('integrator', ['euler', 'ab2'])
+def test_adaptive_zero_tolerance_is_every_step(integrator):
+    """delta = 0: every step in which anything moved re-evaluates, which is
+    the default schedule (N = 1) bit for bit."""
+    a = _stretched_box()
+    a.set_time_scales(1, integrator)
+    a.step(7)
+    b = _stretched_box()
+    b.set_time_scales(10 ** 9, integrator)
+    b.set_force_tolerance(0.0)
+    b.step(7)
+    assert b.force_evaluations == 7
+    ra, rb = a.get(), b.get()
+    for k in ('X', 'u', 'Fv', 'rho'):
+        assert np.array_equal(ra[k], rb[k]), k
+
+
+def test_adaptive_infinite_tolerance():
+    """delta = inf: with no bound on the interval the forces of the first
+    step are held for the whole run (one evaluation); with the bound N = 4
+    the schedule is the constant separation N = 4, bit for bit."""
+    v, t = I.icosphere(1)
+    rest = v * 2.5
+    s = _stretched_box()
+    s.set_time_scales(10 ** 9, 'euler')
+    s.set_force_tolerance(np.inf)
+    F0 = O.membrane(rest, t, PARAMS, s.get()['X'])[0]
+    for n in range(9):
+        s.step(1)
+        assert np.array_equal(s.get()['Fv'], F0), n
+    assert s.force_evaluations == 1
+    a = _stretched_box()
+    a.set_time_scales(4, 'ab2')
+    a.step(11)
+    b = _stretched_box()
+    b.set_time_scales(4, 'ab2')
+    b.set_force_tolerance(np.inf)
+    b.step(11)
+    assert b.force_evaluations == 3
+    ra, rb = a.get(), b.get()
+    for k in ('X', 'u', 'Fv'):
+        assert np.array_equal(ra[k], rb[k]), k
+
+
+@pytest.mark.parametrize('delta,N', [(0.05, 10 ** 9), (0.07, 4)])
+def test_adaptive_schedule_follows_the_criterion(delta, N):
+    """A cell stretched and carried by the accelerating fluid, so that the
+    displacement per step grows: after each step the forces are those of the
+    positions at the start of the step exactly when the criterion, evaluated
+    here from the positions alone, calls for an evaluation (the first step,
+    N steps since the last one, or a vertex more than delta from its
+    position then), and the held ones otherwise; the evaluations are
+    irregular in time."""
+    v, t = I.icosphere(1)
+    rest = v * 2.5
+    s = _stretched_box()
+    s.set_time_scales(N, 'euler')
+    s.set_force_tolerance(delta)
+    held, Xe, ne, steps = None, None, None, []
+    for n in range(24):
+        Xn = s.get()['X']
+        evaluate = Xe is None or n - ne >= N or np.linalg.norm(Xn - Xe, axis=1).max() > delta
+        if evaluate:
+            held, Xe, ne = O.membrane(rest, t, PARAMS, Xn)[0], Xn, n
+            steps.append(n)
+        s.step(1)
+        assert np.array_equal(s.get()['Fv'], held), n
+    assert s.force_evaluations == len(steps)
+    gaps = np.diff(steps)
+    assert len(steps) >= 4 and len(set(gaps.tolist())) > 1, steps
