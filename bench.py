@@ -198,27 +198,33 @@ def run_form(cfg, precision, warmup, steps, torch, flush, u_ref=None):
     return res, u
 
 
-TIME_SCALES = [(1, 'euler'), (2, 'euler'), (4, 'euler'), (4, 'ab2'), (10, 'ab2')]
+# (force_every, integrator, adaptive tolerance or None)
+TIME_SCALES = [(1, 'euler', None), (2, 'euler', None), (4, 'euler', None), (4, 'ab2', None), (10, 'ab2', None),
+               (10, 'ab2', 0.05), (10, 'ab2', 0.1)]
 
 
 def time_scales(cfg, precision, warmup, steps, torch, flush):
     """Time-scale separation (membrane forces every N steps, held in
-    between) and the vertex integrator: throughput of the same workload per
-    setting, and the velocity and vertex drift after warmup + steps steps
-    relative to forces every step with Euler."""
+    between, or adaptively: when a vertex moved more than the tolerance since
+    the last evaluation, at most N steps apart) and the vertex integrator:
+    throughput of the same workload per setting, and the velocity and vertex
+    drift after warmup + steps steps relative to forces every step with
+    Euler."""
     from paper_2305_02752_gb300 import hemo
     out, ref = [], None
-    for n, integ in TIME_SCALES:
+    for n, integ, tol in TIME_SCALES:
         sim = hemo.Simulation.from_config(cfg, precision)
         sim.set_time_scales(n, integ)
+        if tol is not None:
+            sim.set_force_tolerance(tol)
         sim.step(warmup)
         sim.sync()
         total, _, _ = timed_steps(sim, torch, steps, flush, phase_every=0)
         f = sim.get_fields(hemo.HEMO_U | hemo.HEMO_VERTS)
         sim.close()
         u, X = f['u'].astype(np.float64), f['X']
-        r = {'force_every': n, 'integrator': integ, 'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6,
-             'ms_per_step': total / steps}
+        r = {'force_every': n, 'integrator': integ, 'force_tolerance': tol,
+             'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps}
         if ref is None:
             ref = (u, X)
         else:

@@ -194,6 +194,23 @@ enum hemo_integrator {
  * refuses other settings). */
 int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
 
+/* Adaptive time-scale separation (Sec. 2.6: the separation of the cell and
+ * fluid updates may be constant or adaptive; the paper's adaptive criterion
+ * is in a cited work, so this one is the library's own).  With delta >= 0
+ * the membrane forces are evaluated on the next step and from then on at
+ * every step at whose start the largest vertex displacement since the last
+ * evaluation, |X_v - X_v(last evaluation)|, exceeds delta (lattice units),
+ * or at which force_every steps (hemo_set_time_scales) have passed since the
+ * last evaluation; they are held in between.  The decision is taken on the
+ * device each step (no host synchronisation); the displacement includes the
+ * cells' translation, so the criterion is conservative.  delta = 0 evaluates
+ * on every step in which anything moved (the default schedule); delta < 0
+ * returns to the constant schedule.  hemo_set_time_scales and
+ * hemo_set_vertices restart it (the next step evaluates).  Errors:
+ * HEMO_ERR_ARG for NaN; HEMO_ERR_STATE while recording for hemo_backward
+ * and with the Lees-Edwards boundary; HEMO_ERR_OOM. */
+int hemo_set_force_tolerance(hemo_sim *sim, double delta);
+
 /* Internal viscosity (Sec. 1: the cytosol is five times as viscous as the
  * plasma; Sec. 3: the red-cell model carries an internal viscosity ratio).
  * From the next step on, fluid nodes inside a cell membrane (at the vertex

@@ -163,6 +163,11 @@ struct hemo_sim {
     bool have_prev = false;       // Uprev holds the previous step's vertex velocity
     void *Uprev = nullptr;
     void *csp = nullptr;          // per cell: centroid of the last re-base as R hi, lo
+    // adaptive separation: tolerance (< 0: off), offsets at the last force
+    // evaluation and the device decision words (see View)
+    double force_tol = -1.0;
+    void *off_eval = nullptr;
+    unsigned long long *adapt = nullptr;
     // internal viscosity (Sec. 1, Sec. 3): ratio of the viscosity inside cells
     double visc_ratio = 1.0;      // 1: off
     uint8_t *ind = nullptr;       // N: inside a cell
@@ -174,8 +179,9 @@ struct hemo_sim {
     void *f2 = nullptr, *le_aux = nullptr;
     long long *le_n = nullptr;
     // graphs, one per step variant: parity + 2 force step + 4 integrator mode
+    // (0..11), and with the adaptive separation 12 + parity + 2 integrator mode
     cudaStream_t cap = nullptr;
-    static constexpr int NGRAPH = 12;
+    static constexpr int NGRAPH = 18;
     cudaGraphExec_t graph[NGRAPH] = {};
     int graph_kernels[NGRAPH] = {};
     int last_graph = -1;
@@ -305,6 +311,10 @@ View<R> make_view(hemo_sim *s) {
     v.integ = 0;
     v.Uprev = (R *)s->Uprev;
     v.csp = (R *)s->csp;
+    if (s->force_tol >= 0) {
+        v.off_eval = (R *)s->off_eval;
+        v.adapt = s->adapt;
+    }
     if (s->visc_ratio != 1.0) {
         v.ind = s->ind;
         v.tog = s->tog;
@@ -320,18 +330,26 @@ View<R> make_view(hemo_sim *s) {
     return v;
 }
 
-// One coupled step.  force: evaluate the membrane forces (else the last
-// ones are held, Sec. 2.6); v.integ selects the vertex integrator.
+// One coupled step.  force: 1 evaluate the membrane forces, 0 hold the last
+// ones (Sec. 2.6), 2 decide on the device (adaptive separation); v.integ
+// selects the vertex integrator.
 template <typename R>
-void enqueue_step(hemo_sim *s, const View<R> &v, int parity, bool force, cudaStream_t st) {
+void enqueue_step(hemo_sim *s, const View<R> &v, int parity, int force, cudaStream_t st) {
     auto mark = [&](int k) {
         if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
     };
     mark(HEMO_PHASE_MEMBRANE);
     if (s->ncell) {
         // (the bin counts start at zero: the previous scan reset them)
-        if (force) launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
-        else launch_hold_bins<R>(v, st);                        // F_v held: anchors and bin counts only
+        if (force == 2) {  // adaptive: both kernels, each runs only on its kind of step
+            launch_adapt_decide(v.adapt, s->force_tol, s->force_every, st);
+            launch_cell_forces<R>(v, 0, nullptr, st);
+            launch_hold_bins<R>(v, st);
+        } else if (force) {
+            launch_cell_forces<R>(v, 0, nullptr, st);  // re-base, A and V, F_v at X^n; anchors and bin counts
+        } else {
+            launch_hold_bins<R>(v, st);  // F_v held: anchors and bin counts only
+        }
     }
     if (v.ind) launch_inside<R>(v, st);  // cell interiors at X^n (internal viscosity)
     mark(HEMO_PHASE_BINS);
@@ -569,14 +587,16 @@ int ensure_ready(hemo_sim *s) {
     return is_f64(s) ? finalize_impl<double>(s) : finalize_impl<float>(s);
 }
 
-// The step variant k = parity + 2 force + 4 integ, captured on first use.
+// The step variant k = parity + 2 force + 4 integ, or 12 + parity + 2 integ
+// with the adaptive separation, captured on first use.
 template <typename R>
 int capture_graph(hemo_sim *s, int k) {
     cudaGraph_t g = nullptr;
     View<R> v = make_view<R>(s);
-    v.integ = k >> 2;
+    const bool adaptive = k >= 12;
+    v.integ = adaptive ? (k - 12) >> 1 : k >> 2;
     HEMO_CU(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    enqueue_step<R>(s, v, k & 1, (k >> 1) & 1, s->cap);
+    enqueue_step<R>(s, v, k & 1, adaptive ? 2 : (k >> 1) & 1, s->cap);
     cudaError_t e = cudaStreamEndCapture(s->cap, &g);
     if (e != cudaSuccess) return fail(HEMO_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
     size_t nn = 0;
@@ -885,7 +905,7 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
     int rc = ensure_ready(s);
     if (rc) return rc;
     if (s->steps_done & 1) return fail(HEMO_ERR_STATE, "hemo_record: start at an even step count");
-    if (s->force_every != 1 || s->integrator != HEMO_EULER)
+    if (s->force_every != 1 || s->integrator != HEMO_EULER || s->force_tol >= 0)
         return fail(HEMO_ERR_STATE, "hemo_record: the differentiation form needs forces every step and Euler");
     for (const HostMesh &m : s->meshes)
         if (m.k_local > 0 || m.theta_m > 0)
@@ -1210,6 +1230,15 @@ int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const doubl
     return HEMO_OK;
 }
 
+// the adaptive separation evaluates the forces on the next step again
+static int adapt_restart(hemo_sim *s) {
+    if (!s->adapt) return HEMO_OK;
+    const unsigned long long init[4] = {0ull, 0ull, 0ull, 1ull};
+    HEMO_CU(cudaMemcpyAsync(s->adapt, init, sizeof init, cudaMemcpyHostToDevice, s->stream));
+    HEMO_CU(cudaStreamSynchronize(s->stream));  // (init is on the stack)
+    return HEMO_OK;
+}
+
 int hemo_step(hemo_sim *s, int nsteps) {
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     if (nsteps < 0) return fail(HEMO_ERR_ARG, "nsteps must be >= 0");
@@ -1221,7 +1250,8 @@ int hemo_step(hemo_sim *s, int nsteps) {
     for (int k = 0; k < nsteps; ++k) {
         const bool force = (s->steps_done - s->ts_origin) % s->force_every == 0;
         const int integ = s->integrator == HEMO_AB2 ? (s->have_prev ? 2 : 1) : 0;
-        const int gi = (int)(s->steps_done & 1) + 2 * (int)force + 4 * integ;
+        const int parity = (int)(s->steps_done & 1);
+        const int gi = s->force_tol >= 0 ? 12 + parity + 2 * integ : parity + 2 * (int)force + 4 * integ;
         if (!s->graph[gi]) {
             rc = is_f64(s) ? capture_graph<double>(s, gi) : capture_graph<float>(s, gi);
             if (rc) return rc;
@@ -1252,7 +1282,24 @@ int hemo_set_time_scales(hemo_sim *s, int force_every, int integrator) {
     s->integrator = integrator;
     s->ts_origin = s->steps_done;
     s->have_prev = false;
-    return HEMO_OK;
+    return adapt_restart(s);
+}
+
+int hemo_set_force_tolerance(hemo_sim *s, double delta) {
+    if (!s) return fail(HEMO_ERR_ARG, "null simulation");
+    if (std::isnan(delta)) return fail(HEMO_ERR_ARG, "hemo_set_force_tolerance: delta is NaN");
+    if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_force_tolerance: not while recording for the reverse sweep");
+    if (s->le && delta >= 0) return fail(HEMO_ERR_STATE, "hemo_set_force_tolerance: not with the Lees-Edwards boundary");
+    int rc = ensure_ready(s);
+    if (rc) return rc;
+    if (delta >= 0 && !s->adapt) {
+        s->off_eval = dalloc(s, rsize(s) * 3 * (size_t)std::max(s->nv, 1));
+        s->adapt = (unsigned long long *)dalloc(s, 4 * sizeof(unsigned long long));
+        if (!s->off_eval || !s->adapt) return fail(HEMO_ERR_OOM, "adaptive separation buffers");
+    }
+    s->force_tol = delta < 0 ? -1.0 : delta;
+    s->ts_origin = s->steps_done;
+    return adapt_restart(s);
 }
 
 int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
@@ -1286,8 +1333,8 @@ int hemo_set_lees_edwards(hemo_sim *s, double U) {
     if (s->steps_done || s->le) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: only once, before the first step");
     if (!s->per[0] || !s->per[1] || !s->per[2] || s->has_walls)
         return fail(HEMO_ERR_ARG, "hemo_set_lees_edwards: needs a lattice periodic on every axis without walls");
-    if (s->force_every != 1 || s->integrator != HEMO_EULER)
-        return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: needs forces every step with Euler (hemo_set_time_scales)");
+    if (s->force_every != 1 || s->integrator != HEMO_EULER || s->force_tol >= 0)
+        return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: needs forces every step with Euler (hemo_set_time_scales, hemo_set_force_tolerance)");
     if (s->rec) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: not while recording");
     if (s->visc_ratio != 1.0) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: not with an internal viscosity ratio other than 1");
     s->f2 = dalloc(s, tsize(s) * Q * (size_t)s->N);
@@ -1429,6 +1476,7 @@ struct StateHeader {
     int64_t N, nv, ncell, precision, le;
     int64_t steps_done, ts_origin;
     int64_t force_every, integrator, have_prev;
+    double force_tol;        // adaptive separation (< 0: off)
     int64_t sections;        // number of buffers that follow
 };
 constexpr uint64_t STATE_MAGIC = 0x314154534f4d4548ull;  // the bytes "HEMOSTA1" in little-endian order
@@ -1448,6 +1496,10 @@ std::vector<std::pair<void *, size_t>> state_sections(hemo_sim *s) {
         v.push_back({s->Uprev, rs * 3 * nv});           // previous vertex velocity (Adams-Bashforth)
     }
     if (s->le) v.push_back({s->le_n, sizeof(long long)});  // Lees-Edwards step counter
+    if (s->force_tol >= 0) {  // adaptive separation: offsets at the last evaluation, decision words
+        v.push_back({s->off_eval, rs * 3 * (size_t)std::max(s->nv, 1)});
+        v.push_back({s->adapt, 4 * sizeof(unsigned long long)});
+    }
     return v;
 }
 
@@ -1492,6 +1544,7 @@ int hemo_save_state(hemo_sim *s, void *buf, size_t bytes) {
     h.force_every = s->force_every;
     h.integrator = s->integrator;
     h.have_prev = s->have_prev;
+    h.force_tol = s->force_tol;
     const auto sec = state_sections(s);
     h.sections = (int64_t)sec.size();
     HEMO_CU(cudaMemcpyAsync(buf, &h, sizeof h, cudaMemcpyDefault, s->stream));
@@ -1513,11 +1566,17 @@ int hemo_load_state(hemo_sim *s, const void *buf, size_t bytes) {
     if (h.magic != STATE_MAGIC) return fail(HEMO_ERR_ARG, "hemo_load_state: not a saved state");
     if (h.N != s->N || h.nv != s->nv || h.ncell != s->ncell || h.precision != s->precision || h.le != (int64_t)s->le)
         return fail(HEMO_ERR_ARG, "hemo_load_state: the state belongs to a simulation of other sizes, precision or boundary");
+    if (h.force_every < 1 || (h.integrator != HEMO_EULER && h.integrator != HEMO_AB2) || h.steps_done < 0 ||
+        std::isnan(h.force_tol))
+        return fail(HEMO_ERR_ARG, "hemo_load_state: corrupt header");
+    if (h.force_tol >= 0) {  // the adaptive separation's buffers, then its state
+        if ((rc = hemo_set_force_tolerance(s, h.force_tol))) return rc;
+    } else {
+        s->force_tol = -1.0;
+    }
     const auto sec = state_sections(s);
     if (h.sections != (int64_t)sec.size() || bytes < state_size(s))
         return fail(HEMO_ERR_ARG, "hemo_load_state: buffer size does not match the simulation");
-    if (h.force_every < 1 || (h.integrator != HEMO_EULER && h.integrator != HEMO_AB2) || h.steps_done < 0)
-        return fail(HEMO_ERR_ARG, "hemo_load_state: corrupt header");
     const char *p = (const char *)buf + sizeof h;
     for (auto &x : sec) {
         HEMO_CU(cudaMemcpyAsync(x.first, p, x.second, cudaMemcpyDefault, s->stream));
@@ -1569,6 +1628,7 @@ int hemo_set_vertices(hemo_sim *s, const double *verts) {
     if (is_f64(s)) launch_set_vertices<double>(make_view<double>(s), (const double *)s->staging, s->stream);
     else launch_set_vertices<float>(make_view<float>(s), (const double *)s->staging, s->stream);
     HEMO_CU(cudaGetLastError());
+    if ((rc = adapt_restart(s))) return rc;
     return hemo_sync(s);
 }
 

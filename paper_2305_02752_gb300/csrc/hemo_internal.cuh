@@ -137,6 +137,11 @@ template <typename R> struct View {
     // Uprev; 2 Adams-Bashforth X += 3/2 U - 1/2 Uprev and U kept in Uprev
     int integ;
     R *Uprev;                  // nv*3 interpolated velocity of the previous step
+    // adaptive time-scale separation (null when off): offsets at the last
+    // force evaluation, and the device words {largest displacement since it
+    // (FP64 bits), steps since it, evaluate on this step, first step pending}
+    R *off_eval;
+    unsigned long long *adapt;
     // internal viscosity (null when off): per-node indicator of the cell
     // interiors and the toggle counts it is built from; relaxation rate inside
     uint8_t *ind;
@@ -197,6 +202,8 @@ template <typename R> struct AdjView {
 // launchers (R = double for HEMO_F64, float otherwise)
 template <typename R> void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st);
 template <typename R> void launch_hold_bins(const View<R> &v, cudaStream_t st);
+// adaptive separation: decide whether this step evaluates the membrane forces
+void launch_adapt_decide(unsigned long long *adapt, double tol, int every, cudaStream_t st);
 // inside/outside indicator at the current vertex positions into v.ind
 template <typename R> void launch_inside(const View<R> &v, cudaStream_t st);
 // Lees-Edwards boundary: two-array collision and streaming, the coupling of

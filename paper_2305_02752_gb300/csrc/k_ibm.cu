@@ -256,7 +256,7 @@ __device__ __forceinline__ int neighbour_blocks(int b, int nb, int periodic, int
 template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 192; };
 template <typename R>
 __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, const int org[3], int *srow, R *sw,
-                                            R *sF, int *sperm, const float *fscale = nullptr) {
+                                            R *sF, int *sperm, const R *fscale = nullptr) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int i = v.perm[p0 + j];
         int row = 0;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, con
             ok &= b >= 0 && b < BLK;
             row += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
             peskin4(v.anc_t[3 * (size_t)i + d], sw + 12 * j + 4 * d);
-            if (sF) sF[4 * j + d] = fscale ? v.Fv[3 * (size_t)i + d] * (R)fscale[d] : v.Fv[3 * (size_t)i + d];
+            if (sF) sF[4 * j + d] = fscale ? v.Fv[3 * (size_t)i + d] * fscale[d] : v.Fv[3 * (size_t)i + d];
         }
         srow[j] = ok ? row : -1;
         if (sperm) sperm[j] = i;
@@ -278,25 +278,29 @@ __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, con
 // stencil and add four x-neighbours into the bin's 11^3 shared tile.  The
 // tile is written out whole (compact [3][11^3]) for the owners to gather.
 //
-// FP32: the tile accumulates in 32-bit fixed point with integer shared
-// atomics (native, unaffected by address collisions, and exact: the sums do
-// not depend on the order of the vertices).  Per bin and component the
-// scale is the power of two 2^e with e = 30 - ceil(log2(max|F| * n / 8)):
-// a node's sum is at most max|F| times the sum of its n weights, each at
-// most 1/8, so |sum| * 2^e <= 2^30.  The quantum is max|F| * n * 2^-33 per
-// contribution, below FP32 rounding of sums of that size.  FP64 accumulates
-// in double.
+// The tile accumulates in fixed point with integer shared atomics (native,
+// unaffected by address collisions, and exact: the sums do not depend on the
+// order of the vertices, so every run gives the same bits).  FP32: 32-bit
+// integers; per bin and component the scale is the power of two 2^e with
+// e = 30 - ceil(log2(max|F| * n / 8)): a node's sum is at most max|F| times
+// the sum of its n weights, each at most 1/8, so |sum| * 2^e <= 2^30, and
+// the quantum, max|F| * n * 2^-33 per contribution, is below the FP32
+// rounding of sums of that size.  FP64: 64-bit integers with 2^62 in place
+// of 2^30 (quantum max|F| n 2^-65, below FP64 rounding).
 template <typename R> struct TileAcc {
-    using T = R;
+    using T = long long;
+    static constexpr int E = 61;  // log2 of the bound minus one
 };
 template <> struct TileAcc<float> {
     using T = int;
+    static constexpr int E = 29;
 };
+__device__ __forceinline__ int fixed_of(float x) { return __float2int_rn(x); }
+__device__ __forceinline__ long long fixed_of(double x) { return __double2ll_rn(x); }
 
 template <typename R>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kernel(View<R> v) {
     using A = typename TileAcc<R>::T;
-    constexpr bool FIXED = std::is_same<A, int>::value;
     constexpr int CAP = Stage<R>::CAP;
     const int k = blockIdx.x;
     const int s = v.start[k], e = v.start[k + 1];
@@ -305,33 +309,33 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
     __shared__ int srow[CAP];
     __shared__ __align__(16) R sw[12 * CAP];
     __shared__ __align__(16) R sF[4 * CAP];
-    __shared__ float smax[3][8];
-    __shared__ float scale[3];
+    __shared__ R smax[3][8];
+    __shared__ R scale[3];
     for (int q = threadIdx.x; q < TILE_SMEM; q += blockDim.x) acc[0][q] = acc[1][q] = acc[2][q] = A(0);
     int org[3];
     bin_origin(v, k, org);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
-    if (FIXED) {  // one scale per component for the whole bin
-        float m[3] = {0.f, 0.f, 0.f};
+    {  // one scale per component for the whole bin
+        R m[3] = {R(0), R(0), R(0)};
         for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
             const int i = v.perm[j];
-            for (int d = 0; d < 3; ++d) m[d] = fmaxf(m[d], fabsf((float)v.Fv[3 * (size_t)i + d]));
+            for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(v.Fv[3 * (size_t)i + d]));
         }
         for (int d = 0; d < 3; ++d) {
-            for (int o = 16; o > 0; o >>= 1) m[d] = fmaxf(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
+            for (int o = 16; o > 0; o >>= 1) m[d] = fmax(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
             if (lane == 0) smax[d][warp] = m[d];
         }
         __syncthreads();
         if (threadIdx.x < 3) {
-            float mm = 0.f;
-            for (int w = 0; w < nw; ++w) mm = fmaxf(mm, smax[threadIdx.x][w]);
-            const float bound = mm * (float)(e - s) * 0.125f;
-            if (!(bound <= 3.0e38f)) {  // non-finite forces
+            R mm = R(0);
+            for (int w = 0; w < nw; ++w) mm = fmax(mm, smax[threadIdx.x][w]);
+            const R bound = mm * R(e - s) * R(0.125);
+            if (!(bound <= R(3.0e38))) {  // non-finite forces
                 atomicOr(v.status, ST_NUMERIC);
-                scale[threadIdx.x] = 0.f;
+                scale[threadIdx.x] = R(0);
             } else {
-                scale[threadIdx.x] = bound > 0.f ? ldexpf(1.f, min(29 - ilogbf(bound), 120)) : 0.f;
+                scale[threadIdx.x] = bound > R(0) ? ldexp(R(1), min(TileAcc<R>::E - ilogb(bound), 120)) : R(0);
             }
         }
         __syncthreads();  // the staging below applies the scale
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
     for (int p0 = s; p0 < e; p0 += CAP) {
         const int n = min(CAP, e - p0);
         if (p0 != s) __syncthreads();
-        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr, FIXED ? scale : nullptr);
+        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr, scale);
         __syncthreads();
         for (int q = 2 * warp + h; q < n; q += 2 * nw) {
             const int row0 = srow[q];
@@ -356,21 +360,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
                 const R wa = wx[a];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    if (FIXED) atomicAdd((int *)&acc[d][row + a], __float2int_rn((float)(f[d] * wa)));
-                    else atomicAdd(&acc[d][row + a], f[d] * wa);
+                    if constexpr (sizeof(A) == 4) atomicAdd((int *)&acc[d][row + a], fixed_of(f[d] * wa));
+                    else atomicAdd((unsigned long long *)&acc[d][row + a], (unsigned long long)fixed_of(f[d] * wa));
                 }
             }
         }
     }
     __syncthreads();
     R *out = v.tiles + (size_t)k * 3 * TILE3;
-    float inv[3] = {1.f, 1.f, 1.f};
-    if (FIXED)
-        for (int d = 0; d < 3; ++d) inv[d] = scale[d] > 0.f ? 1.f / scale[d] : 0.f;
+    R inv[3];
+    for (int d = 0; d < 3; ++d) inv[d] = scale[d] > R(0) ? R(1) / scale[d] : R(0);  // (exact: powers of two)
     TileWalk tw(threadIdx.x, blockDim.x);
     for (int q = threadIdx.x; q < TILE3; q += blockDim.x, tw.next()) {
         const int sidx = tw.l0 + TS_Y * tw.l1 + TS_Z * tw.l2;
-        for (int d = 0; d < 3; ++d) out[d * TILE3 + q] = FIXED ? (R)((float)acc[d][sidx] * inv[d]) : (R)acc[d][sidx];
+        for (int d = 0; d < 3; ++d) out[d * TILE3 + q] = (R)acc[d][sidx] * inv[d];
     }
 }
 
@@ -524,30 +527,67 @@ __global__ void __launch_bounds__(256) spread_gather3_kernel(View<R> v) {
 // INTEG 0 Euler; 1 Euler, keeping U; 2 the two-step Adams-Bashforth form
 // with the kept velocity of the previous step, keeping U.  All loads are
 // issued before the stores (off and Uprev are distinct buffers).
+//
+// With the adaptive separation on (v.off_eval set) it returns the vertex's
+// displacement since the last force evaluation, |off - off_eval| of the new
+// offsets (held steps do not re-base, so that is X - X_eval); else 0.
 template <int INTEG, typename R>
-__device__ __forceinline__ void move_vertex(const View<R> &v, int i, R U0, R U1, R U2) {
+__device__ __forceinline__ double move_vertex(const View<R> &v, int i, R U0, R U1, R U2) {
     R *o = v.off + 3 * (size_t)i;
     const R x0 = o[0], x1 = o[1], x2 = o[2];
+    R n0, n1, n2;
     if constexpr (INTEG == 0) {
-        o[0] = x0 + U0;
-        o[1] = x1 + U1;
-        o[2] = x2 + U2;
+        n0 = x0 + U0;
+        n1 = x1 + U1;
+        n2 = x2 + U2;
     } else {
         R *p = v.Uprev + 3 * (size_t)i;
         if constexpr (INTEG == 2) {
             const R p0 = p[0], p1 = p[1], p2 = p[2];
-            o[0] = x0 + (R(1.5) * U0 - R(0.5) * p0);
-            o[1] = x1 + (R(1.5) * U1 - R(0.5) * p1);
-            o[2] = x2 + (R(1.5) * U2 - R(0.5) * p2);
+            n0 = x0 + (R(1.5) * U0 - R(0.5) * p0);
+            n1 = x1 + (R(1.5) * U1 - R(0.5) * p1);
+            n2 = x2 + (R(1.5) * U2 - R(0.5) * p2);
         } else {
-            o[0] = x0 + U0;
-            o[1] = x1 + U1;
-            o[2] = x2 + U2;
+            n0 = x0 + U0;
+            n1 = x1 + U1;
+            n2 = x2 + U2;
         }
         p[0] = U0;
         p[1] = U1;
         p[2] = U2;
     }
+    o[0] = n0;
+    o[1] = n1;
+    o[2] = n2;
+    if (!v.off_eval) return 0.0;
+    const R *e = v.off_eval + 3 * (size_t)i;
+    const R d0 = n0 - e[0], d1 = n1 - e[1], d2 = n2 - e[2];
+    return (double)sqrt_r(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// the largest displacement of a warp's vertices into the adaptive word (as
+// double bits: non-negative doubles order as their bit patterns); every
+// lane calls it
+__device__ __forceinline__ void adapt_max(unsigned long long *adapt, double d) {
+    unsigned long long m = (unsigned long long)__double_as_longlong(d);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+        m = q > m ? q : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(adapt, m);
+}
+
+// Adaptive separation, once per step before the membrane kernels: evaluate
+// the forces on the first step, when `every` steps have passed since the last
+// evaluation, or when a vertex has moved more than tol since it; the
+// displacement word is cleared for the coming step's interpolation.
+__global__ void adapt_decide_kernel(unsigned long long *a, double tol, int every) {
+    const bool eval = a[3] || a[1] >= (unsigned long long)every || __longlong_as_double((long long)a[0]) > tol;
+    a[2] = eval ? 1ull : 0ull;
+    a[1] = eval ? 1ull : a[1] + 1ull;
+    a[3] = 0ull;
+    a[0] = 0ull;
 }
 
 // Anchors, keys and bin counts on a step between two membrane-force
@@ -555,6 +595,7 @@ __device__ __forceinline__ void move_vertex(const View<R> &v, int i, R U0, R U1,
 // X = (hi + lo of the centroid of the last re-base) + offset.
 template <typename R>
 __global__ void __launch_bounds__(256) hold_bins_kernel(View<R> v) {
+    if (v.adapt && v.adapt[2]) return;  // adaptive separation: this step evaluates the forces
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.nv) return;
     const R *cs = v.csp + 6 * (size_t)v.vcell[i];
@@ -633,7 +674,9 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v, int parts) 
                 U1 += __shfl_xor_sync(0xffffffffu, U1, o);
                 U2 += __shfl_xor_sync(0xffffffffu, U2, o);
             }
-            if (row0 >= 0 && (lane & 15) == 0) move_vertex<INTEG>(v, sperm[q], U0, U1, U2);
+            double dmax = 0.0;
+            if (row0 >= 0 && (lane & 15) == 0) dmax = move_vertex<INTEG>(v, sperm[q], U0, U1, U2);
+            if (v.adapt) adapt_max(v.adapt, dmax);
         }
     }
 }
@@ -693,6 +736,7 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
     }
     cp_async_wait_all();
     __syncthreads();
+    double dmax = 0.0;  // adaptive separation: this thread's largest displacement
     for (int j = jf; j < e; j += blockDim.x) {
         int i;
         int ai[3];
@@ -739,8 +783,9 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
                     U2 += wa * t.z;
                 }
             }
-        move_vertex<INTEG>(v, i, U0, U1, U2);
+        dmax = fmax(dmax, move_vertex<INTEG>(v, i, U0, U1, U2));
     }
+    if (v.adapt) adapt_max(v.adapt, dmax);
 }
 
 // Peskin weights and their derivatives d/dt for the fraction t
@@ -1006,6 +1051,10 @@ void launch_interpolate(const View<R> &v, cudaStream_t st) {
 template <typename R>
 void launch_hold_bins(const View<R> &v, cudaStream_t st) {
     if (v.nv) hold_bins_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v);
+}
+
+void launch_adapt_decide(unsigned long long *adapt, double tol, int every, cudaStream_t st) {
+    adapt_decide_kernel<<<1, 1, 0, st>>>(adapt, tol, every);
 }
 
 template <typename R>

@@ -545,34 +545,29 @@ constexpr int PAIR_X = 2 * NODE_BX;  // nodes of a row per warp
 
 // The 19 pair words arriving at nodes x0, x0 + 1 (low half: node x0).
 // LAYOUT 0: natural order; 1: after an even step (direction i from slot
-// opp(i) of the nodes x - c_i).  row0: index of the row's node x = 0;
-// o: the row's y and z neighbour offsets; xb, xa: the nodes before x0 and
-// after x0 + 1 (wrapped).
+// opp(i) of the nodes x - c_i).  Where that is one node off the pair
+// (cx_i != 0), the two aligned words around it are loaded and the halves
+// picked, so that every load is independent and all are in flight at once.
+// row0: index of the row's node x = 0; o: the row's y and z neighbour
+// offsets; xb2, xa2: the pair positions before and after x0 (wrapped).
 template <typename T, int LAYOUT, typename I>
-__device__ __forceinline__ void load_pair_words(const View<float> &v, int n0, int row0, int xb, int xa, const Nbr &o,
-                                                bool act, bool first, bool last, unsigned w[Q]) {
+__device__ __forceinline__ void load_pair_words(const View<float> &v, int n0, int row0, int xb2, int xa2, const Nbr &o,
+                                                bool act, unsigned w[Q]) {
     const T *f = (const T *)v.f;
     const I N = (I)v.N;
+    unsigned e[Q];  // the second word of the directions read one node off
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (LAYOUT == 0 || cx(i) == 0) {
-            const int roff = LAYOUT == 0 ? 0 : o.of(0, -cy(i), -cz(i));
-            const int slot = LAYOUT == 0 ? i : opp(i);
-            w[i] = act ? ld_pair(f + (I)slot * N + (I)(n0 + roff)) : 0u;
-        } else {
-            const int roff = o.of(0, -cy(i), -cz(i));
-            const T *src = f + (I)opp(i) * N;
-            const unsigned own = act ? ld_pair(src + (I)(n0 + roff)) : 0u;  // values at x0, x0 + 1
-            if (cx(i) > 0) {  // from x0 - 1 and x0
-                const unsigned left = __shfl_up_sync(0xffffffffu, own, 1);
-                const unsigned vb = first ? (act ? ld_one(src + (I)(row0 + roff + xb)) : 0u) : (left >> 16);
-                w[i] = vb | (own << 16);
-            } else {  // from x0 + 1 and x0 + 2
-                const unsigned right = __shfl_down_sync(0xffffffffu, own, 1);
-                const unsigned va = last ? (act ? ld_one(src + (I)(row0 + roff + xa)) : 0u) : (right & 0xffffu);
-                w[i] = (own >> 16) | (va << 16);
-            }
-        }
+        const int roff = LAYOUT == 0 ? 0 : o.of(0, -cy(i), -cz(i));
+        const T *src = f + (I)(LAYOUT == 0 ? i : opp(i)) * N;
+        w[i] = act ? ld_pair(src + (I)(n0 + roff)) : 0u;  // values at x0, x0 + 1
+        if (LAYOUT == 1 && cx(i) != 0)  // values at x0 - 2, x0 - 1 or x0 + 2, x0 + 3
+            e[i] = act ? ld_pair(src + (I)(row0 + roff + (cx(i) > 0 ? xb2 : xa2))) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (LAYOUT == 1 && cx(i) > 0) w[i] = (e[i] >> 16) | (w[i] << 16);          // from x0 - 1, x0
+        else if (LAYOUT == 1 && cx(i) < 0) w[i] = (w[i] >> 16) | (e[i] << 16);     // from x0 + 1, x0 + 2
     }
 }
 
@@ -598,7 +593,7 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY) collide_pair_kernel(View<fl
     const Nbr o = nbr_at(v, x0, y, z);
     const RowRefs rr = row_refs<T>(v, y, z, PARITY == 1);
     unsigned w[Q];
-    load_pair_words<T, PARITY, I>(v, n0, row0, xb, xa, o, act, first, last, w);
+    load_pair_words<T, PARITY, I>(v, n0, row0, x0 == 0 ? nx - 2 : x0 - 2, xa, o, act, w);
     const size_t N = (size_t)v.N;
     const float2 F0 = act ? *reinterpret_cast<const float2 *>(v.F + n0) : make_float2(0.f, 0.f);
     const float2 F1 = act ? *reinterpret_cast<const float2 *>(v.F + N + n0) : make_float2(0.f, 0.f);
@@ -687,12 +682,11 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_pair_kernel(View<fl
             }
         return;
     }
-    const bool first = lane == 0, last = lane == 31 || x0 + 2 >= nx;
-    const int xb = x0 == 0 ? nx - 1 : x0 - 1, xa = x0 + 2 >= nx ? 0 : x0 + 2;
+    const int xa = x0 + 2 >= nx ? 0 : x0 + 2;
     const Nbr o = nbr_at(v, x0, y, z);
     const RowRefs rr = row_refs<T>(v, y, z, LAYOUT == 1);
     unsigned w[Q];
-    load_pair_words<T, LAYOUT, I>(v, n0, row0, xb, xa, o, act, first, last, w);
+    load_pair_words<T, LAYOUT, I>(v, n0, row0, x0 == 0 ? nx - 2 : x0 - 2, xa, o, act, w);
     if (!act) return;
     const size_t N = (size_t)v.N;
     float u[2][3];

@@ -179,6 +179,7 @@ template <typename R> __device__ __forceinline__ void st4(R *p, R x, R y, R z, R
 
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<R> v, int mode, double *stats) {
+    if (mode == 0 && v.adapt && !v.adapt[2]) return;  // adaptive separation: the forces are held on this step
     const int c = blockIdx.x;
     const MeshDev<R> m = v.meshes[v.cell_type[c]];
     const int first = v.cell_first[c];
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
             for (int k = 0; k < 3; ++k) {
                 o[k] = r[k];
                 if (v.off_rec) v.off_rec[3 * (size_t)(first + i) + k] = r[k];
+                if (v.off_eval) v.off_eval[3 * (size_t)(first + i) + k] = r[k];  // positions of this evaluation
             }
         }
     };

@@ -72,6 +72,7 @@ def lib():
         'hemo_add_cells': ([vp, C.POINTER(hemo_mesh_desc), i, vp, vp, C.POINTER(i)], i),
         'hemo_step': ([vp, i], i),
         'hemo_set_time_scales': ([vp, i, i], i),
+        'hemo_set_force_tolerance': ([vp, d], i),
         'hemo_set_viscosity_ratio': ([vp, d], i),
         'hemo_set_lees_edwards': ([vp, d], i),
         'hemo_get_inside': ([vp, vp], i),
@@ -108,6 +109,7 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the load test)."""
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_set_time_scales',
+            'hemo_set_force_tolerance',
             'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_set_lees_edwards', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
@@ -284,6 +286,12 @@ class Simulation:
         """Membrane forces every `force_every` steps, held in between, and
         the vertex integrator 'euler' or 'ab2' (Sec. 2.6), from this step on."""
         check(lib().hemo_set_time_scales(self.handle, int(force_every), INTEGRATORS[integrator]))
+
+    def set_force_tolerance(self, delta):
+        """Adaptive separation: evaluate the membrane forces when a vertex
+        has moved more than delta since the last evaluation (or
+        force_every steps have passed); delta < 0: constant schedule."""
+        check(lib().hemo_set_force_tolerance(self.handle, float(delta)))
 
     def set_viscosity_ratio(self, ratio):
         """Viscosity inside cells relative to the plasma (1 = off): inside

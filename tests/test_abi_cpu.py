@@ -195,6 +195,11 @@ def test_null_handles():
     assert L.hemo_set_viscosity_ratio(None, 5.0) == hemo.HEMO_ERR_ARG
     assert L.hemo_get_inside(None, None) == hemo.HEMO_ERR_ARG
     assert L.hemo_set_lees_edwards(None, 0.01) == hemo.HEMO_ERR_ARG
+    assert L.hemo_set_force_tolerance(None, 0.1) == hemo.HEMO_ERR_ARG
+    n = C.c_size_t(7)
+    assert L.hemo_state_bytes(None, C.byref(n)) == hemo.HEMO_ERR_ARG and n.value == 7
+    assert L.hemo_save_state(None, None, 0) == hemo.HEMO_ERR_ARG
+    assert L.hemo_load_state(None, None, 0) == hemo.HEMO_ERR_ARG
     L.hemo_destroy(None)
 
 
