@@ -89,10 +89,12 @@ typedef struct {
  * same.  Off by default: the per-node kernel is the faster of the two. */
 enum { HEMO_OPT_STAGED_COLLISION = 1u };
 
-/* HEMO_OPT_NODE_COLLISION: with 16-bit storage, collide one node per thread
- * instead of two (the two-node kernels need nx even).  The results are the
- * same bits; the option exists to compare the two. */
-enum { HEMO_OPT_NODE_COLLISION = 2u };
+/* 16-bit storage with nx even computes the post-streaming velocity two
+ * nodes per thread (32-bit population pairs) and collides one node per
+ * thread.  HEMO_OPT_NODE_COLLISION: one node per thread in both kernels;
+ * HEMO_OPT_PAIR_COLLISION: two nodes per thread in both.  The results are the
+ * same bits in every case; the options exist to compare the kernels. */
+enum { HEMO_OPT_NODE_COLLISION = 2u, HEMO_OPT_PAIR_COLLISION = 8u };
 
 /* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the staged
  * collision (HEMO_OPT_STAGED_COLLISION, 16-bit storage, odd steps).  Its

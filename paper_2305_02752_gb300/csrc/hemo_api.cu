@@ -274,7 +274,12 @@ View<R> make_view(hemo_sim *s) {
     v.erows = s->erows;
     v.nerows = s->nerows;
     v.rref = s->rref;
-    v.node_pairs = tsize(s) == 2 && (s->nx % 2) == 0 && !(s->options & HEMO_OPT_NODE_COLLISION);
+    // 16-bit storage, nx even: the velocity pass two nodes per thread (the
+    // faster form, measured); the collision two nodes per thread only on
+    // request (the per-node kernel is faster on odd steps and as fast on even)
+    v.node_pairs = 0;
+    if (tsize(s) == 2 && (s->nx % 2) == 0 && !(s->options & HEMO_OPT_NODE_COLLISION))
+        v.node_pairs = PAIR_MOMENTS | ((s->options & HEMO_OPT_PAIR_COLLISION) ? PAIR_COLLIDE : 0);
     v.stalled_wait_test = (s->options & HEMO_OPT_TEST_STALLED_WAIT) ? 1 : 0;
     for (int d = 0; d < 3; ++d) {
         v.g[d] = R(s->g[d]);

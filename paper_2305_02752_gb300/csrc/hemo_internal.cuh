@@ -19,6 +19,7 @@ constexpr unsigned ST_NUMERIC = 1u;
 constexpr unsigned ST_DOMAIN = 2u;
 constexpr unsigned ST_TIMEOUT = 4u;  // a pipeline wait gave up
 constexpr float U_LIMIT2 = 0.09f;   // |u|^2 above which the step is unstable
+constexpr int PAIR_MOMENTS = 1, PAIR_COLLIDE = 2;  // View::node_pairs bits
 
 // ---------------------------------------------------------------------------
 // D3Q19 in the library's order: 0 rest; 1..6 = +x -x +y -y +z -z; 7..18 =
@@ -169,7 +170,7 @@ template <typename R> struct View {
     // (P, M) of the stored populations (see k_lattice.cu); all zero when no
     // reference is set.  Null for 4- and 8-byte storage.
     const float2 *rref;
-    int node_pairs;            // 16-bit storage: collide two nodes per thread (nx even)
+    int node_pairs;            // 16-bit storage, nx even: PAIR_* bits, kernels that take two nodes per thread
     int stalled_wait_test;     // staged collision: first wait on a barrier nothing completes (HEMO_OPT_TEST_STALLED_WAIT)
     // a buffer whose contents are dead: the kernel drops its full 128-byte
     // lines from L2 without writing them back (null / 0 = nothing to drop)

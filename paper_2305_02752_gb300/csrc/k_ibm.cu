@@ -104,31 +104,49 @@ __global__ void anchor_count_kernel(View<R> v) {
     if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(v.counts + key, __popc(grp));
 }
 
-// exclusive scan of the block counts by one CTA of 1024 threads; the counts
+// exclusive scan of the block counts by one CTA of 1024 threads, over tiles
+// of 1024 consecutive counts (coalesced loads; warp shuffles within a warp,
+// the 32 warp totals by warp 0, a running carry between tiles; the next
+// tile's counts are loaded before the current one is scanned); the counts
 // are reset to zero for the next binning
 __global__ void __launch_bounds__(1024) scan_kernel(int *counts, int *start, int *cursor, int nbins) {
-    __shared__ int part[1024];
-    const int per = (nbins + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    const int hi = min(lo + per, nbins);
-    int s = 0;
-    for (int k = lo; k < hi; ++k) s += counts[k];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
-        const int add = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __shared__ int wsum[32];
+    __shared__ int carry_s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int carry = 0;
+    int next = t < nbins ? counts[t] : 0;
+    for (int base = 0; base < nbins; base += 1024) {
+        const int k = base + t, c = next;
+        if (base + 1024 + t < nbins) next = counts[base + 1024 + t];
+        int x = c;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[threadIdx.x] += add;
+        if (w == 0) {  // the warp totals' inclusive scan
+            int y = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            wsum[lane] = y;
+            if (lane == 31) carry_s = y;
+        }
         __syncthreads();
+        const int excl = carry + (w ? wsum[w - 1] : 0) + x - c;
+        if (k < nbins) {
+            start[k] = excl;
+            cursor[k] = excl;
+            counts[k] = 0;
+        }
+        carry += carry_s;
+        __syncthreads();  // (wsum and carry_s are rewritten by the next tile)
     }
-    int run = part[threadIdx.x] - s;
-    for (int k = lo; k < hi; ++k) {
-        start[k] = run;
-        cursor[k] = run;
-        run += counts[k];
-        counts[k] = 0;
-    }
-    if (threadIdx.x == 1023) start[nbins] = part[1023];
+    if (t == 0) start[nbins] = carry;
 }
 
 // scatter with per-block cursors; lanes of a warp with the same key reserve
@@ -253,7 +271,8 @@ __device__ __forceinline__ int neighbour_blocks(int b, int nb, int periodic, int
 // per component if given).  The per-vertex loops below then touch
 // shared memory only.  Chunk size by precision keeps the FP64 kernels within
 // 48 KB of static shared memory.
-template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 192; };
+// (FP32: 240 keeps the spreading kernel at six CTAs per SM)
+template <typename R> struct Stage { static constexpr int CAP = sizeof(R) == 8 ? 32 : 240; };
 template <typename R>
 __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, const int org[3], int *srow, R *sw,
                                             R *sF, int *sperm, const R *fscale = nullptr) {
@@ -316,11 +335,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
     bin_origin(v, k, org);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int h = lane >> 4, b = lane & 3, c = (lane >> 2) & 3;
+    // A bin of at most CAP vertices is staged once, before the scale is known
+    // (its forces unscaled; the scale is applied in the loop below, exactly,
+    // being a power of two), which saves a pass over the forces; larger bins
+    // take that pass first and are staged in chunks of equal size.
+    const bool one = e - s <= CAP;
+    if (one) stage_chunk(v, s, e - s, org, srow, sw, sF, (int *)nullptr);
     {  // one scale per component for the whole bin
         R m[3] = {R(0), R(0), R(0)};
-        for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
-            const int i = v.perm[j];
-            for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(v.Fv[3 * (size_t)i + d]));
+        if (one) {
+            for (int j = threadIdx.x; j < e - s; j += blockDim.x)  // (the forces this thread staged)
+                for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(sF[4 * j + d]));
+        } else {
+            for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
+                const int i = v.perm[j];
+                for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(v.Fv[3 * (size_t)i + d]));
+            }
         }
         for (int d = 0; d < 3; ++d) {
             for (int o = 16; o > 0; o >>= 1) m[d] = fmax(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
@@ -338,13 +368,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
                 scale[threadIdx.x] = bound > R(0) ? ldexp(R(1), min(TileAcc<R>::E - ilogb(bound), 120)) : R(0);
             }
         }
-        __syncthreads();  // the staging below applies the scale
+        __syncthreads();  // the staging below or the loop applies the scale
     }
-    for (int p0 = s; p0 < e; p0 += CAP) {
-        const int n = min(CAP, e - p0);
-        if (p0 != s) __syncthreads();
-        stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr, scale);
-        __syncthreads();
+    const R sc[3] = {one ? scale[0] : R(1), one ? scale[1] : R(1), one ? scale[2] : R(1)};
+    const int nch = (e - s + CAP - 1) / CAP, csz = (e - s + nch - 1) / nch;
+    for (int p0 = s; p0 < e; p0 += csz) {
+        const int n = min(csz, e - p0);
+        if (!one) {
+            if (p0 != s) __syncthreads();
+            stage_chunk(v, p0, n, org, srow, sw, sF, (int *)nullptr, scale);
+            __syncthreads();
+        }
         for (int q = 2 * warp + h; q < n; q += 2 * nw) {
             const int row0 = srow[q];
             if (row0 < 0) continue;  // vertex outside the lattice (domain status already raised)
@@ -352,8 +386,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
             const R wyz = w[4 + b] * w[8 + c];
             R wx[4], fq[4];
             ld4v(w, wx);
-            ld4v(sF + 4 * q, fq);  // (times the fixed-point scale)
-            const R f[3] = {fq[0] * wyz, fq[1] * wyz, fq[2] * wyz};
+            ld4v(sF + 4 * q, fq);  // (times the fixed-point scale, or scaled here)
+            const R f[3] = {(fq[0] * sc[0]) * wyz, (fq[1] * sc[1]) * wyz, (fq[2] * sc[2]) * wyz};
             const int row = row0 + TS_Y * b + TS_Z * c;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
@@ -499,22 +533,28 @@ __global__ void __launch_bounds__(256) spread_gather3_kernel(View<R> v) {
             ps[d][1] = lo ? l[d] + 1 : 0;
             ns[d] = (lo || hi) ? 2 : 1;
         }
-        // at most two slots per axis: fixed trip counts keep the tables in registers
+        // at most two slots per axis: fixed trip counts keep the tables in
+        // registers; the tile addresses of all eight (slot x, y, z) choices
+        // are formed first and the loads issued predicated, so that they are
+        // all in flight together (summed in the same order, iz, iy, ix)
+        const R *src[8];
+        bool on[8];
 #pragma unroll
-        for (int iz = 0; iz < 2; ++iz)
+        for (int m = 0; m < 8; ++m) {
+            const int ix = m & 1, iy = (m >> 1) & 1, iz = m >> 2;
+            const bool in = iz < ns[2] && iy < ns[1] && ix < ns[0];
+            const int kk = in ? nbin[9 * sl[2][iz] + 3 * sl[1][iy] + sl[0][ix]] : -1;
+            on[m] = kk >= 0;
+            src[m] = v.tiles + (size_t)(kk < 0 ? 0 : kk) * 3 * TILE3 + (ps[0][ix] + TILE * (ps[1][iy] + TILE * ps[2][iz]));
+        }
 #pragma unroll
-            for (int iy = 0; iy < 2; ++iy)
-#pragma unroll
-                for (int ix = 0; ix < 2; ++ix) {
-                    if (iz >= ns[2] || iy >= ns[1] || ix >= ns[0]) continue;
-                    const int kk = nbin[9 * sl[2][iz] + 3 * sl[1][iy] + sl[0][ix]];
-                    if (kk < 0) continue;
-                    const R *tt = v.tiles + (size_t)kk * 3 * TILE3;
-                    const int ti = ps[0][ix] + TILE * (ps[1][iy] + TILE * ps[2][iz]);
-                    f0 += tt[ti];
-                    f1 += tt[TILE3 + ti];
-                    f2 += tt[2 * TILE3 + ti];
-                }
+        for (int m = 0; m < 8; ++m) {
+            if (on[m]) {
+                f0 += src[m][0];
+                f1 += src[m][TILE3];
+                f2 += src[m][2 * TILE3];
+            }
+        }
         const size_t n = (size_t)x + (size_t)v.nx * ((size_t)y + (size_t)v.ny * z);
         const bool wall = !v.spread_all_nodes && (v.ntype[n] & 0x7f);
         v.F[n] = wall ? R(0) : v.g[0] + f0;

@@ -927,7 +927,7 @@ dim3 node_grid(const View<R> &v) {
 template <typename T, typename R, int PARITY, typename I, bool VISC>
 void launch_collide_as(const View<R> &v, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value && sizeof(T) == 2) {
-        if (v.node_pairs) {
+        if (v.node_pairs & PAIR_COLLIDE) {
             const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
             collide_pair_kernel<T, PARITY, I, VISC><<<g, dim3(NODE_BX, NODE_BY), 0, st>>>(v);
             return;
@@ -980,7 +980,7 @@ cudaError_t set_tile_smem_limit(int precision, int bytes) {
 template <typename T, typename R, int LAYOUT, typename I>
 void launch_moments_as(const View<R> &v, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value && sizeof(T) == 2) {
-        if (v.node_pairs) {
+        if (v.node_pairs & PAIR_MOMENTS) {
             const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
             moments_pair_kernel<T, LAYOUT, I><<<g, dim3(NODE_BX, NODE_BY), 0, st>>>(v);
             return;

@@ -391,13 +391,15 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         const V3<R> pi = xyz(ld4(xs + 4 * i));
         V3<R> f = {R(0), R(0), R(0)};
         int4 g = __ldg(m.vfan + i);  // slot 0: the last entry
+        int4 gn = __ldg(m.vfan + (size_t)m.nv + i);  // slot 1, requested ahead (its L2 latency overlaps slot 0's use)
         Q4<R> ap = ld4(tn + 4 * g.x);  // T_k-1: n / |n|^2 and |n|
         V3<R> xp = xyz(ld4(xs + 4 * g.y));  // position of j_k-1
         int op = g.w;  // edge of T_k-1 opposite i
         int tp = g.x;  // T_k-1
         for (int k = 1; k <= m.maxv; ++k) {
-            g = __ldg(m.vfan + (size_t)k * m.nv + i);
+            g = gn;
             if (g.x < 0) break;
+            if (k < m.maxv) gn = __ldg(m.vfan + (size_t)(k + 1) * m.nv + i);  // the next slot, ahead
             const Q4<R> ak = ld4(tn + 4 * g.x);
             const V3<R> xk = xyz(ld4(xs + 4 * g.y));
             const Q4<R> cf = ld4(es + 4 * (g.z >> 1));

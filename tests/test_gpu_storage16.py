@@ -1,8 +1,9 @@
 """16-bit population storage: the two-nodes-per-thread kernels against the
 one-node kernels, and the per-row reference equilibrium.
 
-* Pair kernels (the default for 16-bit storage with nx even) and the
-  per-node kernels (HEMO_OPT_NODE_COLLISION) give the same bits:
+* Two-node kernels (by default the velocity pass for 16-bit storage with nx
+  even; the collision too with HEMO_OPT_PAIR_COLLISION) and the per-node
+  kernels (HEMO_OPT_NODE_COLLISION) give the same bits:
   populations, density and velocity after even and odd step counts, with
   walls on y or z, fully periodic boxes whose rows are not a multiple of the
   64-node warp chunk (ragged last chunks, a row of two nodes), and cells.
@@ -67,11 +68,14 @@ BOXES = {
 @pytest.mark.parametrize('prec', ['f16', 'bf16'])
 @pytest.mark.parametrize('case', sorted(BOXES))
 def test_pair_kernels_match_node_kernels(case, prec, steps):
+    """Default (pair velocity pass), both passes by pairs, both per node."""
     c = BOXES[case]()
     a = _run(c, prec, steps, 0)
     b = _run(c, prec, steps, hemo.HEMO_OPT_NODE_COLLISION)
+    p = _run(c, prec, steps, hemo.HEMO_OPT_PAIR_COLLISION)
     for k in ('f', 'rho', 'u'):
         assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(p[k], b[k]), k
 
 
 @pytest.mark.parametrize('prec', ['f16', 'bf16'])
@@ -79,8 +83,10 @@ def test_pair_kernels_with_cells(prec):
     cfg = small_cell_shear(n=24, steps=9, seed=5)
     a = _run(None, prec, 9, 0, cells=cfg)
     b = _run(None, prec, 9, hemo.HEMO_OPT_NODE_COLLISION, cells=cfg)
+    p = _run(None, prec, 9, hemo.HEMO_OPT_PAIR_COLLISION, cells=cfg)
     for k in ('f', 'u', 'X'):
         assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(p[k], b[k]), k
 
 
 def test_odd_row_length_uses_node_kernels():
