@@ -104,6 +104,13 @@ enum { HEMO_OPT_NODE_COLLISION = 2u, HEMO_OPT_PAIR_COLLISION = 8u };
  * as a real stalled copy would.  Not for production runs. */
 enum { HEMO_OPT_TEST_STALLED_WAIT = 4u };
 
+/* HEMO_OPT_WIDE_INDEX: the lattice kernels form population indices i N + n
+ * in 64 bits on every lattice.  By default they use 32-bit indices whenever
+ * 19 N < 2^32 (N = nx ny nz), and 64-bit ones above, from about 226 M
+ * nodes on.  The results are the same bits; the option exists so that the
+ * 64-bit variants can be tested on small lattices. */
+enum { HEMO_OPT_WIDE_INDEX = 16u };
+
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
  * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
  * F_volume, Sec. 2.3; forms chosen where the paper refers elsewhere):

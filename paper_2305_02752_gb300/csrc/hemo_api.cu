@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hemo_internal.cuh"
 
 using namespace hemo;
@@ -23,6 +25,18 @@ int fail(int code, const std::string &msg) {
     g_err = msg;
     return code;
 }
+
+// NVTX ranges (no-ops unless a profiler is attached): one per API call that
+// launches work, and one per phase of the step where its kernels are
+// enqueued (inside a graph capture: once per captured variant; the device
+// time per phase comes from the event nodes of hemo_set_phase_timing)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+const char *const PHASE_NAMES[HEMO_NUM_PHASES] = {"membrane", "bins", "spread", "collide", "moments", "interp"};
 
 #define HEMO_CU(call)                                                                              \
     do {                                                                                           \
@@ -281,6 +295,7 @@ View<R> make_view(hemo_sim *s) {
     if (tsize(s) == 2 && (s->nx % 2) == 0 && !(s->options & HEMO_OPT_NODE_COLLISION))
         v.node_pairs = PAIR_MOMENTS | ((s->options & HEMO_OPT_PAIR_COLLISION) ? PAIR_COLLIDE : 0);
     v.stalled_wait_test = (s->options & HEMO_OPT_TEST_STALLED_WAIT) ? 1 : 0;
+    v.wide_index = (s->options & HEMO_OPT_WIDE_INDEX) ? 1 : 0;
     for (int d = 0; d < 3; ++d) {
         v.g[d] = R(s->g[d]);
         v.uw[0][d] = R(0);
@@ -342,6 +357,8 @@ template <typename R>
 void enqueue_step(hemo_sim *s, const View<R> &v, int parity, int force, cudaStream_t st) {
     auto mark = [&](int k) {
         if (s->timing) cudaEventRecordWithFlags(s->tev[k], st, cudaEventRecordExternal);
+        if (k != HEMO_PHASE_MEMBRANE) nvtxRangePop();
+        if (k != HEMO_NUM_PHASES) nvtxRangePushA(PHASE_NAMES[k]);
     };
     mark(HEMO_PHASE_MEMBRANE);
     if (s->ncell) {
@@ -905,6 +922,7 @@ int loss_impl(hemo_sim *s, double *loss, double *dL_dverts) {
 extern "C" {
 
 int hemo_record(hemo_sim *s, int checkpoint_every) {
+    NvtxRange nvtx_("hemo_record");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     if (checkpoint_every < 2 || (checkpoint_every & 1)) return fail(HEMO_ERR_ARG, "checkpoint_every must be even and >= 2");
     int rc = ensure_ready(s);
@@ -930,6 +948,7 @@ int hemo_record(hemo_sim *s, int checkpoint_every) {
 }
 
 int hemo_deformation_loss(hemo_sim *s, double *loss, double *dL_dverts) {
+    NvtxRange nvtx_("hemo_deformation_loss");
     if (!s || !loss) return fail(HEMO_ERR_ARG, "null pointer");
     int rc = ensure_ready(s);
     if (rc) return rc;
@@ -937,6 +956,7 @@ int hemo_deformation_loss(hemo_sim *s, double *loss, double *dL_dverts) {
 }
 
 int hemo_backward(hemo_sim *s, const double *dL_dverts, double *grad, int ngrad) {
+    NvtxRange nvtx_("hemo_backward");
     if (!s || !grad || (s->nv && !dL_dverts)) return fail(HEMO_ERR_ARG, "null pointer");
     if (ngrad < 4 * (int)s->meshes.size() + 4) return fail(HEMO_ERR_ARG, "grad needs 4 * mesh types + 4 entries");
     if (!s->rec || s->steps_done <= s->rec_start) return fail(HEMO_ERR_STATE, "hemo_backward: nothing recorded (hemo_record, then hemo_step)");
@@ -1051,6 +1071,7 @@ int plan_rows(hemo_sim *s, const uint8_t *mask) {
 }
 
 int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
+    NvtxRange nvtx_("hemo_create_lattice");
     if (!d || !out) return fail(HEMO_ERR_ARG, "hemo_create_lattice: null pointer");
     *out = nullptr;
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(HEMO_ERR_ARG, "lattice sizes must be >= 1");
@@ -1134,6 +1155,7 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
 }
 
 int hemo_set_velocity(hemo_sim *s, const double *u) {
+    NvtxRange nvtx_("hemo_set_velocity");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     if (s->steps_done) return fail(HEMO_ERR_STATE, "hemo_set_velocity: only before the first step");
     const double *ud = nullptr;
@@ -1156,6 +1178,7 @@ int hemo_set_velocity(hemo_sim *s, const double *u) {
 
 int hemo_add_cells(hemo_sim *s, const hemo_mesh_desc *m, int ncells, const double *centers, const double *rot,
                    int *first_cell_id) {
+    NvtxRange nvtx_("hemo_add_cells");
     if (!s || !m) return fail(HEMO_ERR_ARG, "hemo_add_cells: null pointer");
     if (s->finalized || s->steps_done) return fail(HEMO_ERR_STATE, "hemo_add_cells: only before the first step");
     if (s->meshes.size() >= (size_t)MAX_TYPES) return fail(HEMO_ERR_ARG, "too many mesh types");
@@ -1245,6 +1268,7 @@ static int adapt_restart(hemo_sim *s) {
 }
 
 int hemo_step(hemo_sim *s, int nsteps) {
+    NvtxRange nvtx_("hemo_step");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     if (nsteps < 0) return fail(HEMO_ERR_ARG, "nsteps must be >= 0");
     int rc = ensure_ready(s);
@@ -1333,6 +1357,7 @@ int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
 }
 
 int hemo_set_lees_edwards(hemo_sim *s, double U) {
+    NvtxRange nvtx_("hemo_set_lees_edwards");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     if (!std::isfinite(U) || !(std::fabs(U) < 0.3)) return fail(HEMO_ERR_ARG, "Lees-Edwards velocity must be finite and below 0.3 in magnitude");
     if (s->steps_done || s->le) return fail(HEMO_ERR_STATE, "hemo_set_lees_edwards: only once, before the first step");
@@ -1363,6 +1388,7 @@ int hemo_set_lees_edwards(hemo_sim *s, double U) {
 }
 
 int hemo_get_inside(hemo_sim *s, uint8_t *inside) {
+    NvtxRange nvtx_("hemo_get_inside");
     if (!s || !inside) return fail(HEMO_ERR_ARG, "null pointer");
     int rc = ensure_ready(s);
     if (rc) return rc;
@@ -1389,6 +1415,7 @@ int hemo_get_inside(hemo_sim *s, uint8_t *inside) {
 }
 
 int hemo_sync(hemo_sim *s) {
+    NvtxRange nvtx_("hemo_sync");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     HEMO_CU(cudaStreamSynchronize(s->stream));
     unsigned st = 0;
@@ -1418,6 +1445,7 @@ int hemo_get_lattice_plan(const hemo_sim *s, int *plan) {
 
 int hemo_get_fields(hemo_sim *s, unsigned what, void *rho, void *u, double *verts, double *forces,
                     double *cellstats) {
+    NvtxRange nvtx_("hemo_get_fields");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     int rc = ensure_ready(s);
     if (rc) return rc;
@@ -1455,6 +1483,7 @@ int hemo_get_fields(hemo_sim *s, unsigned what, void *rho, void *u, double *vert
 }
 
 int hemo_get_populations(hemo_sim *s, double *f) {
+    NvtxRange nvtx_("hemo_get_populations");
     if (!s || !f) return fail(HEMO_ERR_ARG, "null pointer");
     int rc = ensure_ready(s);
     if (rc) return rc;
@@ -1533,6 +1562,7 @@ int hemo_state_bytes(hemo_sim *s, size_t *bytes) {
 }
 
 int hemo_save_state(hemo_sim *s, void *buf, size_t bytes) {
+    NvtxRange nvtx_("hemo_save_state");
     int rc = state_ready(s, "hemo_save_state");
     if (rc) return rc;
     if (!buf) return fail(HEMO_ERR_ARG, "hemo_save_state: null buffer");
@@ -1562,6 +1592,7 @@ int hemo_save_state(hemo_sim *s, void *buf, size_t bytes) {
 }
 
 int hemo_load_state(hemo_sim *s, const void *buf, size_t bytes) {
+    NvtxRange nvtx_("hemo_load_state");
     int rc = state_ready(s, "hemo_load_state");
     if (rc) return rc;
     if (!buf) return fail(HEMO_ERR_ARG, "hemo_load_state: null buffer");
@@ -1612,6 +1643,7 @@ int hemo_get_edges(hemo_sim *s, int type, int32_t *edges, int *ne) {
 }
 
 int hemo_set_vertices(hemo_sim *s, const double *verts) {
+    NvtxRange nvtx_("hemo_set_vertices");
     if (!s || !verts) return fail(HEMO_ERR_ARG, "null pointer");
     if (s->steps_done) return fail(HEMO_ERR_STATE, "hemo_set_vertices: only before the first step");
     int rc = ensure_ready(s);
@@ -1638,6 +1670,7 @@ int hemo_set_vertices(hemo_sim *s, const double *verts) {
 }
 
 int hemo_get_bins(hemo_sim *s, int32_t *key, int32_t *perm, int32_t *start) {
+    NvtxRange nvtx_("hemo_get_bins");
     if (!s) return fail(HEMO_ERR_ARG, "null simulation");
     int rc = ensure_ready(s);
     if (rc) return rc;

@@ -172,6 +172,7 @@ template <typename R> struct View {
     const float2 *rref;
     int node_pairs;            // 16-bit storage, nx even: PAIR_* bits, kernels that take two nodes per thread
     int stalled_wait_test;     // staged collision: first wait on a barrier nothing completes (HEMO_OPT_TEST_STALLED_WAIT)
+    int wide_index;            // lattice kernels: 64-bit population indices on any lattice (HEMO_OPT_WIDE_INDEX)
     // a buffer whose contents are dead: the kernel drops its full 128-byte
     // lines from L2 without writing them back (null / 0 = nothing to drop)
     void *dead;
@@ -339,8 +340,9 @@ __device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
 // Lattice kernels over all nodes use a grid of (x chunks of NODE_BX) x (y
 // groups of NODE_BY) x z with blocks of NODE_BX x NODE_BY threads: node
 // coordinates come without integer division and a warp covers 32
-// consecutive nodes of one x-row.
-constexpr int NODE_BX = 32, NODE_BY = 8;
+// consecutive nodes of one x-row.  The velocity pass (few registers, many
+// CTAs per SM) takes y groups of MOM_BY: smaller CTAs, measured faster.
+constexpr int NODE_BX = 32, NODE_BY = 8, MOM_BY = 4;
 
 __device__ __forceinline__ int link_code(uint64_t lk, int i) { return (int)((lk >> (2 * i)) & 3u); }
 

@@ -480,8 +480,8 @@ __device__ __forceinline__ void moments_core(const View<R> &v, int n, const Nbr 
 }
 
 template <typename T, typename R, int LAYOUT, typename I>
-__global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_kernel(View<R> v) {
-    const int x = blockIdx.x * NODE_BX + threadIdx.x, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+__global__ void __launch_bounds__(NODE_BX * MOM_BY) moments_kernel(View<R> v) {
+    const int x = blockIdx.x * NODE_BX + threadIdx.x, y = blockIdx.y * MOM_BY + threadIdx.y, z = blockIdx.z;
     if (x >= v.nx || y >= v.ny) return;
     const int n = x + v.nx * (y + v.ny * z);
     const uint8_t nt = v.ntype[n];
@@ -657,9 +657,9 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY) collide_pair_kernel(View<fl
 // post-streaming velocity of two nodes per thread (16-bit storage); LAYOUT
 // as in load_pops
 template <typename T, int LAYOUT, typename I>
-__global__ void __launch_bounds__(NODE_BX * NODE_BY) moments_pair_kernel(View<float> v) {
+__global__ void __launch_bounds__(NODE_BX * MOM_BY) moments_pair_kernel(View<float> v) {
     const int lane = threadIdx.x;
-    const int x0 = blockIdx.x * PAIR_X + 2 * lane, y = blockIdx.y * NODE_BY + threadIdx.y, z = blockIdx.z;
+    const int x0 = blockIdx.x * PAIR_X + 2 * lane, y = blockIdx.y * MOM_BY + threadIdx.y, z = blockIdx.z;
     if (y >= v.ny) return;
     const int nx = v.nx;
     const bool act = x0 < nx;
@@ -907,10 +907,11 @@ __global__ void restore_natural_kernel(View<R> v, const R *in) {
 }
 
 inline int nblocks(long long n, int b) { return (int)((n + b - 1) / b); }
-// 32-bit population indices when every index i N + n fits
+// 32-bit population indices when every index i N + n fits (unless 64-bit
+// ones are asked for)
 template <typename R>
 bool narrow_index(const View<R> &v) {
-    return (unsigned long long)Q * (unsigned long long)v.N <= 0xffffffffull;
+    return !v.wide_index && (unsigned long long)Q * (unsigned long long)v.N <= 0xffffffffull;
 }
 template <typename R>
 dim3 node_grid(const View<R> &v) {
@@ -981,12 +982,13 @@ template <typename T, typename R, int LAYOUT, typename I>
 void launch_moments_as(const View<R> &v, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value && sizeof(T) == 2) {
         if (v.node_pairs & PAIR_MOMENTS) {
-            const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, NODE_BY), (unsigned)v.nz);
-            moments_pair_kernel<T, LAYOUT, I><<<g, dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+            const dim3 g((unsigned)nblocks(v.nx, PAIR_X), (unsigned)nblocks(v.ny, MOM_BY), (unsigned)v.nz);
+            moments_pair_kernel<T, LAYOUT, I><<<g, dim3(NODE_BX, MOM_BY), 0, st>>>(v);
             return;
         }
     }
-    moments_kernel<T, R, LAYOUT, I><<<node_grid(v), dim3(NODE_BX, NODE_BY), 0, st>>>(v);
+    const dim3 g((unsigned)nblocks(v.nx, NODE_BX), (unsigned)nblocks(v.ny, MOM_BY), (unsigned)v.nz);
+    moments_kernel<T, R, LAYOUT, I><<<g, dim3(NODE_BX, MOM_BY), 0, st>>>(v);
 }
 
 template <typename R>
