@@ -111,6 +111,13 @@ enum { HEMO_OPT_TEST_STALLED_WAIT = 4u };
  * 64-bit variants can be tested on small lattices. */
 enum { HEMO_OPT_WIDE_INDEX = 16u };
 
+/* HEMO_OPT_NODE_STAGING: the FP32 interpolation stages each bin's lattice
+ * neighbourhood node by node (4-byte asynchronous copies) instead of by one
+ * tensor copy (used by default where nx is a multiple of 4 and the
+ * neighbourhood does not wrap around a periodic edge).  The results are the
+ * same bits. */
+enum { HEMO_OPT_NODE_STAGING = 32u };
+
 /* One membrane mesh type (Sec. 2.3: triangulated membrane whose vertices are
  * Lagrangian points).  Energies (F_total = F_link + F_bend + F_area +
  * F_volume, Sec. 2.3; forms chosen where the paper refers elsewhere):

@@ -11,6 +11,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "hemo_internal.cuh"
@@ -127,6 +128,10 @@ struct AdjBuffers {
 
 struct hemo_sim {
     int precision = 0;
+    // tensor map of u for the interpolation's staging (FP32 arithmetic, nx
+    // a multiple of 4, unless HEMO_OPT_NODE_STAGING)
+    CUtensorMap u_tmap;
+    bool u_tma = false;
     int nx = 0, ny = 0, nz = 0;
     long long N = 0;
     int per[3] = {1, 1, 1};
@@ -265,6 +270,34 @@ int ensure_staging(hemo_sim *s, size_t bytes) {
     return HEMO_OK;
 }
 
+// The tensor map of u ([3][nz][ny][nx] FP32, described as a 4-D tensor x,
+// y, z, component) for the interpolation's staging, box 16 x 11 x 11 x 3
+// (see k_ibm.cu).  False (node-by-node staging) for FP64, for nx not a
+// multiple of 4 (row strides must be multiples of 16 bytes), on request,
+// or when the driver does not provide the encoder.
+bool encode_u_tmap(hemo_sim *s) {
+    if (s->precision == HEMO_F64 || (s->options & HEMO_OPT_NODE_STAGING) || s->nx % 4 != 0 || !s->u) return false;
+    if (((uintptr_t)s->u & 15) != 0) return false;
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->nx * s->ny * 4, (cuuint64_t)s->N * 4};
+    const cuuint32_t box[4] = {16, 11, 11, 3}, estr[4] = {1, 1, 1, 1};
+    const CUresult r = reinterpret_cast<EncodeFn>(fn)(&s->u_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->u, dims, strides,
+                                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 template <typename R>
 View<R> make_view(hemo_sim *s) {
     View<R> v{};
@@ -296,6 +329,8 @@ View<R> make_view(hemo_sim *s) {
         v.node_pairs = PAIR_MOMENTS | ((s->options & HEMO_OPT_PAIR_COLLISION) ? PAIR_COLLIDE : 0);
     v.stalled_wait_test = (s->options & HEMO_OPT_TEST_STALLED_WAIT) ? 1 : 0;
     v.wide_index = (s->options & HEMO_OPT_WIDE_INDEX) ? 1 : 0;
+    v.u_tmap = s->u_tma ? (const void *)&s->u_tmap : nullptr;
+    v.u_tmap_base = s->u_tma ? s->u : nullptr;
     for (int d = 0; d < 3; ++d) {
         v.g[d] = R(s->g[d]);
         v.uw[0][d] = R(0);
@@ -1128,6 +1163,7 @@ int hemo_create_lattice(const hemo_lattice_desc *d, hemo_sim **out) {
         return bail(fail(HEMO_ERR_OOM, "device allocation of the lattice failed"));
     if (s->rref && cudaMemsetAsync(s->rref, 0, sizeof(float2) * (size_t)s->ny * s->nz, s->stream) != cudaSuccess)
         return bail(fail(HEMO_ERR_CUDA, "memset failed"));
+    s->u_tma = encode_u_tmap(s);
     if (cudaHostAlloc((void **)&s->status_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)

@@ -173,6 +173,11 @@ template <typename R> struct View {
     int node_pairs;            // 16-bit storage, nx even: PAIR_* bits, kernels that take two nodes per thread
     int stalled_wait_test;     // staged collision: first wait on a barrier nothing completes (HEMO_OPT_TEST_STALLED_WAIT)
     int wide_index;            // lattice kernels: 64-bit population indices on any lattice (HEMO_OPT_WIDE_INDEX)
+    // interpolation staging by tensor copies: the host-side tensor map of u
+    // (CUtensorMap, 4-D: x, y, z, component) and the array it describes;
+    // null when off (FP64, or nx not a multiple of 4)
+    const void *u_tmap;
+    const void *u_tmap_base;
     // a buffer whose contents are dead: the kernel drops its full 128-byte
     // lines from L2 without writing them back (null / 0 = nothing to drop)
     void *dead;
@@ -336,6 +341,52 @@ __device__ __forceinline__ Nbr make_nbr(const View<R> &v, int n) {
     const int r = n / v.nx;
     return nbr_at(v, n % v.nx, r % v.ny, r / v.ny);
 }
+
+// mbarrier and async-proxy helpers (completion of bulk and tensor copies
+// into shared memory; every wait is bounded)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// waits for the phase with the given parity; gives up after limit_ns
+// (about a second by default)
+__device__ inline bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 256; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // Lattice kernels over all nodes use a grid of (x chunks of NODE_BX) x (y
 // groups of NODE_BY) x z with blocks of NODE_BX x NODE_BY threads: node

@@ -22,7 +22,10 @@
 // per vertex, partial sums reduced with warp shuffles, several CTAs per bin).
 // With the Lees-Edwards boundary the vertices whose stencil reaches across
 // the plane are kept in one extra bin, handled in k_lees.cu.
+#include <cstring>
 #include <type_traits>
+
+#include <cuda.h>
 
 #include "hemo_internal.cuh"
 
@@ -725,16 +728,53 @@ __global__ void __launch_bounds__(256) interpolate_kernel(View<R> v, int parts) 
 // of u is staged once as (ux, uy, uz, 0) per node, so each stencil node is
 // one 16-byte shared load; the weights stay in registers and each thread
 // sums its vertex's 64 terms itself (no staging of weights, no shuffles).
+//
+// Staging.  With a tensor map of u (4-D: x, y, z, component) one thread
+// copies the box x in [ox - 4, ox + 12), y in [oy - 1, oy + 10), z in
+// [oz - 1, oz + 10), all three components, into shared memory with a single
+// tensor copy (x starts 16-byte aligned: ox is a multiple of 8; coordinates
+// outside the lattice read as zero, the resting wall beyond a non-periodic
+// edge); the threads then rearrange it into the node records, in place (each
+// first reads its nodes' values into registers).  A bin whose neighbourhood
+// wraps around a periodic edge, and every bin without a tensor map, is
+// staged node by node with 4-byte asynchronous copies.
+constexpr int IT_Y = TILE, IT_Z = TILE * TILE;  // node record strides of the interpolation tile
+constexpr int UBOX_X = 16;                      // x extent of the tensor copy (nodes)
+constexpr unsigned UBOX_BYTES = 3u * UBOX_X * TILE * TILE * 4u;
+constexpr int INTERP_SMEM = UBOX_BYTES > 16u * TILE3 ? (int)UBOX_BYTES : 16 * TILE3;
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *map, int c0, int c1, int c2, int c3, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
 template <int INTEG>
-__global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
+__global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, const __grid_constant__ CUtensorMap umap) {
     drop_dead_lines(v);
     const int k = blockIdx.x;
     const int s = v.start[k], e = v.start[k + 1];
     if (s == e) return;
-    __shared__ float4 tile[TILE_SMEM];
+    __shared__ __align__(128) unsigned char tile_raw[INTERP_SMEM];
     __shared__ int jtab[3][TILE];  // wrapped lattice coordinate, -1 beyond a non-periodic edge
+    __shared__ __align__(8) uint64_t bar;
+    float4 *tile = reinterpret_cast<float4 *>(tile_raw);
     int org[3];
     bin_origin(v, k, org);
+    // the tensor copy serves a neighbourhood that does not wrap
+    bool boxed = v.u_tmap != nullptr;
+    for (int d = 0; d < 3; ++d) {
+        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+        if (v.per[d] && (org[d] - 1 < 0 || org[d] + BLK + 1 >= dims)) boxed = false;
+    }
+    if (boxed && threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        fence_async_smem();
+        mbar_expect_tx(&bar, UBOX_BYTES);
+        tma_load_4d(tile_raw, &umap, org[0] - 4, org[1] - 1, org[2] - 1, 0, &bar);
+    }
     // this thread's first vertex: its records are requested before the tile
     // is staged, so their latency overlaps the staging
     const int jf = s + threadIdx.x;
@@ -748,33 +788,66 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
             atf[d] = v.anc_t[3 * (size_t)ifst + d];
         }
     }
-    if (threadIdx.x < 3 * TILE) {
-        const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
-        const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
-        int j = org[d] - 1 + l;
-        if (v.per[d]) j = wrap(j, dims);
-        else if (j < 0 || j >= dims) j = -1;
-        jtab[d][l] = j;
-    }
-    __syncthreads();
-    const size_t N = (size_t)v.N;
-    // asynchronous copies (no register round trip: all of a thread's loads
-    // are in flight at once); nodes beyond a non-periodic edge are a
-    // resting wall
-    for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
-        const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
-        const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
-        float4 *dst = tile + (l0 + TS_Y * l1 + TS_Z * l2);
-        if ((jx | jy | jz) >= 0) {
-            const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
-            cp_async4(&dst->x, v.u + n);
-            cp_async4(&dst->y, v.u + N + n);
-            cp_async4(&dst->z, v.u + 2 * N + n);
-        } else {
-            *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (boxed) {
+        __syncthreads();  // (the barrier is initialised)
+        const bool ok = mbar_wait(&bar, 0);
+        if (__syncthreads_or(!ok)) {  // the copy did not complete in time: report, let it land, leave
+            if (threadIdx.x == 0) {
+                atomicOr(v.status, ST_TIMEOUT);
+                mbar_wait(&bar, 0);
+            }
+            __syncthreads();
+            return;
         }
+        // rearrange [component][z][y][x - ox + 4] into node records, in place
+        constexpr int PER = (TILE3 + 255) / 256;
+        const float *box = reinterpret_cast<const float *>(tile_raw);
+        float4 r[PER];
+        TileWalk tw(threadIdx.x, blockDim.x);
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int q = threadIdx.x + 256 * m;
+            if (q < TILE3) {
+                const int b0 = tw.l0 + 3 + UBOX_X * (tw.l1 + TILE * tw.l2);
+                r[m] = make_float4(box[b0], box[b0 + UBOX_X * TILE * TILE], box[b0 + 2 * UBOX_X * TILE * TILE], 0.f);
+            }
+            tw.next();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int q = threadIdx.x + 256 * m;
+            if (q < TILE3) tile[q] = r[m];
+        }
+    } else {
+        if (threadIdx.x < 3 * TILE) {
+            const int d = threadIdx.x / TILE, l = threadIdx.x % TILE;
+            const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
+            int j = org[d] - 1 + l;
+            if (v.per[d]) j = wrap(j, dims);
+            else if (j < 0 || j >= dims) j = -1;
+            jtab[d][l] = j;
+        }
+        __syncthreads();
+        const size_t N = (size_t)v.N;
+        // asynchronous copies (no register round trip: all of a thread's loads
+        // are in flight at once); nodes beyond a non-periodic edge are a
+        // resting wall
+        for (int q = threadIdx.x; q < TILE3; q += blockDim.x) {
+            const int l0 = q % TILE, l1 = (q / TILE) % TILE, l2 = q / (TILE * TILE);
+            const int jx = jtab[0][l0], jy = jtab[1][l1], jz = jtab[2][l2];
+            float4 *dst = tile + q;
+            if ((jx | jy | jz) >= 0) {
+                const size_t n = (size_t)jx + (size_t)v.nx * ((size_t)jy + (size_t)v.ny * jz);
+                cp_async4(&dst->x, v.u + n);
+                cp_async4(&dst->y, v.u + N + n);
+                cp_async4(&dst->z, v.u + 2 * N + n);
+            } else {
+                *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     double dmax = 0.0;  // adaptive separation: this thread's largest displacement
     for (int j = jf; j < e; j += blockDim.x) {
@@ -803,7 +876,7 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
         for (int d = 0; d < 3; ++d) {
             const int b = ai[d] - org[d];
             ok &= b >= 0 && b < BLK;
-            r0 += b * (d == 0 ? 1 : (d == 1 ? TS_Y : TS_Z));
+            r0 += b * (d == 0 ? 1 : (d == 1 ? IT_Y : IT_Z));
             peskin4(at[d], w[d]);
         }
         if (!ok) continue;
@@ -813,7 +886,7 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const float wyz = w[1][b] * w[2][c];
-                const float4 *row = tile + r0 + TS_Y * b + TS_Z * c;
+                const float4 *row = tile + r0 + IT_Y * b + IT_Z * c;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     const float wa = wyz * w[0][a];
@@ -1077,7 +1150,19 @@ void launch_spread(const View<R> &v, cudaStream_t st) {
 
 template <typename R, int INTEG>
 void launch_interpolate_as(const View<R> &v, cudaStream_t st) {
-    if constexpr (std::is_same<R, float>::value) interpolate_v4_kernel<INTEG><<<v.nbins, 256, 0, st>>>(v);
+    if constexpr (std::is_same<R, float>::value) {
+        // the tensor map describes the step's u array only (the adjoint's
+        // recomputation keeps u per step elsewhere)
+        View<float> w = v;
+        CUtensorMap map;
+        if (v.u_tmap && v.u_tmap_base == (const void *)v.u) {
+            std::memcpy(&map, v.u_tmap, sizeof(map));
+        } else {
+            std::memset(&map, 0, sizeof(map));
+            w.u_tmap = nullptr;
+        }
+        interpolate_v4_kernel<INTEG><<<v.nbins, 256, 0, st>>>(w, map);
+    }
     else interpolate_kernel<R, INTEG><<<v.nbins * FP64_BIN_PARTS, 256, 0, st>>>(v, FP64_BIN_PARTS);
 }
 
