@@ -219,12 +219,15 @@ def time_scales(cfg, precision, warmup, steps, torch, flush):
             sim.set_force_tolerance(tol)
         sim.step(warmup)
         sim.sync()
+        evals0 = sim.force_evaluations
         total, _, _ = timed_steps(sim, torch, steps, flush, phase_every=0)
         f = sim.get_fields(hemo.HEMO_U | hemo.HEMO_VERTS)
+        evals = sim.force_evaluations - evals0
         sim.close()
         u, X = f['u'].astype(np.float64), f['X']
         r = {'force_every': n, 'integrator': integ, 'force_tolerance': tol,
-             'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps}
+             'mlups': cfg.n_fluid * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps,
+             'force_evaluations_timed': evals}
         if ref is None:
             ref = (u, X)
         else:

@@ -227,6 +227,13 @@ int hemo_set_time_scales(hemo_sim *sim, int force_every, int integrator);
  * and with the Lees-Edwards boundary; HEMO_ERR_OOM. */
 int hemo_set_force_tolerance(hemo_sim *sim, double delta);
 
+/* Membrane-force evaluations (Sec. 2.6: the steps on which the cell forces
+ * are computed rather than held) since the simulation was created, over
+ * every schedule it has run with, into *count.  With the adaptive
+ * separation the count is kept on the device and read here (the call waits
+ * for the stream).  Errors: HEMO_ERR_ARG for null pointers; HEMO_ERR_CUDA. */
+int hemo_get_force_evaluations(hemo_sim *sim, long long *count);
+
 /* Internal viscosity (Sec. 1: the cytosol is five times as viscous as the
  * plasma; Sec. 3: the red-cell model carries an internal viscosity ratio).
  * From the next step on, fluid nodes inside a cell membrane (at the vertex

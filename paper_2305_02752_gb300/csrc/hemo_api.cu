@@ -179,6 +179,7 @@ struct hemo_sim {
     int force_every = 1;          // membrane forces on every force_every-th step, held in between
     int integrator = HEMO_EULER;
     long long ts_origin = 0;      // step count at which the setting was made
+    long long evals_host = 0;     // membrane-force evaluations of constant-schedule steps (adaptive ones: adapt[4])
     bool have_prev = false;       // Uprev holds the previous step's vertex velocity
     void *Uprev = nullptr;
     void *csp = nullptr;          // per cell: centroid of the last re-base as R hi, lo
@@ -257,6 +258,7 @@ int status_code(unsigned st) {
     if (st & ST_NUMERIC) return fail(HEMO_ERR_NUMERIC, "device status: non-finite or |u| > 0.3 velocity, or a link stretched past its maximum strain");
     if (st & ST_DOMAIN) return fail(HEMO_ERR_DOMAIN, "device status: a vertex left the lattice across a non-periodic axis");
     if (st & ST_TIMEOUT) return fail(HEMO_ERR_CUDA, "device status: a copy pipeline wait timed out");
+    if (st & ST_BOUNDS) return fail(HEMO_ERR_CUDA, "device status: an index failed its bounds check (bounds-checked build)");
     return HEMO_OK;
 }
 
@@ -1314,6 +1316,7 @@ int hemo_step(hemo_sim *s, int nsteps) {
     if (nsteps == 0) return HEMO_OK;
     for (int k = 0; k < nsteps; ++k) {
         const bool force = (s->steps_done - s->ts_origin) % s->force_every == 0;
+        if (force && s->force_tol < 0) ++s->evals_host;
         const int integ = s->integrator == HEMO_AB2 ? (s->have_prev ? 2 : 1) : 0;
         const int parity = (int)(s->steps_done & 1);
         const int gi = s->force_tol >= 0 ? 12 + parity + 2 * integ : parity + 2 * (int)force + 4 * integ;
@@ -1359,12 +1362,26 @@ int hemo_set_force_tolerance(hemo_sim *s, double delta) {
     if (rc) return rc;
     if (delta >= 0 && !s->adapt) {
         s->off_eval = dalloc(s, rsize(s) * 3 * (size_t)std::max(s->nv, 1));
-        s->adapt = (unsigned long long *)dalloc(s, 4 * sizeof(unsigned long long));
+        s->adapt = (unsigned long long *)dalloc(s, ADAPT_WORDS * sizeof(unsigned long long));
         if (!s->off_eval || !s->adapt) return fail(HEMO_ERR_OOM, "adaptive separation buffers");
+        HEMO_CU(cudaMemsetAsync(s->adapt, 0, ADAPT_WORDS * sizeof(unsigned long long), s->stream));
     }
     s->force_tol = delta < 0 ? -1.0 : delta;
     s->ts_origin = s->steps_done;
     return adapt_restart(s);
+}
+
+int hemo_get_force_evaluations(hemo_sim *s, long long *count) {
+    if (!s || !count) return fail(HEMO_ERR_ARG, "null argument");
+    long long n = s->evals_host;
+    if (s->adapt) {
+        unsigned long long d = 0;
+        HEMO_CU(cudaMemcpyAsync(&d, s->adapt + 4, sizeof d, cudaMemcpyDeviceToHost, s->stream));
+        HEMO_CU(cudaStreamSynchronize(s->stream));
+        n += (long long)d;
+    }
+    *count = n;
+    return HEMO_OK;
 }
 
 int hemo_set_viscosity_ratio(hemo_sim *s, double ratio) {
@@ -1546,10 +1563,11 @@ struct StateHeader {
     int64_t N, nv, ncell, precision, le;
     int64_t steps_done, ts_origin;
     int64_t force_every, integrator, have_prev;
+    int64_t evals_host;      // force evaluations of constant-schedule steps
     double force_tol;        // adaptive separation (< 0: off)
     int64_t sections;        // number of buffers that follow
 };
-constexpr uint64_t STATE_MAGIC = 0x314154534f4d4548ull;  // the bytes "HEMOSTA1" in little-endian order
+constexpr uint64_t STATE_MAGIC = 0x324154534f4d4548ull;  // the bytes "HEMOSTA2" in little-endian order
 
 // the buffers of the dynamic state, in order: (device pointer, bytes)
 std::vector<std::pair<void *, size_t>> state_sections(hemo_sim *s) {
@@ -1568,7 +1586,7 @@ std::vector<std::pair<void *, size_t>> state_sections(hemo_sim *s) {
     if (s->le) v.push_back({s->le_n, sizeof(long long)});  // Lees-Edwards step counter
     if (s->force_tol >= 0) {  // adaptive separation: offsets at the last evaluation, decision words
         v.push_back({s->off_eval, rs * 3 * (size_t)std::max(s->nv, 1)});
-        v.push_back({s->adapt, 4 * sizeof(unsigned long long)});
+        v.push_back({s->adapt, ADAPT_WORDS * sizeof(unsigned long long)});
     }
     return v;
 }
@@ -1612,6 +1630,7 @@ int hemo_save_state(hemo_sim *s, void *buf, size_t bytes) {
     h.le = s->le;
     h.steps_done = s->steps_done;
     h.ts_origin = s->ts_origin;
+    h.evals_host = s->evals_host;
     h.force_every = s->force_every;
     h.integrator = s->integrator;
     h.have_prev = s->have_prev;
@@ -1656,6 +1675,7 @@ int hemo_load_state(hemo_sim *s, const void *buf, size_t bytes) {
     }
     s->steps_done = h.steps_done;
     s->ts_origin = h.ts_origin;
+    s->evals_host = h.evals_host;
     s->force_every = (int)h.force_every;
     s->integrator = (int)h.integrator;
     s->have_prev = h.have_prev != 0;

@@ -18,8 +18,30 @@ constexpr int MAX_TYPES = 8;        // membrane mesh types per simulation
 constexpr unsigned ST_NUMERIC = 1u;
 constexpr unsigned ST_DOMAIN = 2u;
 constexpr unsigned ST_TIMEOUT = 4u;  // a pipeline wait gave up
+constexpr unsigned ST_BOUNDS = 8u;   // an index failed its check (bounds-checked build only)
+
+// The bounds-checked build (HEMO_BOUNDS_CHECK=1, libhemo_checked.so) tests
+// the data-driven indices of the vertex, bin and membrane kernels (vertex
+// ids read from the bin order, cell ids, mesh-table entries, bin slots)
+// before use: a failed test sets ST_BOUNDS in the status word and the
+// access is skipped.  In the default build index_ok is the constant true
+// and the tests compile away.
+#ifndef HEMO_BOUNDS_CHECK
+#define HEMO_BOUNDS_CHECK 0
+#endif
+__device__ __forceinline__ bool index_ok(bool ok, unsigned *status) {
+#if HEMO_BOUNDS_CHECK
+    if (!ok && status) atomicOr(status, ST_BOUNDS);
+    return ok;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
 constexpr float U_LIMIT2 = 0.09f;   // |u|^2 above which the step is unstable
 constexpr int PAIR_MOMENTS = 1, PAIR_COLLIDE = 2;  // View::node_pairs bits
+constexpr int ADAPT_WORDS = 5;                      // View::adapt
 
 // ---------------------------------------------------------------------------
 // D3Q19 in the library's order: 0 rest; 1..6 = +x -x +y -y +z -z; 7..18 =
@@ -142,7 +164,7 @@ template <typename R> struct View {
     // force evaluation, and the device words {largest displacement since it
     // (FP64 bits), steps since it, evaluate on this step, first step pending}
     R *off_eval;
-    unsigned long long *adapt;
+    unsigned long long *adapt;  // ADAPT_WORDS words; the fifth counts the evaluations
     // internal viscosity (null when off): per-node indicator of the cell
     // interiors and the toggle counts it is built from; relaxation rate inside
     uint8_t *ind;

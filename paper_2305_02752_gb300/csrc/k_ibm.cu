@@ -82,6 +82,7 @@ __global__ void anchor_count_kernel(View<R> v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.nv) return;
     const int c = v.vcell[i];
+    if (!index_ok(c >= 0 && c < v.ncell, v.status)) return;
     const int dims[3] = {v.nx, v.ny, v.nz};
     int b[3];
     for (int d = 0; d < 3; ++d) {
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(int *counts, int *start, int
 
 // scatter with per-block cursors; lanes of a warp with the same key reserve
 // their slots with one atomic
-__global__ void scatter_kernel(const int *key, int *cursor, int *perm_raw, int nv) {
+__global__ void scatter_kernel(const int *key, int *cursor, int *perm_raw, int nv, unsigned *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
     const int k = key[i];
@@ -165,7 +166,8 @@ __global__ void scatter_kernel(const int *key, int *cursor, int *perm_raw, int n
     int base = 0;
     if (lane == leader) base = atomicAdd(cursor + k, __popc(grp));
     base = __shfl_sync(act, base, leader);
-    perm_raw[base + __popc(grp & ((1u << lane) - 1u))] = i;
+    const int slot = base + __popc(grp & ((1u << lane) - 1u));
+    if (index_ok(slot >= 0 && slot < nv, status)) perm_raw[slot] = i;
 }
 
 // One warp per block: each id's rank among the block's ids (ids are unique)
@@ -281,6 +283,10 @@ __device__ __forceinline__ void stage_chunk(const View<R> &v, int p0, int n, con
                                             R *sF, int *sperm, const R *fscale = nullptr) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int i = v.perm[p0 + j];
+        if (!index_ok(i >= 0 && i < v.nv, v.status)) {
+            srow[j] = -1;
+            continue;
+        }
         int row = 0;
         bool ok = true;
         for (int d = 0; d < 3; ++d) {
@@ -352,6 +358,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) spread_tile_kerne
         } else {
             for (int j = s + threadIdx.x; j < e; j += blockDim.x) {
                 const int i = v.perm[j];
+                if (!index_ok(i >= 0 && i < v.nv, v.status)) continue;
                 for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(v.Fv[3 * (size_t)i + d]));
             }
         }
@@ -575,7 +582,7 @@ __global__ void __launch_bounds__(256) spread_gather3_kernel(View<R> v) {
 // displacement since the last force evaluation, |off - off_eval| of the new
 // offsets (held steps do not re-base, so that is X - X_eval); else 0.
 template <int INTEG, typename R>
-__device__ __forceinline__ double move_vertex(const View<R> &v, int i, R U0, R U1, R U2) {
+__device__ __forceinline__ R move_vertex(const View<R> &v, int i, R U0, R U1, R U2) {
     R *o = v.off + 3 * (size_t)i;
     const R x0 = o[0], x1 = o[1], x2 = o[2];
     R n0, n1, n2;
@@ -602,10 +609,10 @@ __device__ __forceinline__ double move_vertex(const View<R> &v, int i, R U0, R U
     o[0] = n0;
     o[1] = n1;
     o[2] = n2;
-    if (!v.off_eval) return 0.0;
+    if (!v.off_eval) return R(0);
     const R *e = v.off_eval + 3 * (size_t)i;
     const R d0 = n0 - e[0], d1 = n1 - e[1], d2 = n2 - e[2];
-    return (double)sqrt_r(d0 * d0 + d1 * d1 + d2 * d2);
+    return sqrt_r(d0 * d0 + d1 * d1 + d2 * d2);
 }
 
 // the largest displacement of a warp's vertices into the adaptive word (as
@@ -628,6 +635,7 @@ __device__ __forceinline__ void adapt_max(unsigned long long *adapt, double d) {
 __global__ void adapt_decide_kernel(unsigned long long *a, double tol, int every) {
     const bool eval = a[3] || a[1] >= (unsigned long long)every || __longlong_as_double((long long)a[0]) > tol;
     a[2] = eval ? 1ull : 0ull;
+    a[4] += eval ? 1ull : 0ull;  // evaluations so far
     a[1] = eval ? 1ull : a[1] + 1ull;
     a[3] = 0ull;
     a[0] = 0ull;
@@ -641,7 +649,9 @@ __global__ void __launch_bounds__(256) hold_bins_kernel(View<R> v) {
     if (v.adapt && v.adapt[2]) return;  // adaptive separation: this step evaluates the forces
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.nv) return;
-    const R *cs = v.csp + 6 * (size_t)v.vcell[i];
+    const int c = v.vcell[i];
+    if (!index_ok(c >= 0 && c < v.ncell, v.status)) return;
+    const R *cs = v.csp + 6 * (size_t)c;
     const R *o = v.off + 3 * (size_t)i;
     const R ch[3] = {cs[0], cs[1], cs[2]}, cl[3] = {cs[3], cs[4], cs[5]}, oi[3] = {o[0], o[1], o[2]};
     bin_vertex(v, (size_t)i, ch, cl, oi);
@@ -782,10 +792,11 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
     float atf[3] = {0.f, 0.f, 0.f};
     if (jf < e) {
         ifst = v.perm[jf];
+        if (!index_ok(ifst >= 0 && ifst < v.nv, v.status)) ifst = -1;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            aif[d] = v.anc_i[3 * (size_t)ifst + d];
-            atf[d] = v.anc_t[3 * (size_t)ifst + d];
+            aif[d] = ifst < 0 ? 0 : v.anc_i[3 * (size_t)ifst + d];
+            atf[d] = ifst < 0 ? 0.f : v.anc_t[3 * (size_t)ifst + d];
         }
     }
     if (boxed) {
@@ -849,7 +860,7 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
         cp_async_wait_all();
     }
     __syncthreads();
-    double dmax = 0.0;  // adaptive separation: this thread's largest displacement
+    float dmax = 0.f;  // adaptive separation: this thread's largest displacement
     for (int j = jf; j < e; j += blockDim.x) {
         int i;
         int ai[3];
@@ -863,12 +874,16 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
             }
         } else {
             i = v.perm[j];
+            if (!index_ok(i >= 0 && i < v.nv, v.status)) continue;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 ai[d] = v.anc_i[3 * (size_t)i + d];
                 at[d] = v.anc_t[3 * (size_t)i + d];
             }
         }
+#if HEMO_BOUNDS_CHECK
+        if (i < 0) continue;  // (a vertex id that failed its check)
+#endif
         float w[3][4];
         int r0 = 0;
         bool ok = true;
@@ -896,9 +911,9 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
                     U2 += wa * t.z;
                 }
             }
-        dmax = fmax(dmax, move_vertex<INTEG>(v, i, U0, U1, U2));
+        dmax = fmaxf(dmax, move_vertex<INTEG>(v, i, U0, U1, U2));
     }
-    if (v.adapt) adapt_max(v.adapt, dmax);
+    if (v.adapt) adapt_max(v.adapt, (double)dmax);  // (FP64 once per thread, adaptive runs only)
 }
 
 // Peskin weights and their derivatives d/dt for the fraction t
@@ -1128,17 +1143,17 @@ void launch_bins(const View<R> &v, cudaStream_t st, bool stable) {
     anchor_count_kernel<R><<<nblocks(v.nv, 256), 256, 0, st>>>(v);
     scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins);
     if (stable) {
-        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm_raw, v.nv);
+        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm_raw, v.nv, v.status);
         sort_bins_kernel<<<nblocks((long long)v.nbins * 32, 128), 128, 0, st>>>(v.start, v.perm_raw, v.perm, v.nbins);
     } else {
-        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv);
+        scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv, v.status);
     }
 }
 
 template <typename R>
 void launch_bin_ranges(const View<R> &v, cudaStream_t st) {
     scan_kernel<<<1, 1024, 0, st>>>(v.counts, v.start, v.cursor, v.nbins + (v.le ? 1 : 0));  // (+ the Lees-Edwards bin)
-    scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv);
+    scatter_kernel<<<nblocks(v.nv, 256), 256, 0, st>>>(v.key, v.cursor, v.perm, v.nv, v.status);
 }
 
 template <typename R>
@@ -1316,7 +1331,7 @@ extern "C" int hemo_bin_vertices_noalloc(const double *verts, int nv, int nx, in
                                                                periodic[2] != 0, (int)nb0, (int)nb1, key, counts);
     scan_kernel<<<1, 1024, 0, st>>>(counts, start, cursor, nbins);
     if (nv > 0) {
-        scatter_kernel<<<(nv + 255) / 256, 256, 0, st>>>(key, cursor, perm_raw, nv);
+        scatter_kernel<<<(nv + 255) / 256, 256, 0, st>>>(key, cursor, perm_raw, nv, nullptr);
         sort_bins_kernel<<<(int)(((long long)nbins * 32 + 127) / 128), 128, 0, st>>>(start, perm_raw, perm, nbins);
     }
     const cudaError_t e = cudaGetLastError();

@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         for (int t = threadIdx.x; t < m.nt; t += blockDim.x) {
             const int4 T = Tn;
             if (t + (int)blockDim.x < m.nt) Tn = __ldg(m.tri4 + t + blockDim.x);
+            if (!index_ok(T.x >= 0 && T.x < m.nv && T.y >= 0 && T.y < m.nv && T.z >= 0 && T.z < m.nv, v.status))
+                continue;
             const V3<R> p0 = xyz(ld4(xs + 4 * T.x)), p1 = xyz(ld4(xs + 4 * T.y)), p2 = xyz(ld4(xs + 4 * T.z));
             const V3<R> n = cross(p1 - p0, p2 - p0);
             const R q = dot(n, n), ln = sqrt_r(q), iq = R(1) / q;
@@ -359,6 +361,10 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
             il0n = __ldg(m.invL0 + e + blockDim.x);
             th0n = __ldg(m.th0 + e + blockDim.x);
         }
+        if (!index_ok(E.x >= 0 && E.x < m.nv && E.y >= 0 && E.y < m.nv && E.z >= 0 && E.z < m.nv && E.w >= 0 &&
+                          E.w < m.nv && T.x >= 0 && T.x < m.nt && T.y >= 0 && T.y < m.nt,
+                      v.status))
+            continue;
         const V3<R> p0 = xyz(ld4(xs + 4 * E.x)), p1 = xyz(ld4(xs + 4 * E.y));
         const V3<R> pa = xyz(ld4(xs + 4 * E.z)), pb = xyz(ld4(xs + 4 * E.w));
         const V3<R> ed = p1 - p0;
@@ -392,13 +398,19 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_kernel(View<
         V3<R> f = {R(0), R(0), R(0)};
         int4 g = __ldg(m.vfan + i);  // slot 0: the last entry
         int4 gn = __ldg(m.vfan + (size_t)m.nv + i);  // slot 1, requested ahead (its L2 latency overlaps slot 0's use)
+        auto fan_ok = [&](int4 q) {
+            return index_ok(q.x >= 0 && q.x < m.nt && q.y >= 0 && q.y < m.nv && (q.z >> 1) >= 0 && (q.z >> 1) < m.ne &&
+                                q.w >= 0 && q.w < m.ne,
+                            v.status);
+        };
+        if (!fan_ok(g)) continue;
         Q4<R> ap = ld4(tn + 4 * g.x);  // T_k-1: n / |n|^2 and |n|
         V3<R> xp = xyz(ld4(xs + 4 * g.y));  // position of j_k-1
         int op = g.w;  // edge of T_k-1 opposite i
         int tp = g.x;  // T_k-1
         for (int k = 1; k <= m.maxv; ++k) {
             g = gn;
-            if (g.x < 0) break;
+            if (g.x < 0 || !fan_ok(g)) break;
             if (k < m.maxv) gn = __ldg(m.vfan + (size_t)(k + 1) * m.nv + i);  // the next slot, ahead
             const Q4<R> ak = ld4(tn + 4 * g.x);
             const V3<R> xk = xyz(ld4(xs + 4 * g.y));

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, 'libhemo.so')
+# HEMO_BOUNDS_CHECK=1 in the environment loads the bounds-checked build
+LIB_PATH = os.path.join(_HERE, 'libhemo_checked.so' if os.environ.get('HEMO_BOUNDS_CHECK') == '1' else 'libhemo.so')
 
 HEMO_OK, HEMO_ERR_ARG, HEMO_ERR_OOM, HEMO_ERR_CUDA, HEMO_ERR_NUMERIC, HEMO_ERR_DOMAIN, HEMO_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6
@@ -76,6 +77,7 @@ def lib():
         'hemo_step': ([vp, i], i),
         'hemo_set_time_scales': ([vp, i, i], i),
         'hemo_set_force_tolerance': ([vp, d], i),
+        'hemo_get_force_evaluations': ([vp, C.POINTER(ll)], i),
         'hemo_set_viscosity_ratio': ([vp, d], i),
         'hemo_set_lees_edwards': ([vp, d], i),
         'hemo_get_inside': ([vp, vp], i),
@@ -112,7 +114,7 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the load test)."""
     return ['hemo_create_lattice', 'hemo_set_velocity', 'hemo_add_cells', 'hemo_step', 'hemo_set_time_scales',
-            'hemo_set_force_tolerance',
+            'hemo_set_force_tolerance', 'hemo_get_force_evaluations',
             'hemo_set_viscosity_ratio', 'hemo_get_inside', 'hemo_set_lees_edwards', 'hemo_sync',
             'hemo_get_fields', 'hemo_get_sizes', 'hemo_get_lattice_plan', 'hemo_velocity_set', 'hemo_get_populations',
             'hemo_get_links', 'hemo_get_edges', 'hemo_set_vertices', 'hemo_get_bins',
@@ -295,6 +297,13 @@ class Simulation:
         has moved more than delta since the last evaluation (or
         force_every steps have passed); delta < 0: constant schedule."""
         check(lib().hemo_set_force_tolerance(self.handle, float(delta)))
+
+    @property
+    def force_evaluations(self):
+        """Membrane-force evaluations since creation (every schedule)."""
+        n = C.c_longlong(0)
+        check(lib().hemo_get_force_evaluations(self.handle, C.byref(n)))
+        return n.value
 
     def set_viscosity_ratio(self, ratio):
         """Viscosity inside cells relative to the plasma (1 = off): inside

@@ -196,6 +196,8 @@ def test_null_handles():
     assert L.hemo_get_inside(None, None) == hemo.HEMO_ERR_ARG
     assert L.hemo_set_lees_edwards(None, 0.01) == hemo.HEMO_ERR_ARG
     assert L.hemo_set_force_tolerance(None, 0.1) == hemo.HEMO_ERR_ARG
+    cnt = C.c_longlong(-5)
+    assert L.hemo_get_force_evaluations(None, C.byref(cnt)) == hemo.HEMO_ERR_ARG and cnt.value == -5
     n = C.c_size_t(7)
     assert L.hemo_state_bytes(None, C.byref(n)) == hemo.HEMO_ERR_ARG and n.value == 7
     assert L.hemo_save_state(None, None, 0) == hemo.HEMO_ERR_ARG
@@ -276,3 +278,13 @@ def test_binding_signatures_match_the_header():
         want = [] if params.strip() in ('', 'void') else [_c_kind(p) for p in params.split(',')]
         assert [_ctypes_kind(t) for t in fn.argtypes] == want, name
         assert _ctypes_kind(fn.restype) == ('ptr' if '*' in ret else _c_kind(ret)), name
+
+
+def test_bounds_checked_library_is_built():
+    """build() also makes the bounds-checked library; it exports the same
+    symbols."""
+    from paper_2305_02752_gb300 import build as B
+    assert os.path.exists(B.LIB_CHECKED)
+    L = C.CDLL(B.LIB_CHECKED)
+    for n in header_functions():
+        assert hasattr(L, n), n

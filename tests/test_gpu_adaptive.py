@@ -37,6 +37,7 @@ def run_both(cfg, precision, steps, delta, force_every, integrator):
     sim.step(steps)
     ref.step(steps)
     got = sim.get_fields()
+    got['evaluations'] = sim.force_evaluations
     sim.close()
     return got, ref.get(), ref.force_evaluations
 
@@ -47,6 +48,7 @@ def test_shear_cell_f64(delta, force_every, integrator):
     cfg = small_cell_shear(steps=40)
     got, exp, nevals = run_both(cfg, 'f64', 40, delta, force_every, integrator)
     assert 3 <= nevals <= 30, nevals  # held steps and evaluations both occur
+    assert got['evaluations'] == nevals  # the device decided the same steps
     for k in ('u', 'X'):
         assert_close(got[k], exp[k], F64_TOL, k)
     assert forces_close(got['Fv'], exp['Fv'], cfg)
@@ -56,6 +58,7 @@ def test_channel_f32_200_steps():
     cfg = I.channel(nx=32, ny=32, nz=64, ncell=6, seed=3, steps=200, pack_iter=50, exact_iter=50)
     got, exp, nevals = run_both(cfg, 'f32', 200, 0.053, 10, 'ab2')
     assert 40 <= nevals <= 120, nevals
+    assert abs(got['evaluations'] - nevals) <= 2  # (FP32 displacements decide near the threshold)
     assert_close(got['u'], exp['u'], F32_TOL, 'u')
     assert_close(got['X'], exp['X'], F32_TOL, 'X')
 
@@ -145,3 +148,30 @@ def test_resume_with_adaptive_separation_bitwise():
     c.close()
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
+
+
+def test_evaluation_count_across_schedules():
+    """Constant schedules are counted on the host, the adaptive one on the
+    device; the total over a switch of schedule and across a checkpoint
+    equals the oracle's."""
+    cfg = small_cell_shear(steps=24)
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    ref = O.from_config(cfg)
+    for s in (sim, ref):
+        s.set_time_scales(3, 'euler')
+        s.step(10)  # steps 0, 3, 6, 9
+    assert sim.force_evaluations == ref.force_evaluations == 4
+    for s in (sim, ref):
+        s.set_force_tolerance(0.0021)
+        s.step(7)
+    state = sim.save_state()
+    sim.close()
+    sim = hemo.Simulation.from_config(cfg, 'f64')
+    sim.load_state(state)
+    assert sim.force_evaluations == ref.force_evaluations
+    for s in (sim, ref):
+        s.set_force_tolerance(-1.0)
+        s.set_time_scales(2, 'euler')
+        s.step(5)
+    assert sim.force_evaluations == ref.force_evaluations
+    sim.close()
