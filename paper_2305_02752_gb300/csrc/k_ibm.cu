@@ -760,6 +760,8 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const void *map, int c0, 
         : "memory");
 }
 
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 template <int INTEG>
 __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, const __grid_constant__ CUtensorMap umap) {
     drop_dead_lines(v);
@@ -884,6 +886,13 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
 #if HEMO_BOUNDS_CHECK
         if (i < 0) continue;  // (a vertex id that failed its check)
 #endif
+        // the move's loads (offsets; the previous velocity for Adams-Bashforth;
+        // the offsets of the last force evaluation for the adaptive
+        // separation) are requested into L1 before the stencil sums, whose
+        // shared loads would otherwise hide nothing of their latency
+        prefetch_l1(v.off + 3 * (size_t)i);
+        if (INTEG == 2) prefetch_l1(v.Uprev + 3 * (size_t)i);
+        if (v.off_eval) prefetch_l1(v.off_eval + 3 * (size_t)i);
         float w[3][4];
         int r0 = 0;
         bool ok = true;
