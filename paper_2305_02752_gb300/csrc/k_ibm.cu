@@ -109,20 +109,38 @@ __global__ void anchor_count_kernel(View<R> v) {
 }
 
 // exclusive scan of the block counts by one CTA of 1024 threads, over tiles
-// of 1024 consecutive counts (coalesced loads; warp shuffles within a warp,
-// the 32 warp totals by warp 0, a running carry between tiles; the next
-// tile's counts are loaded before the current one is scanned); the counts
-// are reset to zero for the next binning
+// of 4096 consecutive counts, four per thread (16-byte loads and stores
+// where the arrays are 16-byte aligned; a thread's own sums, warp shuffles
+// over the thread totals, the 32 warp totals by warp 0, a running carry
+// between tiles; the next tile's counts are loaded before the current one
+// is scanned); the counts are reset to zero for the next binning
+__device__ __forceinline__ int4 load_quad(const int *p, int k, int n, bool vec) {
+    if (vec && k + 3 < n) return *reinterpret_cast<const int4 *>(p + k);
+    return make_int4(k < n ? p[k] : 0, k + 1 < n ? p[k + 1] : 0, k + 2 < n ? p[k + 2] : 0, k + 3 < n ? p[k + 3] : 0);
+}
+__device__ __forceinline__ void store_quad(int *p, int k, int n, bool vec, int4 q) {
+    if (vec && k + 3 < n) {
+        *reinterpret_cast<int4 *>(p + k) = q;
+        return;
+    }
+    if (k < n) p[k] = q.x;
+    if (k + 1 < n) p[k + 1] = q.y;
+    if (k + 2 < n) p[k + 2] = q.z;
+    if (k + 3 < n) p[k + 3] = q.w;
+}
 __global__ void __launch_bounds__(1024) scan_kernel(int *counts, int *start, int *cursor, int nbins) {
     __shared__ int wsum[32];
     __shared__ int carry_s;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const bool vec = (((uintptr_t)counts | (uintptr_t)start | (uintptr_t)cursor) & 15) == 0;
     int carry = 0;
-    int next = t < nbins ? counts[t] : 0;
-    for (int base = 0; base < nbins; base += 1024) {
-        const int k = base + t, c = next;
-        if (base + 1024 + t < nbins) next = counts[base + 1024 + t];
-        int x = c;  // inclusive scan within the warp
+    int4 next = load_quad(counts, 4 * t, nbins, vec);
+    for (int base = 0; base < nbins; base += 4096) {
+        const int k0 = base + 4 * t;
+        const int4 c = next;
+        if (base + 4096 < nbins) next = load_quad(counts, k0 + 4096, nbins, vec);
+        const int own = c.x + c.y + c.z + c.w;
+        int x = own;  // inclusive scan of the thread totals within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -141,12 +159,11 @@ __global__ void __launch_bounds__(1024) scan_kernel(int *counts, int *start, int
             if (lane == 31) carry_s = y;
         }
         __syncthreads();
-        const int excl = carry + (w ? wsum[w - 1] : 0) + x - c;
-        if (k < nbins) {
-            start[k] = excl;
-            cursor[k] = excl;
-            counts[k] = 0;
-        }
+        const int e0 = carry + (w ? wsum[w - 1] : 0) + x - own;
+        const int4 ex = make_int4(e0, e0 + c.x, e0 + c.x + c.y, e0 + c.x + c.y + c.z);
+        store_quad(start, k0, nbins, vec, ex);
+        store_quad(cursor, k0, nbins, vec, ex);
+        store_quad(counts, k0, nbins, vec, make_int4(0, 0, 0, 0));
         carry += carry_s;
         __syncthreads();  // (wsum and carry_s are rewritten by the next tile)
     }
