@@ -102,6 +102,10 @@ template <typename R> struct MeshDev {
     // then -1; entry {T_k, j_k, edge (i, j_k) << 1 | role, edge (j_k, j_k+1)}
     // with T_k = (i, j_k, j_k+1) as oriented
     const int4 *vfan;
+    // strides coprime with nt and ne (about n/32): the FP64 adjoint takes
+    // triangle and edge q * stride mod n, so that a warp's shared-memory
+    // atomics fall on far-apart vertices
+    int tstride, estride;
     // optional terms for large deformations (0 = off): per-triangle rest area
     // (processing order) and local area modulus; 1 / theta_m^2 of the
     // nonlinear bending term

@@ -7,9 +7,10 @@
 // while the FP64 centroid carries the position), sums area and volume over
 // the triangles in FP64, and accumulates the four force terms per vertex in
 // shared memory before one coalesced write.  The edge and triangle tables
-// arrive in a processing order permuted on the host so that the lanes of a
-// warp work on parts of the mesh far apart (fewer colliding shared-memory
-// atomics) while the table loads stay coalesced.  Energies (forms documented in
+// arrive in a processing order sorted on the host by smallest vertex id, so
+// that the lanes of a warp load nearby shared-memory records; the FP64
+// adjoint, which scatters with shared-memory atomics, walks them with a
+// coprime stride instead (lanes on far-apart mesh parts).  Energies (forms documented in
 // hemo.h):
 //   link   K L0 [eps^2/2 - 1/2 ln(1 - eps^2/m^2)],   eps = (L - L0)/L0
 //   bend   1/2 kb (theta - theta0)^2, theta = signed angle between the
@@ -535,7 +536,8 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
 
     Acc<R> th[4];  // lamFv . unit-modulus forces: link, bend, area, volume
     const int step = slices * (int)blockDim.x;  // this CTA's share of the edge and triangle terms
-    for (int e = slice * (int)blockDim.x + threadIdx.x; e < m.ne; e += step) {
+    for (int qe = slice * (int)blockDim.x + threadIdx.x; qe < m.ne; qe += step) {
+        const int e = (int)(((long long)qe * m.estride) % m.ne);
         const int i0 = m.edge[4 * e], i1 = m.edge[4 * e + 1], ia = m.edge[4 * e + 2], ib = m.edge[4 * e + 3];
         const int t1 = m.etri[2 * e], t2 = m.etri[2 * e + 1];
         const V3<D> p0 = dld3(xs + 3 * i0, xt + 3 * i0), p1 = dld3(xs + 3 * i1, xt + 3 * i1);
@@ -568,7 +570,8 @@ __global__ void __launch_bounds__(NT, CellMinBlocks<R, NT>::B) cell_adjoint_kern
         add_into(ft + 3 * i1, m.k_bend, tans(f1));
         th[1].add(dot(la, vals(fa)) + dot(lb, vals(fb)) + dot(l0, vals(f0)) + dot(l1, vals(f1)));
     }
-    for (int t = slice * (int)blockDim.x + threadIdx.x; t < m.nt; t += step) {
+    for (int qt = slice * (int)blockDim.x + threadIdx.x; qt < m.nt; qt += step) {
+        const int t = (int)(((long long)qt * m.tstride) % m.nt);
         const int j[3] = {m.tri[3 * t], m.tri[3 * t + 1], m.tri[3 * t + 2]};
         const V3<D> p[3] = {dld3(xs + 3 * j[0], xt + 3 * j[0]), dld3(xs + 3 * j[1], xt + 3 * j[1]),
                             dld3(xs + 3 * j[2], xt + 3 * j[2])};

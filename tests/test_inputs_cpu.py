@@ -287,3 +287,23 @@ def test_kbt_scaling():
     assert I.kbt_lattice(1.5) / k == pytest.approx(4.0, rel=1e-12)
     assert I.kbt_lattice(1.0, 0.25) / k == pytest.approx(2.0, rel=1e-12)
     assert k == pytest.approx(1.917e-7, rel=1e-3)
+
+
+def test_locality_order_renumbers_the_same_surface():
+    """The renumbering is a bijection of the vertices that keeps every
+    triangle (with its orientation) and brings neighbouring vertices to
+    nearby ids."""
+    v, t = I.icosphere(3)
+    v2, t2 = I.locality_order(v, t)
+    assert v2.shape == v.shape and t2.shape == t.shape
+    # recover the permutation from the positions
+    key = {tuple(np.round(p, 12)): k for k, p in enumerate(v)}
+    old = np.array([key[tuple(np.round(p, 12))] for p in v2])
+    assert sorted(old) == list(range(len(v)))
+    # triangle k of the renumbered mesh is triangle k of the original
+    assert np.array_equal(old[t2], t)
+    gap = lambda tt: np.median(np.abs(np.concatenate([tt[:, 0] - tt[:, 1], tt[:, 1] - tt[:, 2], tt[:, 2] - tt[:, 0]])))
+    assert gap(t2) < gap(t) / 10
+    a0, v0 = _mesh_area_volume(v, t)
+    a1, v1 = _mesh_area_volume(v2, t2)
+    assert abs(a1 - a0) < 1e-12 * a0 and abs(v1 - v0) < 1e-12 * v0
