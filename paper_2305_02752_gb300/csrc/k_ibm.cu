@@ -17,9 +17,10 @@
 // of its neighbouring bins that map onto its nodes and writes F = g + sum for
 // every node once (no separate clearing pass).  Interpolation: one CTA per
 // non-empty bin stages the velocity of its 11^3 neighbourhood in shared
-// memory and evaluates the 64-node stencils of its own vertices from there
-// (FP32: one thread per vertex over 16-byte node records; FP64: half-warps
-// per vertex, partial sums reduced with warp shuffles, several CTAs per bin).
+// memory (FP32: one 4-D tensor copy where the neighbourhood does not wrap)
+// and evaluates the 64-node stencils of its own vertices from there (FP32:
+// one thread per vertex over 16-byte node records; FP64: half-warps per
+// vertex, partial sums reduced with warp shuffles, several CTAs per bin).
 // With the Lees-Edwards boundary the vertices whose stencil reaches across
 // the plane are kept in one extra bin, handled in k_lees.cu.
 #include <cstring>
