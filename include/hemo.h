@@ -96,12 +96,14 @@ enum { HEMO_OPT_STAGED_COLLISION = 1u };
  * same bits in every case; the options exist to compare the kernels. */
 enum { HEMO_OPT_NODE_COLLISION = 2u, HEMO_OPT_PAIR_COLLISION = 8u };
 
-/* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the staged
- * collision (HEMO_OPT_STAGED_COLLISION, 16-bit storage, odd steps).  Its
- * kernel first waits, at most 2 ms, on a barrier that no copy completes; the
- * wait runs out, the kernel returns without colliding, and the step reports
- * HEMO_ERR_CUDA ("a copy pipeline wait timed out") through the device status,
- * as a real stalled copy would.  Not for production runs. */
+/* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the kernels
+ * that wait on copies: the staged collision (HEMO_OPT_STAGED_COLLISION,
+ * 16-bit storage, odd steps) and the FP32 interpolation's tensor copy.  Each
+ * first waits, at most 2 ms, on a barrier that no copy completes (before
+ * issuing any); the wait runs out, the kernel returns without its work, and
+ * the step reports HEMO_ERR_CUDA ("a copy pipeline wait timed out") through
+ * the device status, as a real stalled copy would.  Not for production
+ * runs. */
 enum { HEMO_OPT_TEST_STALLED_WAIT = 4u };
 
 /* HEMO_OPT_WIDE_INDEX: the lattice kernels form population indices i N + n

@@ -798,6 +798,20 @@ __global__ void __launch_bounds__(256, 6) interpolate_v4_kernel(View<float> v, c
         const int dims = d == 0 ? v.nx : (d == 1 ? v.ny : v.nz);
         if (v.per[d] && (org[d] - 1 < 0 || org[d] + BLK + 1 >= dims)) boxed = false;
     }
+    if (boxed && v.stalled_wait_test) {
+        // failure-path test: wait on a barrier that nothing arrives at (no
+        // copy issued); the bounded wait runs out and the CTA reports it
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        const bool ok = threadIdx.x == 0 ? mbar_wait(&bar, 0u, 2000000ull) : true;
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(v.status, ST_TIMEOUT);
+            return;
+        }
+    }
     if (boxed && threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();

@@ -10,10 +10,11 @@ staged collision's bounded waits.
   forces, the centroid split and the previous velocity are part of the
   state), and BF16 storage with its row reference; a state is refused by a
   simulation of another size or precision.
-* Stalled wait: with HEMO_OPT_TEST_STALLED_WAIT the staged collision waits
-  on a barrier that nothing completes; the wait runs out after 2 ms, the
-  step reports HEMO_ERR_CUDA through the device status, and the GPU context
-  stays usable (a new simulation steps normally afterwards).
+* Stalled wait: with HEMO_OPT_TEST_STALLED_WAIT the staged collision, and
+  the FP32 interpolation before its tensor copy, wait on a barrier that
+  nothing completes; the wait runs out after 2 ms, the step reports
+  HEMO_ERR_CUDA through the device status, and the GPU context stays usable
+  (a new simulation steps normally afterwards).
 """
 import numpy as np
 import pytest
@@ -109,3 +110,19 @@ def test_stalled_wait_reports_and_context_survives():
     u = ok.get_fields(hemo.HEMO_U)['u']
     ok.close()
     assert np.isfinite(u).all()
+
+
+def test_interpolation_stalled_wait_reports_and_context_survives():
+    cfg = I.channel(nx=32, ny=32, nz=64, ncell=6, seed=3, steps=4, pack_iter=20, exact_iter=10)
+    sim = hemo.Simulation.from_config(cfg, 'f32', options=hemo.HEMO_OPT_TEST_STALLED_WAIT)
+    sim.step(1)   # the interpolation's first wait runs out in the bins staged by tensor copy
+    with pytest.raises(hemo.HemoError) as e:
+        sim.sync()
+    assert e.value.code == hemo.HEMO_ERR_CUDA
+    assert 'timed out' in str(e.value)
+    sim.close()
+    ok = hemo.Simulation.from_config(cfg, 'f32')
+    ok.step(3)
+    ok.sync()
+    assert np.isfinite(ok.get_fields(hemo.HEMO_VERTS)['X']).all()
+    ok.close()
