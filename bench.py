@@ -190,8 +190,13 @@ def run_form(cfg, precision, warmup, steps, torch, flush, u_ref=None):
     _, phases, kps = timed_steps(sim, torch, 20, flush, phase_every=1)
     sim.close()
     nf = cfg.n_fluid
+    coll = phases.get('collide')
+    peak, _ = hbm_peak()
     res = {'mlups': nf * steps / (total * 1e-3) / 1e6, 'ms_per_step': total / steps,
-           'collide_ms': phases.get('collide'), 'phase_ms': phases}
+           'collide_ms': coll, 'phase_ms': phases,
+           # the collision phase (both step parities) against the measured
+           # copy bandwidth, at the form's algorithmic bytes per fluid node
+           'collide_hbm_frac': nf * bytes_per_node(precision) / (coll * 1e-3) / 1e9 / peak if coll else None}
     u = out['u'].astype(np.float64)
     if u_ref is not None:
         res['u_rel_l2_vs_f64'] = float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref))
@@ -550,7 +555,8 @@ def main():
             res[p], _ = run_form(cfg, p, args.warmup, fsteps, torch, flush, u_ref=u64)
         forms = {'steps': args.warmup + fsteps, 'timed_steps': fsteps, 'results': res,
                  'summary': {p: {'mlups': res[p]['mlups'], 'vs_f32': res[p]['mlups'] / res['f32']['mlups'],
-                                 'u_rel_l2_vs_f64': res[p].get('u_rel_l2_vs_f64')} for p in ('f32', 'f16', 'bf16')}}
+                                 'u_rel_l2_vs_f64': res[p].get('u_rel_l2_vs_f64'),
+                                 'collide_hbm_frac': res[p]['collide_hbm_frac']} for p in ('f32', 'f16', 'bf16')}}
     if args.extras:
         ccfg, _ = make_workload('channel')
         line['extras_workload'] = 'channel 64x64x256, 440 RBC, FP32'

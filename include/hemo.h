@@ -82,12 +82,16 @@ typedef struct {
     unsigned options;            /* bit mask of HEMO_OPT_*; 0 = defaults           */
 } hemo_lattice_desc;
 
-/* HEMO_OPT_STAGED_COLLISION: on odd steps (whose reads and writes are
- * shifted by one node in x), stage tiles of wall-free rows through shared
- * memory by bulk copies instead of colliding every node with the per-node
- * kernel; 16-bit storage only (ignored otherwise).  The results are the
- * same.  Off by default: the per-node kernel is the faster of the two. */
-enum { HEMO_OPT_STAGED_COLLISION = 1u };
+/* Staged collision: tiles of wall-free rows go through shared memory by
+ * bulk copies (on odd steps the rows shifted by the velocities, the
+ * one-node x-shift applied in shared memory) instead of every node through
+ * the per-node kernel; the rows next to walls stay per node.  It applies to
+ * 16-bit storage with x periodic and rows of at most 1024 nodes whose bytes
+ * are a multiple of 16, and is used by default where rows hold at least 512
+ * nodes (where it is the faster of the two).  HEMO_OPT_STAGED_COLLISION:
+ * also for shorter rows; HEMO_OPT_UNSTAGED_COLLISION: never (it wins over
+ * the former).  The results are the same bits in every case. */
+enum { HEMO_OPT_STAGED_COLLISION = 1u, HEMO_OPT_UNSTAGED_COLLISION = 64u };
 
 /* 16-bit storage with nx even computes the post-streaming velocity two
  * nodes per thread (32-bit population pairs) and collides one node per
@@ -98,7 +102,7 @@ enum { HEMO_OPT_NODE_COLLISION = 2u, HEMO_OPT_PAIR_COLLISION = 8u };
 
 /* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the kernels
  * that wait on copies: the staged collision (HEMO_OPT_STAGED_COLLISION,
- * 16-bit storage, odd steps) and the FP32 interpolation's tensor copy.  Each
+ * 16-bit storage) and the FP32 interpolation's tensor copy.  Each
  * first waits, at most 2 ms, on a barrier that no copy completes (before
  * issuing any); the wait runs out, the kernel returns without its work, and
  * the step reports HEMO_ERR_CUDA ("a copy pipeline wait timed out") through
@@ -305,7 +309,7 @@ int hemo_get_sizes(const hemo_sim *sim, long long *n_nodes, long long *n_vertice
 
 /* ---- inspection of integer work and raw state (tests, tools) ----------- */
 
-/* How the collision is split (see HEMO_OPT_STAGED_COLLISION): plan[0] tiles of
+/* How the collision is split (see the staged collision): plan[0] tiles of
  * wall-free rows staged through shared memory, plan[1] other rows with fluid
  * (per-node kernel), plan[2] rows per tile at most, plan[3] ring stages.
  * All zero when every node goes through the per-node kernel.  plan: host, 4

@@ -1042,24 +1042,28 @@ int hemo_velocity_set(int32_t *c, double *w) {
 // periodic: none of its populations meets a wall.  Runs of interior rows
 // within a z-plane are cut into tiles of at most tile_rows rows; the rows
 // that are not interior but hold fluid go to the per-node kernel.  Staging
-// needs 16-byte aligned rows (bulk copies) and at least two stages of the
-// ring in shared memory.  It is used on request (HEMO_OPT_STAGED_COLLISION)
-// for 2-byte storage only: the per-node kernel on its (x, y, z) grid with
-// 32-bit indices is faster for every storage type.
-constexpr size_t TILE_RING_BYTES = 54 * 1024;
+// needs 16-byte aligned rows (bulk copies), rows of at most 1024 nodes (a
+// stage's range) and at least two stages of the ring in shared memory (one
+// CTA per SM takes up to four), and is for 2-byte storage only.  By default
+// it is used for rows of at least 512 nodes (measured: on the 1000-node
+// rows of the pipe it takes 13 % less time than the per-node kernel, on
+// 128-node rows about as long); on request (HEMO_OPT_STAGED_COLLISION) for
+// shorter rows too; never with HEMO_OPT_UNSTAGED_COLLISION.
+constexpr size_t TILE_RING_BYTES = 227 * 1024;  // the largest dynamic shared memory of a CTA
+constexpr int TILE_STAGE_NODES = 1024;          // as the kernel's stage layout
+constexpr int TILE_DEFAULT_MIN_NX = 512;
 
 int plan_rows(hemo_sim *s, const uint8_t *mask) {
     const int nx = s->nx, ny = s->ny, nz = s->nz;
     const size_t S = tsize(s), Rb = rsize(s);
-    if (S != 2 || !(s->options & HEMO_OPT_STAGED_COLLISION) || !s->per[0]) return HEMO_OK;
+    if (S != 2 || (s->options & HEMO_OPT_UNSTAGED_COLLISION) || !s->per[0]) return HEMO_OK;
+    if (!(s->options & HEMO_OPT_STAGED_COLLISION) && nx < TILE_DEFAULT_MIN_NX) return HEMO_OK;
     if (((size_t)nx * S) % 16 || ((size_t)nx * Rb) % 16) return HEMO_OK;
-    // whole rows of at most 256 nodes per tile (one per thread; the stage
-    // layout has room for 256), at most 54 KiB of ring per CTA so that four
-    // CTAs share an SM
-    if (nx > 256) return HEMO_OK;
+    if (nx > TILE_STAGE_NODES) return HEMO_OK;
+    // whole rows per tile, as many as a stage's ranges hold
     const size_t per_node = Q * S + 3 * Rb;
-    const int k = std::min(256 / nx, ny);
-    const size_t stage = 256 * per_node;
+    const int k = std::min(TILE_STAGE_NODES / nx, ny);
+    const size_t stage = (size_t)TILE_STAGE_NODES * per_node;
     const int stages = (int)std::min<size_t>(4, (TILE_RING_BYTES - 128) / stage);
     if (stages < 2) return HEMO_OK;
     std::vector<uint8_t> fluid((size_t)ny * nz, 1), any((size_t)ny * nz, mask ? 0 : 1);
@@ -1116,7 +1120,7 @@ int plan_rows(hemo_sim *s, const uint8_t *mask) {
     s->nerows = (int)erows.size();
     s->tile_rows = k;
     s->tile_stages = stages;
-    s->tile_grid = std::min(s->ntiles, 4 * std::max(nsm, 1));
+    s->tile_grid = std::min(s->ntiles, std::max(nsm, 1));  // one persistent CTA per SM
     s->tile_smem = smem;
     return HEMO_OK;
 }

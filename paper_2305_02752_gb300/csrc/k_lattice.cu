@@ -213,18 +213,26 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY, sizeof(R) == 4 ? 4 : 1) col
 // nodes read in one step are whole rows, and every element of those ranges is
 // read and written by exactly one node of the tile (even step: slot i of the
 // tile's own rows; odd step: slot opp(i) of the rows shifted by -c_i, the
-// x-shift applied in shared memory with the periodic wrap).  A persistent CTA
-// copies them, with the force rows, into a ring of shared-memory stages by
-// bulk copies (cp.async.bulk, completion on an mbarrier), collides in place
-// (each node writes its outgoing value where the opposite incoming value was)
-// and writes the same ranges back by bulk stores; the CTAs then collide the
-// rows next to walls node by node.  The ring keeps several
-// tiles of loads in flight per SM without holding them in registers, which
-// is what 2-byte populations need to reach the HBM bandwidth; four CTAs of
-// 256 threads share an SM, so that one computes while another waits.
-constexpr int TILE_THREADS = 256;
-constexpr int TILE_CTAS_PER_SM = 4;
-constexpr int TILE_NODES = 256;  // stride of a direction's range in a stage (nodes)
+// x-shift applied in shared memory with the periodic wrap).  One persistent
+// CTA per SM runs a ring of up to four shared-memory stages of 1024 nodes:
+// a producer warp copies a tile's 19 ranges and its force rows into a stage
+// by bulk copies (cp.async.bulk, completion on the stage's "full" mbarrier),
+// the consumer warps collide in place (each node writes its outgoing value
+// where the opposite incoming value was) and arrive on the stage's "empty"
+// mbarrier, and the producer writes the same ranges back by bulk stores and
+// refills the stage.  The consumers never wait on the producer's issue of
+// copies, only on data, and up to three stages of loads are in flight while
+// they compute the fourth, without holding them in registers (what 2-byte
+// populations need to reach the HBM bandwidth).  A second kernel
+// (collide_erows_kernel) collides the rows next to walls node by node.
+constexpr int TILE_NODES = 1024;           // stride of a direction's range in a stage (nodes)
+constexpr int TILE_CONSUMER_WARPS = 18;
+constexpr int TILE_THREADS = 32 * (1 + TILE_CONSUMER_WARPS);  // warp 0: the producer
+constexpr int TILE_MAX_STAGES = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -272,61 +280,31 @@ __device__ __forceinline__ int cy_of(int i) { return (int)((CY_PACK >> (2 * i)) 
 __device__ __forceinline__ int cz_of(int i) { return (int)((CZ_PACK >> (2 * i)) & 3ull) - 1; }
 static_assert(((CY_PACK >> 6) & 3) == 2 && ((CZ_PACK >> 10) & 3) == 2, "packed velocity components");
 
-constexpr int TILE_COPIES = Q + 3;  // lanes of warp 0 that issue the copies of a stage
+constexpr int TILE_COPIES = Q + 3;  // lanes of the producer warp that issue the copies of a stage
 
 template <typename T, typename R, int PARITY, typename I>
-__global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_kernel(View<R> v) {
+__global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> v) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [stage]: the stage's copies have landed
+    uint64_t *empty = full + TILE_MAX_STAGES;             // [stage]: the consumers are done with it
+    uint64_t *test_bar = empty + TILE_MAX_STAGES;
     unsigned char *ring = smem + 128;
     constexpr int TNM = TILE_NODES;
     constexpr size_t pop_bytes = (size_t)TNM * sizeof(T), stage_bytes = Q * pop_bytes + 3 * (size_t)TNM * sizeof(R);
     const int nx = v.nx, S = v.tile_stages;
     const size_t N = (size_t)v.N;
     const int ntiles = v.ntiles;
-    const int lane = threadIdx.x;  // meaningful in warp 0
-    const bool issuer = threadIdx.x < TILE_COPIES, storer = threadIdx.x < Q;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
     T *f = (T *)v.f;
 
-    // Lane i < 19 of warp 0 copies direction i's range (slot i of the tile's
-    // rows on even steps, slot opp(i) of the rows shifted by -c_i on odd
-    // steps); lanes 19..21 copy the three force components.  Each lane
-    // announces its own bytes on the stage's barrier (22 arrivals).
-    auto issue_load = [&](int it) {
-        const int2 tl = v.rtiles[tile_of(it)];
-        const int s = it % S;
-        unsigned char *st = ring + s * stage_bytes;
-        const unsigned tn = (unsigned)(tl.y * nx);
-        if (lane < Q) {
-            T *buf = (T *)(st + lane * pop_bytes);
-            const T *src = f + (size_t)(PARITY ? opp(lane) : lane) * N;
-            mbar_expect_tx(bar + s, tn * (unsigned)sizeof(T));
-            tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
-                        [&](long long g, int b, int cnt) {
-                            bulk_load(buf + b, src + g, (unsigned)(cnt * sizeof(T)), bar + s);
-                        });
-        } else {
-            const int c = lane - Q;
-            R *fs = (R *)(st + Q * pop_bytes) + c * TNM;
-            mbar_expect_tx(bar + s, tn * (unsigned)sizeof(R));
-            bulk_load(fs, v.F + c * N + (size_t)tl.x * nx, tn * (unsigned)sizeof(R), bar + s);
-        }
-    };
-    auto issue_store = [&](int it) {  // lane < 19: the range it loaded
-        const int2 tl = v.rtiles[tile_of(it)];
-        unsigned char *st = ring + (it % S) * stage_bytes;
-        T *buf = (T *)(st + lane * pop_bytes);
-        T *dst = f + (size_t)(PARITY ? opp(lane) : lane) * N;
-        tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
-                    [&](long long g, int b, int cnt) { bulk_store(dst + g, buf + b, (unsigned)(cnt * sizeof(T))); });
-        bulk_commit();
-    };
-
     drop_dead_lines(v);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(bar + s, TILE_COPIES);
-        if (v.stalled_wait_test) mbar_init(bar + S, 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full + s, TILE_COPIES);
+            mbar_init(empty + s, TILE_CONSUMER_WARPS);
+        }
+        mbar_init(test_bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -334,79 +312,165 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_CTAS_PER_SM) collide_tiles_
         // failure-path test: wait on a barrier that nothing arrives at; the
         // bounded wait runs out and the kernel reports it without touching
         // the populations (no copy has been issued)
-        const bool ok = threadIdx.x == 0 ? mbar_wait(bar + S, 0u, 2000000ull) : true;
+        const bool ok = threadIdx.x == 0 ? mbar_wait(test_bar, 0u, 2000000ull) : true;
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(v.status, ST_TIMEOUT);
             return;
         }
     }
-    if (issuer)
-        for (int it = 0; it < S - 1 && tile_of(it) < ntiles; ++it) issue_load(it);
 
+    if (warp == 0) {
+        // Producer.  Lane i < 19 copies direction i's range (slot i of the
+        // tile's rows on even steps, slot opp(i) of the rows shifted by -c_i
+        // on odd steps) and writes it back; lanes 19..21 copy the three force
+        // components.  Each lane announces its own bytes on the stage's full
+        // barrier (22 arrivals).
+        const bool issuer = lane < TILE_COPIES, storer = lane < Q;
+        auto issue_load = [&](int it) {
+            const int2 tl = v.rtiles[tile_of(it)];
+            const int s = it % S;
+            unsigned char *st = ring + s * stage_bytes;
+            const unsigned tn = (unsigned)(tl.y * nx);
+            if (lane < Q) {
+                T *buf = (T *)(st + lane * pop_bytes);
+                const T *src = f + (size_t)(PARITY ? opp(lane) : lane) * N;
+                mbar_expect_tx(full + s, tn * (unsigned)sizeof(T));
+                tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+                            [&](long long g, int b, int cnt) {
+                                bulk_load(buf + b, src + g, (unsigned)(cnt * sizeof(T)), full + s);
+                            });
+            } else {
+                const int c = lane - Q;
+                R *fs = (R *)(st + Q * pop_bytes) + c * TNM;
+                mbar_expect_tx(full + s, tn * (unsigned)sizeof(R));
+                bulk_load(fs, v.F + c * N + (size_t)tl.x * nx, tn * (unsigned)sizeof(R), full + s);
+            }
+        };
+        auto issue_store = [&](int it) {  // lane < 19: the range it loaded
+            const int2 tl = v.rtiles[tile_of(it)];
+            unsigned char *st = ring + (it % S) * stage_bytes;
+            T *buf = (T *)(st + lane * pop_bytes);
+            T *dst = f + (size_t)(PARITY ? opp(lane) : lane) * N;
+            tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+                        [&](long long g, int b, int cnt) { bulk_store(dst + g, buf + b, (unsigned)(cnt * sizeof(T))); });
+            bulk_commit();
+        };
+        // wait until the consumers are done with tile j, then write it back
+        // (every lane waits, so that the whole warp agrees on the outcome)
+        auto retire = [&](int j) {
+            const bool ok = mbar_wait(empty + j % S, (unsigned)((j / S) & 1));
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            if (storer) issue_store(j);
+            return true;
+        };
+        bool ok = true;
+        int it = 0;
+        for (; tile_of(it) < ntiles; ++it) {
+            if (it >= S) {  // the stage of tile it held tile it - S
+                if (!(ok = retire(it - S))) break;
+                if (storer) bulk_wait_read<0>();  // its stores have read the stage
+                __syncwarp();
+            }
+            if (issuer) issue_load(it);
+        }
+        for (int j = it - S < 0 ? 0 : it - S; ok && j < it; ++j) ok = retire(j);
+        if (!ok) {
+            // a wait ran out (a consumer gave up): report, and let every load
+            // issued into a stage land before the CTA ends
+            if (lane == 0) {
+                atomicOr(v.status, ST_TIMEOUT);
+                for (int j = it - S < 0 ? 0 : it - S; j < it; ++j) mbar_wait(full + j % S, (unsigned)((j / S) & 1));
+            }
+            __syncwarp();
+        }
+        if (storer) bulk_wait_read<0>();
+        return;
+    }
+
+    // Consumers: the nodes of a tile (row j, column x) spread over all
+    // consumer threads; this thread's first node (j0, x0) and the step to
+    // its next one (dj, dx), taken once
+    constexpr int CT = 32 * TILE_CONSUMER_WARPS;
+    const int ct = threadIdx.x - 32;
+    const int x0 = ct % nx, j0 = ct / nx, dx = CT % nx, dj = CT / nx;
+    // the tile table entry is read one tile ahead, and the references of
+    // the thread's first row before the wait for the stage's data, so that
+    // their latency overlaps the wait
+    int2 tl = tile_of(0) < ntiles ? v.rtiles[tile_of(0)] : make_int2(0, 0);
     for (int it = 0; tile_of(it) < ntiles; ++it) {
         const int s = it % S;
-        const bool ok = mbar_wait(bar + s, (unsigned)((it / S) & 1));
-        if (__syncthreads_or(!ok)) {  // let the copies in flight land, then report
-            if (threadIdx.x == 0)
-                for (int j = it; j < it + S - 1 && tile_of(j) < ntiles; ++j)
-                    mbar_wait(bar + j % S, (unsigned)((j / S) & 1));
-            if (storer) bulk_wait_read<0>();
-            if (threadIdx.x == 0) atomicOr(v.status, ST_TIMEOUT);
+        const int2 tl_next = tile_of(it + 1) < ntiles ? v.rtiles[tile_of(it + 1)] : tl;
+        const int y0 = tl.x % v.ny, z0 = tl.x / v.ny;  // a tile's rows lie in one z-plane
+        // the node's row and its neighbours' references (direction i arrives
+        // from the row shifted by -c_i and leaves to the row shifted by
+        // +c_i), reloaded when the row changes
+        int rj = j0 < tl.y ? j0 : tl.y - 1;
+        RowRefs rr = row_refs<T>(v, y0 + rj, z0, PARITY == 1);
+        const bool ok = mbar_wait(full + s, (unsigned)((it / S) & 1));
+        if (!__all_sync(0xffffffffu, ok)) {  // the producer's copies did not land in time
+            if (lane == 0) atomicOr(v.status, ST_TIMEOUT);
             return;
         }
-        const int2 tl = v.rtiles[tile_of(it)];
-        const int TN = tl.y * nx;
         T *P = (T *)(ring + s * stage_bytes);
         const R *Fs = (const R *)(ring + s * stage_bytes + Q * pop_bytes);
-        for (int L = threadIdx.x; L < TN; L += TILE_THREADS) {
-            const int j = L / nx, x = L - j * nx;
-            const int xm = (x == 0 ? nx : x) - 1, xp = (x == nx - 1 ? -1 : x) + 1;
-            // the value arriving from direction i sits in direction i's range
-            // at x - c_i on odd steps (x wrapped), at x on even steps; the
-            // range offsets i * TNM are constants
-            T *const b0 = P + L, *const bm = P + (j * nx + xm), *const bp = P + (j * nx + xp);
-            auto at = [&](int i) -> T & {
-                return (PARITY == 0 ? b0 : (cx(i) > 0 ? bm : (cx(i) < 0 ? bp : b0)))[i * TNM];
-            };
-            // the node's row and its neighbours' references: direction i
-            // arrives from the row shifted by -c_i and leaves to the row
-            // shifted by +c_i
-            const int grow = tl.x + j;
-            const RowRefs rr = row_refs<T>(v, grow % v.ny, grow / v.ny, true);
-            R d[Q], p[Q];
+        for (int j = j0, x = x0; j < tl.y;) {
+            {
+                if (j != rj) {
+                    rj = j;
+                    rr = row_refs<T>(v, y0 + j, z0, PARITY == 1);
+                }
+                const int L = j * nx + x;
+                const int xm = (x == 0 ? nx : x) - 1, xp = (x == nx - 1 ? -1 : x) + 1;
+                // the value arriving from direction i sits in direction i's
+                // range at x - c_i on odd steps (x wrapped), at x on even
+                // steps; the range offsets i * TNM are constants
+                T *const b0 = P + L, *const bm = P + (j * nx + xm), *const bp = P + (j * nx + xp);
+                auto at = [&](int i) -> T & {
+                    return (PARITY == 0 ? b0 : (cx(i) > 0 ? bm : (cx(i) < 0 ? bp : b0)))[i * TNM];
+                };
+                R d[Q], p[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) d[i] = dec<T, R>(at(i), PARITY ? ref_dir(i, rr.at(-cy(i), -cz(i))) : ref_dir(i, rr.own));
-            R rho, ux, uy, uz;
-            const R om = (v.ind && v.ind[(size_t)tl.x * nx + L]) ? v.omega_in : v.omega;
-            bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], om, p, rho, ux, uy, uz);
-            if (v.rec) {
-                const size_t n = (size_t)tl.x * nx + L;
-                v.rec[n] = rho;
-                v.rec[N + n] = ux;
-                v.rec[2 * N + n] = uy;
-                v.rec[3 * N + n] = uz;
+                for (int i = 0; i < Q; ++i)
+                    d[i] = dec<T, R>(at(i), PARITY ? ref_dir(i, rr.at(-cy(i), -cz(i))) : ref_dir(i, rr.own));
+                R rho, ux, uy, uz;
+                const R om = (v.ind && v.ind[(size_t)tl.x * nx + L]) ? v.omega_in : v.omega;
+                bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], om, p, rho, ux, uy, uz);
+                if (v.rec) {
+                    const size_t n = (size_t)tl.x * nx + L;
+                    v.rec[n] = rho;
+                    v.rec[N + n] = ux;
+                    v.rec[2 * N + n] = uy;
+                    v.rec[3 * N + n] = uz;
+                }
+                // outgoing direction i takes the place of incoming opp(i)
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    at(opp(i)) = enc<T, R>(p[i], PARITY ? ref_dir(i, rr.at(cy(i), cz(i))) : ref_dir(i, rr.own));
             }
-            // outgoing direction i takes the place of incoming opp(i)
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                at(opp(i)) = enc<T, R>(p[i], PARITY ? ref_dir(i, rr.at(cy(i), cz(i))) : ref_dir(i, rr.own));
+            x += dx;
+            j += dj;
+            if (x >= nx) {
+                x -= nx;
+                ++j;
+            }
         }
-        fence_async_smem();
-        __syncthreads();
-        if (storer) issue_store(it);
-        if (issuer && tile_of(it + S - 1) < ntiles) {
-            if (storer) bulk_wait_read<1>();  // this lane's range of tile it - 1 has been written out
-            issue_load(it + S - 1);           // into the stage tile it - 1 used
-        }
+        tl = tl_next;
+        fence_async_smem();  // this thread's writes, before the producer's bulk stores read them
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
     }
-    if (storer) bulk_wait_read<0>();
-    // then the rows next to walls, node by node: their nodes own population
-    // slots disjoint from the tiles', so the order does not matter
-    const long long ne = (long long)v.nerows * nx;
-    for (long long t = (long long)blockIdx.x * TILE_THREADS + threadIdx.x; t < ne; t += (long long)gridDim.x * TILE_THREADS) {
-        const int jr = (int)(t / nx);
-        collide_node<T, R, PARITY, I>(v, v.erows[jr] * nx + (int)(t - (long long)jr * nx));
-    }
+}
+
+// The rows next to walls of a staging plan, node by node, one node per
+// thread: their nodes own population slots disjoint from the tiles', so
+// the order of the two kernels does not matter.
+template <typename T, typename R, int PARITY, typename I>
+__global__ void __launch_bounds__(256, 4) collide_erows_kernel(View<R> v) {
+    const int nx = v.nx;
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (t >= (long long)v.nerows * nx) return;
+    const int jr = (int)(t / nx);
+    collide_node<T, R, PARITY, I>(v, v.erows[jr] * nx + (int)(t - (long long)jr * nx));
 }
 
 // post-streaming velocity u = (sum f c + F/2) / rho with the force just
@@ -905,17 +969,32 @@ void launch_collide_parity(const View<R> &v, int parity, cudaStream_t st) {
     }
 }
 
+template <typename T, typename R, int PARITY, typename I>
+void launch_tiles_pi(const View<R> &v, cudaStream_t st) {
+    collide_tiles_kernel<T, R, PARITY, I><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v);
+    const long long ne = (long long)v.nerows * v.nx;
+    if (ne > 0) collide_erows_kernel<T, R, PARITY, I><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(v);
+}
+
+template <typename T, typename R>
+void launch_tiles_as(const View<R> &v, int parity, cudaStream_t st) {
+    if (narrow_index(v)) {
+        if (parity) launch_tiles_pi<T, R, 1, unsigned>(v, st);
+        else launch_tiles_pi<T, R, 0, unsigned>(v, st);
+    } else {
+        if (parity) launch_tiles_pi<T, R, 1, size_t>(v, st);
+        else launch_tiles_pi<T, R, 0, size_t>(v, st);
+    }
+}
+
 template <typename R>
 void launch_collide(const View<R> &v, int precision, int parity, cudaStream_t st) {
     if constexpr (std::is_same<R, float>::value) {
-        // 16-bit storage, odd steps (reads and writes shifted by one node in
-        // x), on request: the staged kernel, which also collides the rows
-        // next to walls node by node once its tiles are done
-        if (v.ntiles && parity == 1) {
-            if (narrow_index(v))
-                HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1, unsigned><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
-            else
-                HEMO_DISPATCH_T(precision, R, (collide_tiles_kernel<T, R, 1, size_t><<<v.tile_grid, TILE_THREADS, v.tile_smem, st>>>(v)));
+        // 16-bit storage with a staging plan: the staged kernel, which also
+        // collides the rows next to walls node by node once its tiles are done
+        if (v.ntiles && (precision == HEMO_F16DEV || precision == HEMO_BF16DEV)) {
+            if (precision == HEMO_F16DEV) launch_tiles_as<__half, R>(v, parity, st);
+            else launch_tiles_as<__nv_bfloat16, R>(v, parity, st);
             return;
         }
     }
@@ -928,11 +1007,18 @@ cudaError_t set_tile_smem_limit(int precision, int bytes) {
     auto set = [&](const void *fn) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     };
-    using R = float;
-    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1, unsigned>)));
-    HEMO_DISPATCH_T(precision, R, (set((const void *)collide_tiles_kernel<T, R, 1, size_t>)));
+    auto set_all = [&](auto tag) {
+        using T = decltype(tag);
+        set((const void *)collide_tiles_kernel<T, float, 1, unsigned>);
+        set((const void *)collide_tiles_kernel<T, float, 1, size_t>);
+        set((const void *)collide_tiles_kernel<T, float, 0, unsigned>);
+        set((const void *)collide_tiles_kernel<T, float, 0, size_t>);
+    };
+    if (precision == HEMO_F16DEV) set_all(__half());
+    else if (precision == HEMO_BF16DEV) set_all(__nv_bfloat16());
     return e;
 }
+
 
 template <typename T, typename R, int LAYOUT, typename I>
 void launch_moments_as(const View<R> &v, cudaStream_t st) {

@@ -39,6 +39,7 @@ HEMO_OPT_TEST_STALLED_WAIT = 4
 HEMO_OPT_PAIR_COLLISION = 8
 HEMO_OPT_WIDE_INDEX = 16
 HEMO_OPT_NODE_STAGING = 32
+HEMO_OPT_UNSTAGED_COLLISION = 64
 HEMO_EULER, HEMO_AB2 = 0, 1
 INTEGRATORS = {'euler': HEMO_EULER, 'ab2': HEMO_AB2}
 

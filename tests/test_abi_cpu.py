@@ -218,7 +218,8 @@ def test_binding_layouts_match_the_header(tmp_path):
     consts = ['HEMO_OK', 'HEMO_ERR_ARG', 'HEMO_ERR_OOM', 'HEMO_ERR_CUDA', 'HEMO_ERR_NUMERIC', 'HEMO_ERR_DOMAIN',
               'HEMO_ERR_STATE', 'HEMO_RHO', 'HEMO_U', 'HEMO_VERTS', 'HEMO_FORCES', 'HEMO_CELLSTATS',
               'HEMO_OPT_STAGED_COLLISION', 'HEMO_OPT_NODE_COLLISION', 'HEMO_OPT_TEST_STALLED_WAIT',
-              'HEMO_OPT_PAIR_COLLISION', 'HEMO_OPT_WIDE_INDEX', 'HEMO_OPT_NODE_STAGING', 'HEMO_EULER',
+              'HEMO_OPT_PAIR_COLLISION', 'HEMO_OPT_WIDE_INDEX', 'HEMO_OPT_NODE_STAGING',
+              'HEMO_OPT_UNSTAGED_COLLISION', 'HEMO_EULER',
               'HEMO_AB2']
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hemo.h"', 'int main(void) {',
              'printf("lat %zu\\n", sizeof(hemo_lattice_desc));', 'printf("mesh %zu\\n", sizeof(hemo_mesh_desc));']

@@ -94,10 +94,8 @@ def test_stalled_wait_reports_and_context_survives():
     cfg = I.channel(nx=64, ny=20, nz=8, ncell=0, pack_iter=1)
     opts = hemo.HEMO_OPT_STAGED_COLLISION | hemo.HEMO_OPT_TEST_STALLED_WAIT
     sim = hemo.Simulation.from_config(cfg, 'f16', options=opts)
-    assert sim.lattice_plan()[0] > 0  # the staged kernel runs on odd steps
-    sim.step(1)   # even step: no staged kernel
-    sim.sync()
-    sim.step(1)   # odd step: the staged kernel's wait runs out
+    assert sim.lattice_plan()[0] > 0  # the staged kernel runs on every step
+    sim.step(1)   # the staged kernel's wait runs out
     with pytest.raises(hemo.HemoError) as e:
         sim.sync()
     assert e.value.code == hemo.HEMO_ERR_CUDA

@@ -2,9 +2,9 @@
 memory by bulk copies; HEMO_OPT_STAGED_COLLISION) against the per-node
 kernel (the default) on the same inputs:
 identical populations, density and velocity after an odd number of steps
-(both step parities), for the storage types that use it (16-bit), on
+(both step parities staged), for the storage types that use it (16-bit), on
 lattices with walls on one axis, with periodic wrap of the shifted rows in
-y and z, with ragged tiles, and with cells."""
+y and z, with ragged tiles, with long rows, and with cells."""
 import numpy as np
 import pytest
 
@@ -50,7 +50,13 @@ def box_case():
     return cfg
 
 
-CASES = {'shear': shear_case, 'channel': channel_case, 'box': box_case}
+def wide_case():
+    """Rows of 264 nodes: three rows per tile, the last tile of each plane
+    ragged (13 interior rows); walls at y = 0 and 16, x and z periodic."""
+    return _perturbed(_no_cells(I.channel(nx=264, ny=17, nz=10, ncell=0, pack_iter=1)), 4)
+
+
+CASES = {'shear': shear_case, 'channel': channel_case, 'box': box_case, 'wide': wide_case}
 
 
 def run(cfg, prec, steps, options):
@@ -89,19 +95,53 @@ def test_staged_with_cells_matches_per_node():
 
 def test_channel_plan():
     """64x64x256 channel, 16-bit storage: rows y = 2..61 of each z-plane are
-    wall-free (60 rows, 15 tiles of 4 rows = 256 nodes), rows 1 and 62 go to
-    the per-node kernel, rows 0 and 63 are walls.  A CTA's ring holds at most
-    54 KiB: four stages of 256 nodes at 50 B (19 two-byte populations and
-    three FP32 force components)."""
+    wall-free (60 rows: tiles of 16, 16, 16 and 12 rows, a stage holding
+    1024 nodes), rows 1 and 62 go to the per-node kernel, rows 0 and 63 are
+    walls.  The ring of the one CTA per SM takes four stages of 1024 nodes at
+    50 B (19 two-byte populations and three FP32 force components)."""
     cfg = _no_cells(I.channel(ncell=0, pack_iter=1))
     for prec in ('f16', 'bf16'):
         sim = hemo.Simulation.from_config(cfg, prec, options=hemo.HEMO_OPT_STAGED_COLLISION)
         plan = sim.lattice_plan()
         sim.close()
-        assert plan == (15 * 256, 2 * 256, 4, 4)
+        assert plan == (4 * 256, 2 * 256, 16, 4)
         sim = hemo.Simulation.from_config(cfg, prec)  # default: per-node kernel only
         assert sim.lattice_plan() == (0, 0, 0, 0)
         sim.close()
+
+
+def test_wide_plan():
+    """Rows of 1000 nodes (the pipe's length): one row per tile, staged by
+    default (rows of at least 512 nodes) and on request alike, not with
+    HEMO_OPT_UNSTAGED_COLLISION; rows of 1032 nodes are longer than a stage
+    holds and are not staged."""
+    cfg = _no_cells(I.channel(nx=1000, ny=12, nz=4, ncell=0, pack_iter=1))
+    for opts in (0, hemo.HEMO_OPT_STAGED_COLLISION):
+        sim = hemo.Simulation.from_config(cfg, 'bf16', options=opts)
+        plan = sim.lattice_plan()
+        sim.close()
+        assert plan == (8 * 4, 2 * 4, 1, 4)
+    for opts in (hemo.HEMO_OPT_UNSTAGED_COLLISION, hemo.HEMO_OPT_UNSTAGED_COLLISION | hemo.HEMO_OPT_STAGED_COLLISION):
+        sim = hemo.Simulation.from_config(cfg, 'bf16', options=opts)
+        assert sim.lattice_plan() == (0, 0, 0, 0)
+        sim.close()
+    cfg = _no_cells(I.channel(nx=1032, ny=12, nz=4, ncell=0, pack_iter=1))
+    sim = hemo.Simulation.from_config(cfg, 'bf16', options=hemo.HEMO_OPT_STAGED_COLLISION)
+    assert sim.lattice_plan() == (0, 0, 0, 0)
+    sim.close()
+
+
+@pytest.mark.parametrize('prec', ['f16', 'bf16'])
+def test_default_staging_matches_per_node(prec):
+    """Rows of 520 nodes are staged by default: the same bits as the
+    per-node kernel (HEMO_OPT_UNSTAGED_COLLISION) after an odd number of
+    steps."""
+    cfg = _perturbed(_no_cells(I.channel(nx=520, ny=14, nz=6, ncell=0, pack_iter=1)), 5)
+    plan, a = run(cfg, prec, 7, 0)
+    plan0, b = run(cfg, prec, 7, hemo.HEMO_OPT_UNSTAGED_COLLISION)
+    assert plan[0] > 0 and plan0 == (0, 0, 0, 0)
+    for k in ('f', 'rho', 'u'):
+        assert np.array_equal(a[k], b[k]), k
 
 
 def test_no_staging_for_4_and_8_byte_storage_or_unaligned_rows():
