@@ -394,7 +394,7 @@ def e2e_job(cfg, precision, torch):
 def traffic_from_profile(precision, workload):
     """DRAM bytes per collide launch from the committed ncu summary, if the
     kernel source has not changed since it was captured."""
-    path = os.path.join(ROOT, 'profiles', f'collide_stream_{precision}_{workload}.json')
+    path = os.path.join(ROOT, 'profiles', f'collide_{precision}_{workload}.json')
     if not os.path.exists(path):
         return None
     try:
@@ -491,6 +491,7 @@ def main():
     cfg, desc = make_workload(args.workload)
     flush = L2Flush(torch)
     sim = hemo.Simulation.from_config(cfg, precision)
+    staged = sim.lattice_plan()[0] > 0  # 16-bit storage on long rows: the staged collision
     sim.step(args.warmup)
     sim.sync()
     clocks = ClockSampler(local)
@@ -536,7 +537,8 @@ def main():
                        'event_overhead_us_per_boundary': 1e3 * (ptotal / PHASE_STEPS - total_ms / args.steps) / PHASE_MARKS,
                        'note': 'phase and kernel times from event nodes in the step graph over a second timed pass; '
                                'each phase includes the overhead of one event boundary'},
-        'roofline': {'bound': 'hbm', 'kernel': 'collide_stream', 'achieved': achieved, 'peak': peak,
+        'roofline': {'bound': 'hbm', 'kernel': 'collide_tiles + collide_erows' if staged else 'collide_stream',
+                     'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': (achieved / peak) if achieved else None,
                      'traffic': traffic_from_profile(precision, args.workload),
                      'algorithmic_bytes_per_launch': nf * bpn, 'peak_kind': f'{peak_kind} HBM copy bandwidth'},
