@@ -149,7 +149,7 @@ struct hemo_sim {
     unsigned options = 0;
     float2 *rref = nullptr;       // 16-bit storage: the rows' reference (P, M), see k_lattice.cu
     // staged collision (tiles of wall-free rows), see plan_rows
-    int2 *rtiles = nullptr;
+    int4 *rtiles = nullptr;
     int *erows = nullptr;
     int ntiles = 0, nerows = 0, tile_rows = 0, tile_stages = 0, tile_grid = 0, tile_smem = 0;
     // cells (host until finalised)
@@ -1091,14 +1091,14 @@ int plan_rows(hemo_sim *s, const uint8_t *mask) {
                 if (!row_fluid(y + dy, z + dz)) return false;
         return true;
     };
-    std::vector<int2> tiles;
+    std::vector<int4> tiles;
     std::vector<int> erows;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny;) {
             if (interior(y, z)) {
                 int len = 1;
                 while (len < k && y + len < ny && interior(y + len, z)) ++len;
-                tiles.push_back(make_int2(y + ny * z, len));
+                tiles.push_back(make_int4(y + ny * z, len, y, z));
                 y += len;
             } else {
                 if (any[(size_t)y + (size_t)ny * z]) erows.push_back(y + ny * z);
@@ -1109,10 +1109,10 @@ int plan_rows(hemo_sim *s, const uint8_t *mask) {
     const int nsm = s->nsm;
     const int smem = (int)(128 + stages * stage);
     HEMO_CU(set_tile_smem_limit(s->precision, (int)TILE_RING_BYTES));  // the cap of every plan
-    s->rtiles = (int2 *)dalloc(s, sizeof(int2) * tiles.size());
+    s->rtiles = (int4 *)dalloc(s, sizeof(int4) * tiles.size());
     s->erows = (int *)dalloc(s, sizeof(int) * std::max<size_t>(erows.size(), 1));
     if (!s->rtiles || !s->erows) return fail(HEMO_ERR_OOM, "allocation of the row tables failed");
-    HEMO_CU(cudaMemcpyAsync(s->rtiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
+    HEMO_CU(cudaMemcpyAsync(s->rtiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s->stream));
     if (!erows.empty())
         HEMO_CU(cudaMemcpyAsync(s->erows, erows.data(), sizeof(int) * erows.size(), cudaMemcpyHostToDevice, s->stream));
     HEMO_CU(cudaStreamSynchronize(s->stream));  // the host vectors go out of scope

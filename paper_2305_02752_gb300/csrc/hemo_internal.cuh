@@ -186,9 +186,10 @@ template <typename R> struct View {
     R *csp;                    // ncell*6 centroid of the last re-base as R hi (3), lo (3)
     int spread_all_nodes;      // 0: F = g + sum at fluid nodes, 0 at walls; 1: the sum at every node
     unsigned *status;
-    // staged collision: tiles {first row, rows} of wall-free rows (x-lines,
-    // row index y + ny z) and the other rows that hold fluid
-    const int2 *rtiles;
+    // staged collision: tiles {first row, rows, y, z of the first row} of
+    // wall-free rows (x-lines, row index y + ny z; a tile's rows lie in one
+    // z-plane) and the other rows that hold fluid
+    const int4 *rtiles;
     int ntiles, tile_rows, tile_stages, tile_grid, tile_smem;
     const int *erows;
     int nerows;

@@ -97,10 +97,12 @@ __device__ __forceinline__ RowRefs row_refs_of(const View<R> &v, int n, bool nei
     return row_refs<T>(v, r % v.ny, r / v.ny, neighbours);
 }
 
-// decode / encode one stored value with the reference `ref` of its slot
+// decode / encode one stored value with the reference `ref` of its slot;
+// has_ref false (directions with cx_i = 0, whose reference is zero): the
+// value as stored, without adding the zero
 template <typename T, typename R>
-__device__ __forceinline__ R dec(T s, float ref) {
-    if constexpr (HasRef<T>::value) return Store<T>::ld(s) + ref;
+__device__ __forceinline__ R dec(T s, float ref, bool has_ref) {
+    if constexpr (HasRef<T>::value) return has_ref ? Store<T>::ld(s) + ref : Store<T>::ld(s);
     else return Store<T>::ld(s);
 }
 template <typename T, typename R>
@@ -122,15 +124,15 @@ __device__ __forceinline__ void load_pops(const View<R> &v, int n, uint64_t lk, 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (LAYOUT == 0) {
-            d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(i, rr.own));
+            d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(i, rr.own), cx(i) != 0);
         } else {
             if (i == 0) {
-                d[i] = dec<T, R>(f[n], 0.f);
+                d[i] = dec<T, R>(f[n], 0.f, false);
             } else if (LINKS && link_code(lk, opp(i))) {  // slot i holds direction opp(i) leaving n
-                d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(opp(i), rr.own));
+                d[i] = dec<T, R>(f[(I)i * N + (I)n], ref_dir(opp(i), rr.own), cx(i) != 0);
             } else {  // direction i leaving n - c_i
                 d[i] = dec<T, R>(f[(I)opp(i) * N + (I)(n + o.of(-cx(i), -cy(i), -cz(i)))],
-                                 ref_dir(i, rr.at(-cy(i), -cz(i))));
+                                 ref_dir(i, rr.at(-cy(i), -cz(i))), cx(i) != 0);
             }
         }
     }
@@ -254,13 +256,12 @@ __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(K) : "memory");
 }
 
-// The rows of a tile (k rows from global row r0 = y0 + ny z) shifted by
+// The rows of a tile (k rows from row (y0, z) of the lattice) shifted by
 // (dy, dz), as at most two contiguous pieces (a periodic wrap in y splits
 // them): fn(first element of the piece in the lattice, first element in the
 // tile buffer, element count).
 template <typename R, typename Fn>
-__device__ __forceinline__ void tile_pieces(const View<R> &v, int r0, int k, int dy, int dz, Fn fn) {
-    const int y0 = r0 % v.ny, z = r0 / v.ny;
+__device__ __forceinline__ void tile_pieces(const View<R> &v, int y0, int z, int k, int dy, int dz, Fn fn) {
     const long long plane = (long long)v.ny * wrap(z + dz, v.nz);
     const int ya = wrap(y0 + dy, v.ny);
     const int c1 = min(k, v.ny - ya);
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> 
         // barrier (22 arrivals).
         const bool issuer = lane < TILE_COPIES, storer = lane < Q;
         auto issue_load = [&](int it) {
-            const int2 tl = v.rtiles[tile_of(it)];
+            const int4 tl = v.rtiles[tile_of(it)];
             const int s = it % S;
             unsigned char *st = ring + s * stage_bytes;
             const unsigned tn = (unsigned)(tl.y * nx);
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> 
                 T *buf = (T *)(st + lane * pop_bytes);
                 const T *src = f + (size_t)(PARITY ? opp(lane) : lane) * N;
                 mbar_expect_tx(full + s, tn * (unsigned)sizeof(T));
-                tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+                tile_pieces(v, tl.z, tl.w, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
                             [&](long long g, int b, int cnt) {
                                 bulk_load(buf + b, src + g, (unsigned)(cnt * sizeof(T)), full + s);
                             });
@@ -347,11 +348,11 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> 
             }
         };
         auto issue_store = [&](int it) {  // lane < 19: the range it loaded
-            const int2 tl = v.rtiles[tile_of(it)];
+            const int4 tl = v.rtiles[tile_of(it)];
             unsigned char *st = ring + (it % S) * stage_bytes;
             T *buf = (T *)(st + lane * pop_bytes);
             T *dst = f + (size_t)(PARITY ? opp(lane) : lane) * N;
-            tile_pieces(v, tl.x, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
+            tile_pieces(v, tl.z, tl.w, tl.y, PARITY ? -cy_of(lane) : 0, PARITY ? -cz_of(lane) : 0,
                         [&](long long g, int b, int cnt) { bulk_store(dst + g, buf + b, (unsigned)(cnt * sizeof(T))); });
             bulk_commit();
         };
@@ -396,11 +397,11 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> 
     // the tile table entry is read one tile ahead, and the references of
     // the thread's first row before the wait for the stage's data, so that
     // their latency overlaps the wait
-    int2 tl = tile_of(0) < ntiles ? v.rtiles[tile_of(0)] : make_int2(0, 0);
+    int4 tl = tile_of(0) < ntiles ? v.rtiles[tile_of(0)] : make_int4(0, 0, 0, 0);
     for (int it = 0; tile_of(it) < ntiles; ++it) {
         const int s = it % S;
-        const int2 tl_next = tile_of(it + 1) < ntiles ? v.rtiles[tile_of(it + 1)] : tl;
-        const int y0 = tl.x % v.ny, z0 = tl.x / v.ny;  // a tile's rows lie in one z-plane
+        const int4 tl_next = tile_of(it + 1) < ntiles ? v.rtiles[tile_of(it + 1)] : tl;
+        const int y0 = tl.z, z0 = tl.w;  // a tile's rows lie in one z-plane
         // the node's row and its neighbours' references (direction i arrives
         // from the row shifted by -c_i and leaves to the row shifted by
         // +c_i), reloaded when the row changes
@@ -431,7 +432,8 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) collide_tiles_kernel(View<R> 
                 R d[Q], p[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i)
-                    d[i] = dec<T, R>(at(i), PARITY ? ref_dir(i, rr.at(-cy(i), -cz(i))) : ref_dir(i, rr.own));
+                    d[i] = dec<T, R>(at(i), PARITY ? ref_dir(i, rr.at(-cy(i), -cz(i))) : ref_dir(i, rr.own),
+                                     cx(i) != 0);
                 R rho, ux, uy, uz;
                 const R om = (v.ind && v.ind[(size_t)tl.x * nx + L]) ? v.omega_in : v.omega;
                 bgk_guo<R>(d, Fs[L], Fs[TNM + L], Fs[2 * TNM + L], om, p, rho, ux, uy, uz);
@@ -547,11 +549,14 @@ template <> struct Bits<__nv_bfloat16> {
     static __device__ __forceinline__ unsigned short to(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
 };
 // the low / high 16-bit value of a pair word, decoded with reference ref
-template <typename T> __device__ __forceinline__ float dec_lo(unsigned w, float ref) {
-    return Store<T>::ld(Bits<T>::of((unsigned short)(w & 0xffffu))) + ref;
+// (not added when has_ref is false, as in dec)
+template <typename T> __device__ __forceinline__ float dec_lo(unsigned w, float ref, bool has_ref) {
+    const float x = Store<T>::ld(Bits<T>::of((unsigned short)(w & 0xffffu)));
+    return has_ref ? x + ref : x;
 }
-template <typename T> __device__ __forceinline__ float dec_hi(unsigned w, float ref) {
-    return Store<T>::ld(Bits<T>::of((unsigned short)(w >> 16))) + ref;
+template <typename T> __device__ __forceinline__ float dec_hi(unsigned w, float ref, bool has_ref) {
+    const float x = Store<T>::ld(Bits<T>::of((unsigned short)(w >> 16)));
+    return has_ref ? x + ref : x;
 }
 template <typename T> __device__ __forceinline__ unsigned enc16(float q, float ref) {
     return Bits<T>::to(Store<T>::st(q - ref));
@@ -626,7 +631,8 @@ __global__ void __launch_bounds__(NODE_BX * NODE_BY) collide_pair_kernel(View<fl
         const int n = n0 + h;
         float d[Q], p[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = h ? dec_hi<T>(w[i], ref_rd(i)) : dec_lo<T>(w[i], ref_rd(i));
+        for (int i = 0; i < Q; ++i)
+            d[i] = h ? dec_hi<T>(w[i], ref_rd(i), cx(i) != 0) : dec_lo<T>(w[i], ref_rd(i), cx(i) != 0);
         const float om = (VISC && act && v.ind && v.ind[n]) ? v.omega_in : v.omega;
         float rho, ux, uy, uz;
         bgk_guo<float>(d, h ? F0.y : F0.x, h ? F1.y : F1.x, h ? F2.y : F2.x, om, p, rho, ux, uy, uz);
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(NODE_BX * MOM_BY) moments_pair_kernel(View<flo
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float ref = LAYOUT == 0 ? ref_dir(i, rr.own) : ref_dir(i, rr.at(-cy(i), -cz(i)));
-            const float d = h ? dec_hi<T>(w[i], ref) : dec_lo<T>(w[i], ref);
+            const float d = h ? dec_hi<T>(w[i], ref, cx(i) != 0) : dec_lo<T>(w[i], ref, cx(i) != 0);
             drho += d;
             if (cx(i)) mx += cx(i) > 0 ? d : -d;
             if (cy(i)) my += cy(i) > 0 ? d : -d;
