@@ -96,7 +96,8 @@ class ClockSampler:
               'clocks_event_reasons.sw_thermal_slowdown', 'clocks_event_reasons.sw_power_cap']
 
     def __init__(self, device_index):
-        self.path = tempfile.mktemp(prefix='clocks_', suffix='.csv')
+        fd, self.path = tempfile.mkstemp(prefix='clocks_', suffix='.csv')
+        os.close(fd)
         self.dev = device_index
         self.proc = None
 
@@ -121,13 +122,21 @@ class ClockSampler:
         self.proc.terminate()
         self.proc.wait()
         self.fh.close()
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                p = [x.strip() for x in line.split(',')]
-                if len(p) == len(self.FIELDS):
-                    rows.append(p)
+            lines = f.readlines()
         os.unlink(self.path)
+        return self.summarise(lines)
+
+    @classmethod
+    def summarise(cls, lines):
+        """Median and largest SM clock and the throttle reasons seen active
+        in `nvidia-smi --format=csv,noheader,nounits` lines of FIELDS
+        (incomplete lines and non-numeric clocks are skipped)."""
+        rows = []
+        for line in lines:
+            p = [x.strip() for x in line.split(',')]
+            if len(p) == len(cls.FIELDS):
+                rows.append(p)
         sm = [float(r[1]) for r in rows if r[1].replace('.', '').isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
         names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
