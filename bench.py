@@ -117,7 +117,9 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': [], 'samples': 0}
+            if os.path.exists(self.path):
+                os.unlink(self.path)
+            return self.summarise([])
         time.sleep(0.2)
         self.proc.terminate()
         self.proc.wait()
