@@ -93,6 +93,28 @@ def test_staged_with_cells_matches_per_node():
         assert np.array_equal(a[k], b[k]), k
 
 
+def test_staged_with_internal_viscosity_matches_per_node():
+    """Cells with an internal viscosity ratio: the staged collision relaxes
+    the inside nodes with their own rate, as the per-node kernel does (the
+    same bits after an odd number of steps)."""
+    cfg = small_cell_shear(n=24, steps=9, seed=7)
+
+    def run_visc(opts):
+        sim = hemo.Simulation.from_config(cfg, 'f16', options=opts)
+        sim.set_viscosity_ratio(5.0)
+        plan = sim.lattice_plan()
+        sim.step(9)
+        out = sim.get_fields(hemo.HEMO_U | hemo.HEMO_VERTS)
+        out['f'] = sim.populations()
+        sim.close()
+        return plan, out
+    plan, a = run_visc(hemo.HEMO_OPT_STAGED_COLLISION)
+    plan0, b = run_visc(hemo.HEMO_OPT_UNSTAGED_COLLISION)
+    assert plan[0] > 0 and plan0 == (0, 0, 0, 0)
+    for k in ('f', 'u', 'X'):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_channel_plan():
     """64x64x256 channel, 16-bit storage: rows y = 2..61 of each z-plane are
     wall-free (60 rows: tiles of 16, 16, 16 and 12 rows, a stage holding
