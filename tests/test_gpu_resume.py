@@ -8,8 +8,9 @@ staged collision's bounded waits.
   cell in shear (k odd, so the populations are saved in the swapped in-place
   layout), with forces held over 3 steps and Adams-Bashforth (the held
   forces, the centroid split and the previous velocity are part of the
-  state), and BF16 storage with its row reference; a state is refused by a
-  simulation of another size or precision.
+  state), and BF16 storage with its row reference (per-node and staged
+  collision); a state is refused by a simulation of another size or
+  precision.
 * Stalled wait: with HEMO_OPT_TEST_STALLED_WAIT the staged collision, and
   the FP32 interpolation before its tensor copy, wait on a barrier that
   nothing completes; the wait runs out after 2 ms, the step reports
@@ -32,20 +33,20 @@ def _fields(sim):
     return out
 
 
-def _resume_case(cfg, prec, k, m, setup=None):
-    a = hemo.Simulation.from_config(cfg, prec)
+def _resume_case(cfg, prec, k, m, setup=None, options=0):
+    a = hemo.Simulation.from_config(cfg, prec, options=options)
     if setup:
         setup(a)
     a.step(k + m)
     ref = _fields(a)
     a.close()
-    b = hemo.Simulation.from_config(cfg, prec)
+    b = hemo.Simulation.from_config(cfg, prec, options=options)
     if setup:
         setup(b)
     b.step(k)
     state = b.save_state()
     b.close()
-    c = hemo.Simulation.from_config(cfg, prec)
+    c = hemo.Simulation.from_config(cfg, prec, options=options)
     c.load_state(state)
     c.step(m)
     got = _fields(c)
@@ -68,6 +69,13 @@ def test_resume_held_forces_ab2_bitwise():
 def test_resume_reduced_precision_bitwise(prec):
     cfg = I.channel(nx=32, ny=24, nz=40, ncell=3, seed=12, pack_iter=20, exact_iter=20)
     _resume_case(cfg, prec, 9, 4)
+
+
+def test_resume_staged_collision_bitwise():
+    """BF16 storage through the staged collision (forced on these short
+    rows), saved after an odd step."""
+    cfg = I.channel(nx=32, ny=24, nz=40, ncell=3, seed=12, pack_iter=20, exact_iter=20)
+    _resume_case(cfg, 'bf16', 9, 4, options=hemo.HEMO_OPT_STAGED_COLLISION)
 
 
 def test_state_of_another_simulation_is_refused():
