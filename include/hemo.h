@@ -94,10 +94,11 @@ typedef struct {
 enum { HEMO_OPT_STAGED_COLLISION = 1u, HEMO_OPT_UNSTAGED_COLLISION = 64u };
 
 /* 16-bit storage with nx even computes the post-streaming velocity two
- * nodes per thread (32-bit population pairs) and collides one node per
- * thread.  HEMO_OPT_NODE_COLLISION: one node per thread in both kernels;
- * HEMO_OPT_PAIR_COLLISION: two nodes per thread in both.  The results are the
- * same bits in every case; the options exist to compare the kernels. */
+ * nodes per thread (32-bit population pairs) and, where the collision is
+ * not staged, collides one node per thread.  HEMO_OPT_NODE_COLLISION: one
+ * node per thread in both kernels; HEMO_OPT_PAIR_COLLISION: two nodes per
+ * thread in both (the unstaged collision only).  The results are the same
+ * bits in every case; the options exist to compare the kernels. */
 enum { HEMO_OPT_NODE_COLLISION = 2u, HEMO_OPT_PAIR_COLLISION = 8u };
 
 /* HEMO_OPT_TEST_STALLED_WAIT: a test of the failure path of the kernels
